@@ -1,0 +1,146 @@
+/*
+ * libchem -- GB300 (sm_103a) per-cell chemistry step: C ABI.
+ *
+ * The operation is the paper's chemistry step (Sec. 2.2): each cell's state (T, p, Y_k)
+ * is advanced over one flow time step dt by integrating the reaction system of Eq. 1,
+ * producing the input -> output map of Eq. 2.  Beside it sit the mixture thermo/transport
+ * properties the paper updates on the GPU (Sec. 2.1, "Newton's method and high-order
+ * temperature polynomials").
+ *
+ * Conventions for every entry point
+ *   - Array arguments are DEVICE pointers owned by the caller; the library never frees them
+ *     and never keeps them after the call returns (the work is enqueued on `stream`).
+ *   - States are FP64 structure-of-arrays, species-major: Y[k * ld + i] is species k of cell
+ *     i; T[i], p[i] per cell; ld >= n.  Units are SI: K, Pa, kg/m^3, J/kg, W/m/K, Pa s, s.
+ *   - Every call is asynchronous on `stream` (NULL = the legacy default stream) and returns
+ *     0 on success or a negative CHEM_E* code; chem_last_error() then gives a message
+ *     (thread-local).  Kernel-side problems of a single cell never fail the call: they are
+ *     reported in the caller's int32 status[] array (codes below).  No kernel traps; every
+ *     device loop is bounded.
+ *   - Opaque handles are owned by the library and released by their *_free function.
+ */
+#ifndef CHEM_H
+#define CHEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* chem_stream;   /* same object as cudaStream_t */
+typedef struct chem_mech_s* chem_mech;
+
+/* return codes */
+#define CHEM_OK 0
+#define CHEM_E_ARG -1      /* bad argument (null pointer, size, ld < n, ...) */
+#define CHEM_E_PARSE -2    /* mechanism file unreadable or malformed */
+#define CHEM_E_CUDA -3     /* a CUDA runtime call failed (message says which) */
+#define CHEM_E_NOMEM -4    /* device allocation for library-owned tables failed */
+#define CHEM_E_WORKSPACE -5 /* workspace missing or smaller than chem_workspace_bytes() */
+#define CHEM_E_UNSUPPORTED -6 /* mechanism larger than the compiled kernels support */
+
+/* per-cell status codes written to status[] */
+#define CHEM_CELL_OK 0
+#define CHEM_CELL_MAX_STEPS 1    /* step budget (opts.max_steps) exhausted */
+#define CHEM_CELL_STEP_FAIL 2    /* step size underflow after Newton / error-test failures */
+#define CHEM_CELL_NONFINITE 3    /* non-finite input or result; state left unchanged */
+#define CHEM_CELL_OUT_OF_RANGE 4 /* input outside the model's validity (T, p, Y) */
+#define CHEM_CELL_ANN_FALLBACK 5 /* the learned step flagged the cell; DI result written */
+
+/* Library limits of the compiled kernels. */
+#define CHEM_MAX_SPECIES 63      /* n = species + 1 <= 64 unknowns per cell */
+#define CHEM_MAX_REACTIONS 1024
+
+/* ---------------------------------------------------------------------------------------- */
+/* Mechanism                                                                                */
+/* ---------------------------------------------------------------------------------------- */
+/* Parse a mechanism file (this project's plain-text SI format: elements, species with
+ * molar masses and compositions, two-range NASA-7 coefficients, transport fits
+ * ln(mu), ln(lambda) = sum_n b_n (ln T)^n, reactions with Arrhenius A [m,mol,s], b,
+ * Ea [J/mol], third-body efficiencies, Troe low-pressure limits and parameters),
+ * validate element balance, and upload the device tables to the current device.
+ * *out receives a handle owned by the library.  Returns CHEM_E_PARSE on malformed input. */
+int chem_load_mech(const char* path, chem_mech* out);
+void chem_free_mech(chem_mech mech);
+int chem_mech_info(chem_mech mech, int* n_species, int* n_reactions, int* n_elements);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Reaction rates (Eq. 1 right-hand side)                                                   */
+/* ---------------------------------------------------------------------------------------- */
+/* Net molar production rates wdot[k * ld + i] (mol/m^3/s) and, if hrr is not NULL, the heat
+ * release rate hrr[i] = -sum_k h_k wdot_k (W/m^3) of n cells at (T[i], p[i], Y[:, i]).
+ * Forward rates k = A T^b exp(-Ea/RT) (third-body [M] = sum_k alpha_k C_k; Lindemann falloff
+ * with the Troe form), reverse rates from K_c = exp(-sum nu g/RT) (p0/RT)^{sum nu},
+ * p0 = 101325 Pa, all in FP64. */
+int chem_rates(chem_mech mech, int64_t n, int64_t ld, const double* T, const double* p,
+               const double* Y, double* wdot, double* hrr, chem_stream stream);
+
+/* Analytic Jacobian of the constant-pressure reactor right-hand side, z = (Y_1..Y_K, T):
+ * jac[i * nn + r * nn_row + c] is d f_r / d z_c of cell i with nn_row = K + 1 and
+ * nn = (K + 1)^2 (row-major per cell, cells contiguous).  Exposed for parity testing. */
+int chem_jacobian(chem_mech mech, int64_t n, int64_t ld, const double* T, const double* p,
+                  const double* Y, double* jac, chem_stream stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Direct integration (Eq. 2)                                                               */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+  double rtol;      /* relative tolerance (default 1e-9 when <= 0) */
+  double atol_Y;    /* absolute tolerance on mass fractions (default 1e-20 when <= 0) */
+  double atol_T;    /* absolute tolerance on T in K (default 1e-9 when <= 0) */
+  int max_steps;    /* per-cell step budget (default 20000 when <= 0) */
+  int reserved;
+} chem_di_opts;
+
+/* Advance cells over dt by direct integration of the closed, adiabatic, constant-pressure
+ * reactor (Eq. 1 with dT/dt = -sum_k h_k wdot_k / (rho c_p)), in place: T[i] and Y[:, i]
+ * are overwritten with the state at t + dt; p[i] is constant.  Variable-order (1..5) BDF
+ * with a modified Newton iteration (analytic Jacobian, dense LU with partial pivoting, all
+ * FP64), one warp per cell.
+ *   idx      NULL to integrate cells 0..n-1, else int32 idx[n] lists the cell columns to
+ *            integrate (indices into the ld-strided arrays, each < ld).
+ *   opts     NULL for defaults.
+ *   status   int32 status[n] (per entry of idx, or per cell), CHEM_CELL_* codes; cells whose
+ *            status is non-zero keep their input state.
+ *   stats    NULL, or int32 stats[4 * n]: steps, RHS evaluations, Jacobian evaluations and
+ *            LU factorisations per cell (stats[k * n + i]), for work accounting.
+ *   workspace device scratch of at least chem_workspace_bytes(mech, n) bytes (the cell work
+ *            queue); it must not be used by another call in flight.
+ * Returns CHEM_E_WORKSPACE if the workspace is missing or too small. */
+int chem_step_di(chem_mech mech, int64_t n, int64_t ld, double dt, double* T, const double* p,
+                 double* Y, const int32_t* idx, const chem_di_opts* opts, int32_t* status,
+                 int32_t* stats, void* workspace, size_t ws_bytes, chem_stream stream);
+
+/* Device scratch needed by chem_step_di for n cells (bytes). */
+size_t chem_workspace_bytes(chem_mech mech, int64_t n);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Mixture thermo and transport properties (Sec. 2.1)                                        */
+/* ---------------------------------------------------------------------------------------- */
+/* Per cell: c_p [J/kg/K] and h [J/kg] (mass-weighted NASA-7), Wilke mixture viscosity mu
+ * [Pa s] and the mixture-averaged conductivity kappa = (sum X_k lambda_k + 1/sum X_k/lambda_k)/2
+ * [W/m/K], with ln(mu_k), ln(lambda_k) cubic in ln T.  Each output may be NULL.
+ * If h_in is not NULL, T is first solved from h(T, Y) = h_in[i] by Newton's method starting
+ * at T[i] (|dT| < 1e-9 K, at most 50 iterations, clamped to [200, 6000] K), written to T_out
+ * (which may alias T), and the properties are evaluated there.
+ * All FP64 when mixed_precision == 0; with mixed_precision == 1 the O(K^2) Wilke and the
+ * conductivity sums run in FP32 (relative error below 1e-5) while c_p, h and the Newton
+ * solve stay FP64. */
+int thermo_props(chem_mech mech, int64_t n, int64_t ld, const double* T, const double* Y,
+                 double* cp, double* h, double* mu, double* kappa, const double* h_in,
+                 double* T_out, int mixed_precision, chem_stream stream);
+
+/* Thread-local description of the last error returned on this thread. */
+const char* chem_last_error(void);
+
+/* Measured FP64 FMA throughput of the current device (GFLOP/s, 2 flops per FMA): a short
+ * DFMA kernel over every SM, timed with CUDA events on `stream`.  Used as the denominator of
+ * the DI roofline. */
+int chem_fp64_peak_gflops(double* gflops, chem_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHEM_H */

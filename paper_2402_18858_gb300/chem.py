@@ -1,0 +1,164 @@
+"""Thin Python binding of libchem (ctypes): argument marshalling only.
+
+Every function has the name of the C entry point it wraps (include/chem.h) and takes torch
+CUDA tensors; all arithmetic runs in the library's kernels.  There is no fallback: if the
+shared library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+_lib = None
+_lock = threading.Lock()
+
+
+class ChemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libchem error {code}: {msg}")
+        self.code = code
+
+
+class DiOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol_Y", C.c_double), ("atol_T", C.c_double),
+                ("max_steps", C.c_int), ("reserved", C.c_int)]
+
+
+def lib(auto_build: bool = False):
+    """The loaded libchem.so (built in-tree by `build.build()`)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not auto_build:
+                raise RuntimeError(f"libchem is not built ({path} missing): run build() first")
+            _build.build()
+        L = C.CDLL(path)
+        vp, i64, dbl, i32 = C.c_void_p, C.c_int64, C.c_double, C.c_int
+        L.chem_load_mech.argtypes = [C.c_char_p, C.POINTER(vp)]
+        L.chem_free_mech.argtypes = [vp]
+        L.chem_free_mech.restype = None
+        L.chem_mech_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.chem_rates.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+        L.chem_jacobian.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
+        L.chem_step_di.argtypes = [vp, i64, i64, dbl, vp, vp, vp, vp, C.POINTER(DiOpts), vp, vp,
+                                   vp, C.c_size_t, vp]
+        L.chem_workspace_bytes.argtypes = [vp, i64]
+        L.chem_workspace_bytes.restype = C.c_size_t
+        L.thermo_props.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
+        L.chem_last_error.restype = C.c_char_p
+        L.chem_fp64_peak_gflops.argtypes = [C.POINTER(dbl), vp]
+        _lib = L
+        return L
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise ChemError(rc, lib().chem_last_error().decode(errors="replace"))
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libchem takes CUDA tensors")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("libchem takes contiguous tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Mech:
+    """A mechanism loaded on the current device (owns a chem_mech handle)."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+        K, I, E = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().chem_mech_info(self.handle, C.byref(K), C.byref(I), C.byref(E)))
+        self.K, self.I, self.E = K.value, I.value, E.value
+        self.n = self.K + 1
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().chem_free_mech(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def chem_load_mech(path: str) -> Mech:
+    h = C.c_void_p()
+    _check(lib().chem_load_mech(path.encode(), C.byref(h)))
+    return Mech(h.value)
+
+
+def _ld(Y: torch.Tensor, m: Mech) -> int:
+    if Y.dim() != 2 or Y.shape[0] != m.K:
+        raise ValueError(f"Y must be [K={m.K}, ld]")
+    return Y.shape[1]
+
+
+def chem_rates(m: Mech, T, p, Y, wdot, hrr=None, n: Optional[int] = None, stream=None) -> None:
+    ld = _ld(Y, m)
+    n = ld if n is None else n
+    _check(lib().chem_rates(m.handle, n, ld, _ptr(T, torch.float64), _ptr(p, torch.float64),
+                            _ptr(Y, torch.float64), _ptr(wdot, torch.float64),
+                            _ptr(hrr, torch.float64), _stream(stream)))
+
+
+def chem_jacobian(m: Mech, T, p, Y, jac, n: Optional[int] = None, stream=None) -> None:
+    ld = _ld(Y, m)
+    n = ld if n is None else n
+    _check(lib().chem_jacobian(m.handle, n, ld, _ptr(T, torch.float64), _ptr(p, torch.float64),
+                               _ptr(Y, torch.float64), _ptr(jac, torch.float64), _stream(stream)))
+
+
+def chem_workspace_bytes(m: Mech, n: int) -> int:
+    return int(lib().chem_workspace_bytes(m.handle, n))
+
+
+def chem_step_di(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0, atol_Y=0.0, atol_T=0.0,
+                 max_steps=0, stats=None, workspace=None, n: Optional[int] = None,
+                 stream=None) -> None:
+    ld = _ld(Y, m)
+    if n is None:
+        n = idx.numel() if idx is not None else ld
+    if workspace is None:
+        raise ValueError("chem_step_di needs a workspace tensor (chem_workspace_bytes)")
+    o = DiOpts(rtol, atol_Y, atol_T, max_steps, 0)
+    _check(lib().chem_step_di(m.handle, n, ld, float(dt), _ptr(T, torch.float64),
+                              _ptr(p, torch.float64), _ptr(Y, torch.float64),
+                              _ptr(idx, torch.int32), C.byref(o), _ptr(status, torch.int32),
+                              _ptr(stats, torch.int32), _ptr(workspace),
+                              workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def thermo_props(m: Mech, T, Y, cp=None, h=None, mu=None, kappa=None, h_in=None, T_out=None,
+                 mixed_precision: bool = False, n: Optional[int] = None, stream=None) -> None:
+    ld = _ld(Y, m)
+    n = ld if n is None else n
+    f64 = torch.float64
+    _check(lib().thermo_props(m.handle, n, ld, _ptr(T, f64), _ptr(Y, f64), _ptr(cp, f64),
+                              _ptr(h, f64), _ptr(mu, f64), _ptr(kappa, f64), _ptr(h_in, f64),
+                              _ptr(T_out, f64), int(bool(mixed_precision)), _stream(stream)))
+
+
+def chem_fp64_peak_gflops(stream=None) -> float:
+    v = C.c_double()
+    _check(lib().chem_fp64_peak_gflops(C.byref(v), _stream(stream)))
+    return v.value

@@ -1,0 +1,1048 @@
+// Warp-per-cell FP64 chemistry kernels for sm_103a: reaction rates (Eq. 1 right-hand side),
+// the analytic Jacobian, and direct integration over one flow step (Eq. 2) by a
+// variable-order BDF with a modified Newton iteration.
+//
+// Design (GB300): FP64 issue is the bottleneck (two FP64 lanes per clock per SM, so a warp
+// FP64 instruction occupies the pipe for 16 cycles and idle lanes cost the same as busy
+// ones).  One warp integrates one cell: lane k owns species k (and k + 32) and row k of the
+// n x n Newton matrix; lane j evaluates reactions j, j + 32, ...; reductions are warp
+// shuffles in a fixed order (results are bit-identical across lanes and runs).  Per-warp
+// shared memory holds the Jacobian, its LU factors and the per-reaction terms; the BDF
+// history lives in registers.  Step-control arithmetic that only steers heuristics (error
+// norms, step-size factors) runs in FP32, the solution, the rates, the equilibrium
+// constants and the LU stay FP64.  Every loop is bounded and every failure becomes a
+// per-cell status code.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace chem {
+
+#define FULLMASK 0xffffffffu
+
+// ------------------------------------------------------------------------------------------
+// warp helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double wsum(double v) {
+  // fixed-order tree into lane 0, then broadcast: every lane sees the same bits
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULLMASK, v, o);
+  return __shfl_sync(FULLMASK, v, 0);
+}
+
+__device__ __forceinline__ float wsumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULLMASK, v, o);
+  return __shfl_sync(FULLMASK, v, 0);
+}
+
+template <int NPL>
+__device__ __forceinline__ double comp_get(const double (&x)[NPL], int i) {
+  // value of component i (owned by lane i & 31, slot i >> 5), on every lane
+  double v = x[0];
+  if (NPL > 1 && (i >> 5) == 1) v = x[NPL > 1 ? 1 : 0];
+  return __shfl_sync(FULLMASK, v, i & 31);
+}
+
+// ------------------------------------------------------------------------------------------
+// per-warp shared memory
+// ------------------------------------------------------------------------------------------
+struct WarpMem {
+  double* J;      // n x ld (Jacobian; rows 0..K-1 first hold dwdot/dC)
+  double* LU;     // n x ld (factors of I - c J)
+  double* C;      // K concentrations
+  double* hRT;    // K
+  double* g;      // K   g/RT = h/RT - s/R
+  double* eg;     // K   exp(-(g/RT - shift)), shift = element-potential term
+  double* ieg;    // K   exp(+(g/RT - shift))
+  double* q;      // I   net rates of progress
+  double* kfe;    // I   effective forward coefficient (third-body factor included)
+  double* kre;    // I   effective reverse coefficient
+  double* aux;    // I   d q / d [M] factor (third-body: q0, Troe: dk/dM (fwd - rev/Kc))
+  double* qT;     // I   d q / d T at fixed C
+  double* invd;   // n   reciprocal pivots
+  double* ru;     // 25  step-size change matrix
+  int* perm;      // n   row permutation of the LU
+  int ld;
+};
+
+__host__ __device__ inline int pad_ld(int n) { return n | 1; }
+
+// doubles per warp: matrices (optional) + species + reactions + small vectors
+__host__ __device__ inline size_t warp_doubles(int K, int I, int n, bool mats, bool jac) {
+  size_t ld = pad_ld(n);
+  size_t d = (mats ? 2 * (size_t)n * ld : (jac ? (size_t)n * ld : 0));
+  d += 5 * (size_t)K + (jac ? 5 : 1) * (size_t)(I > 0 ? I : 1);
+  d += (size_t)n + 32 + (size_t)(n + 1) / 2 + 2;
+  return (d + 1) & ~size_t(1);   // keep 16-byte alignment per warp
+}
+
+__device__ __forceinline__ WarpMem carve(double* base, int K, int I, int n, bool mats, bool jac) {
+  WarpMem w;
+  w.ld = pad_ld(n);
+  double* p = base;
+  w.J = nullptr;
+  w.LU = nullptr;
+  if (mats || jac) { w.J = p; p += (size_t)n * w.ld; }
+  if (mats) { w.LU = p; p += (size_t)n * w.ld; }
+  w.C = p; p += K;
+  w.hRT = p; p += K;
+  w.g = p; p += K;
+  w.eg = p; p += K;
+  w.ieg = p; p += K;
+  const int Ir = I > 0 ? I : 1;
+  w.q = p; p += Ir;
+  if (jac) {
+    w.kfe = p; p += Ir;
+    w.kre = p; p += Ir;
+    w.aux = p; p += Ir;
+    w.qT = p; p += Ir;
+  } else {
+    w.kfe = w.kre = w.aux = w.qT = nullptr;
+  }
+  w.invd = p; p += n;
+  w.ru = p; p += 32;
+  w.perm = (int*)p;
+  return w;
+}
+
+// per-lane species values kept between the RHS and the Jacobian
+template <int NPL>
+struct LaneSp {
+  double cpR[NPL], dcpR[NPL], hRT[NPL], wdot[NPL];
+};
+
+struct CellSc {
+  double T, lnT, invT, RT, rho, Wbar, cp, Q;
+};
+
+// ------------------------------------------------------------------------------------------
+// Troe falloff (Lindemann form with the Troe broadening factor, Gilbert, Luther & Troe 1983)
+// ------------------------------------------------------------------------------------------
+template <bool JAC>
+__device__ __forceinline__ double troe_k(const double* __restrict__ tp, double T, double invT,
+                                         double lnT, double M, double kinf, double dlnkinf,
+                                         double& dkdM, double& dlnk) {
+  const double k0 = exp(tp[0] + tp[1] * lnT - tp[2] * invT);
+  const double a = tp[3], iT3 = tp[4], iT1 = tp[5], T2 = tp[6];
+  const double e3 = exp(-T * iT3), e1 = exp(-T * iT1);
+  double Fc = (1.0 - a) * e3 + a * e1;
+  double dFc = -(1.0 - a) * iT3 * e3 - a * iT1 * e1;
+  if (tp[7] != 0.0) {
+    const double e2 = exp(-T2 * invT);
+    Fc += e2;
+    dFc += T2 * invT * invT * e2;
+  }
+  double Pr = k0 * M / kinf;
+  Pr = fmax(Pr, 1e-300);
+  const double L = log10(Fc);
+  const double c = -0.4 - 0.67 * L;
+  const double nn = 0.75 - 1.27 * L;
+  const double x = log10(Pr) + c;
+  const double den = nn - 0.14 * x;
+  const double f1 = x / den;
+  const double opf = 1.0 + f1 * f1;
+  const double F = exp10(L / opf);
+  const double ipr = 1.0 / (1.0 + Pr);
+  const double k = kinf * Pr * ipr * F;
+  if (JAC) {
+    const double df1dx = nn / (den * den);
+    const double gg = -L * 2.0 * f1 / (opf * opf) * df1dx;          // d log F / d log Pr
+    dkdM = k0 * F * (ipr * ipr + gg * ipr);
+    const double df1dL = df1dx * (-0.67) + (-x / (den * den)) * (-1.27);
+    const double dlogFdL = 1.0 / opf - L * 2.0 * f1 / (opf * opf) * df1dL;
+    const double dlnk0 = tp[1] * invT + tp[2] * invT * invT;
+    dlnk = dlnkinf + (ipr + gg) * (dlnk0 - dlnkinf) + dlogFdL * dFc / Fc;
+  }
+  return k;
+}
+
+// ------------------------------------------------------------------------------------------
+// right-hand side f(z) of the reactor, z = (Y_1..Y_K, T)  [Eq. 1]
+// ------------------------------------------------------------------------------------------
+template <int NPL, bool JAC>
+__device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, const double (&y)[NPL],
+                         double (&f)[NPL], LaneSp<NPL>& sp, CellSc& cs, int lane) {
+  const int K = m.K, I = m.I;
+  const double T = comp_get<NPL>(y, K);
+  const double lnT = log(T), invT = 1.0 / T, RT = kR * T;
+  double sYW = 0.0;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int k = lane + 32 * s;
+    if (k < K) sYW += y[s] * __ldg(m.invW + k);
+  }
+  sYW = wsum(sYW);
+  const double Wbar = 1.0 / sYW;
+  const double rho = p * Wbar / RT;
+  double ctot = 0.0, cpp = 0.0;
+  const int hi = T >= m.Tmid ? 1 : 0;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int k = lane + 32 * s;
+    sp.cpR[s] = sp.dcpR[s] = sp.hRT[s] = 0.0;
+    if (k < K) {
+      const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
+      const double a0 = __ldg(a + 0), a1 = __ldg(a + 1), a2 = __ldg(a + 2), a3 = __ldg(a + 3), a4 = __ldg(a + 4);
+      const double cpR = a0 + T * (a1 + T * (a2 + T * (a3 + T * a4)));
+      const double hRT = __ldg(a + 5) + T * (__ldg(a + 6) + T * (__ldg(a + 7) + T * (__ldg(a + 8) + T * __ldg(a + 9))))
+                         + __ldg(a + 10) * invT;
+      const double sR = __ldg(a + 11) * lnT + T * (__ldg(a + 12) + T * (__ldg(a + 13) + T * (__ldg(a + 14) + T * __ldg(a + 15))))
+                        + __ldg(a + 16);
+      if (JAC) sp.dcpR[s] = a1 + T * (2.0 * a2 + T * (3.0 * a3 + T * 4.0 * a4));
+      const double iW = __ldg(m.invW + k);
+      const double Ck = rho * y[s] * iW;
+      w.C[k] = Ck;
+      w.hRT[k] = hRT;
+      w.g[k] = hRT - sR;
+      sp.cpR[s] = cpR;
+      sp.hRT[s] = hRT;
+      ctot += Ck;
+      cpp += y[s] * cpR * iW;
+    }
+  }
+  ctot = wsum(ctot);
+  const double cp = wsum(cpp) * kR;
+  __syncwarp();
+  // exp(-g'/RT) per species, g' = g - sum_r P_kr g_ref_r (one exp per species instead of
+  // one per reaction; the element-potential shift cancels in every balanced reaction)
+  const int R = m.n_ref;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int k = lane + 32 * s;
+    if (k < K) {
+      double gs = w.g[k];
+      for (int r = 0; r < R; ++r) gs -= __ldg(m.P + (size_t)k * R + r) * w.g[__ldg(m.ref_sp + r)];
+      const double e = exp(-gs);
+      w.eg[k] = e;
+      w.ieg[k] = 1.0 / e;
+    }
+  }
+  __syncwarp();
+  const double P0RT = kP0 / RT, RTP0 = RT / kP0;
+  for (int j = lane; j < I; j += 32) {
+    const int4 ra = __ldg((const int4*)(m.rsp + 8 * (size_t)j));
+    const int4 rb = __ldg((const int4*)(m.rsp + 8 * (size_t)j + 4));
+    const double2 a01 = __ldg((const double2*)(m.arr + 4 * (size_t)j));
+    const double2 a23 = __ldg((const double2*)(m.arr + 4 * (size_t)j + 2));
+    double kf = exp(a01.x + a01.y * lnT - a23.x * invT);
+    double dlnkf = 0.0;
+    if (JAC) dlnkf = a01.y * invT + a23.x * invT * invT;
+    // kr / kf = 1/K_c = exp(sum nu g/RT) (p0/RT)^(-sum nu) = prod_r e_r prod_p (1/e_p) ...
+    double fwd = w.C[ra.x], ratio = w.eg[ra.x], sh = 0.0;
+    if (JAC) sh = -w.hRT[ra.x];
+    if (ra.w > 1) { fwd *= w.C[ra.y]; ratio *= w.eg[ra.y]; if (JAC) sh -= w.hRT[ra.y]; }
+    if (ra.w > 2) { fwd *= w.C[ra.z]; ratio *= w.eg[ra.z]; if (JAC) sh -= w.hRT[ra.z]; }
+    double rev = w.C[rb.x];
+    ratio *= w.ieg[rb.x];
+    if (JAC) sh += w.hRT[rb.x];
+    if (rb.w > 1) { rev *= w.C[rb.y]; ratio *= w.ieg[rb.y]; if (JAC) sh += w.hRT[rb.y]; }
+    if (rb.w > 2) { rev *= w.C[rb.z]; ratio *= w.ieg[rb.z]; if (JAC) sh += w.hRT[rb.z]; }
+    const int dnu = (int)a23.y;
+    if (dnu == -1) ratio *= P0RT;
+    else if (dnu == 1) ratio *= RTP0;
+    else if (dnu == -2) ratio *= P0RT * P0RT;
+    else if (dnu == 2) ratio *= RTP0 * RTP0;
+    double Mfac = 1.0, dkdM = 0.0;
+    if (j >= m.n_elem) {
+      double M = ctot;
+#pragma unroll
+      for (int e = 0; e < kMaxEx; ++e) {
+        const int se = __ldg(m.ex_sp + (size_t)j * kMaxEx + e);
+        if (se >= 0) M += __ldg(m.ex_a + (size_t)j * kMaxEx + e) * w.C[se];
+      }
+      if (j < m.n_tb_end) {
+        Mfac = M;
+      } else {
+        double dlnk = 0.0;
+        kf = troe_k<JAC>(m.troe + 8 * (size_t)j, T, invT, lnT, M, kf, dlnkf, dkdM, dlnk);
+        dlnkf = dlnk;
+      }
+    }
+    const double kr = kf * ratio;
+    const double q0 = kf * fwd - kr * rev;
+    w.q[j] = Mfac * q0;
+    if (JAC) {
+      w.kfe[j] = Mfac * kf;
+      w.kre[j] = Mfac * kr;
+      w.aux[j] = (j < m.n_elem) ? 0.0 : (j < m.n_tb_end ? q0 : dkdM * (fwd - ratio * rev));
+      const double dlnKc = (sh - a23.y) * invT;
+      w.qT[j] = Mfac * (kf * dlnkf * fwd - kr * (dlnkf - dlnKc) * rev);
+    }
+  }
+  __syncwarp();
+  double Qp = 0.0;
+  const double irho = 1.0 / rho;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int k = lane + 32 * s;
+    f[s] = 0.0;
+    sp.wdot[s] = 0.0;
+    if (k < K) {
+      const int e0 = __ldg(m.sp_ptr + k), e1 = __ldg(m.sp_ptr + k + 1);
+      double wd = 0.0;
+      for (int e = e0; e < e1; ++e) wd += __ldg(m.sp_nu + e) * w.q[__ldg(m.sp_rxn + e)];
+      sp.wdot[s] = wd;
+      f[s] = __ldg(m.W + k) * wd * irho;
+      Qp += sp.hRT[s] * wd;
+    }
+  }
+  const double Q = wsum(Qp) * RT;
+  const double fT = -Q / (rho * cp);
+#pragma unroll
+  for (int s = 0; s < NPL; ++s)
+    if (lane + 32 * s == K) f[s] = fT;
+  cs.T = T; cs.lnT = lnT; cs.invT = invT; cs.RT = RT; cs.rho = rho; cs.Wbar = Wbar;
+  cs.cp = cp; cs.Q = Q;
+}
+
+// ------------------------------------------------------------------------------------------
+// analytic Jacobian d f / d z into w.J (row-major, ld), after rhs_eval<NPL, true>
+// ------------------------------------------------------------------------------------------
+template <int NPL>
+__device__ void jac_assemble(const DevMech& m, const WarpMem& w, const double (&y)[NPL],
+                             const LaneSp<NPL>& sp, const CellSc& cs, int lane) {
+  const int K = m.K, ld = w.ld;
+  double dwdT[NPL], S[NPL], colH[NPL];
+  // d wdot_k / d C_m at fixed T (rows of species k), and d wdot_k / dT at fixed C
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int k = lane + 32 * s;
+    dwdT[s] = 0.0;
+    if (k < K) {
+      double* row = w.J + (size_t)k * ld;
+      for (int c = 0; c < K; ++c) row[c] = 0.0;
+      double acc = 0.0, dT = 0.0;
+      const int e0 = __ldg(m.sp_ptr + k), e1 = __ldg(m.sp_ptr + k + 1);
+      for (int e = e0; e < e1; ++e) {
+        const int j = __ldg(m.sp_rxn + e);
+        const double nu = __ldg(m.sp_nu + e);
+        const int4 ra = __ldg((const int4*)(m.rsp + 8 * (size_t)j));
+        const int4 rb = __ldg((const int4*)(m.rsp + 8 * (size_t)j + 4));
+        const double kf = nu * w.kfe[j], kr = nu * w.kre[j];
+        if (ra.w == 1) {
+          row[ra.x] += kf;
+        } else if (ra.w == 2) {
+          row[ra.x] += kf * w.C[ra.y];
+          row[ra.y] += kf * w.C[ra.x];
+        } else {
+          row[ra.x] += kf * w.C[ra.y] * w.C[ra.z];
+          row[ra.y] += kf * w.C[ra.x] * w.C[ra.z];
+          row[ra.z] += kf * w.C[ra.x] * w.C[ra.y];
+        }
+        if (rb.w == 1) {
+          row[rb.x] -= kr;
+        } else if (rb.w == 2) {
+          row[rb.x] -= kr * w.C[rb.y];
+          row[rb.y] -= kr * w.C[rb.x];
+        } else {
+          row[rb.x] -= kr * w.C[rb.y] * w.C[rb.z];
+          row[rb.y] -= kr * w.C[rb.x] * w.C[rb.z];
+          row[rb.z] -= kr * w.C[rb.x] * w.C[rb.y];
+        }
+        if (j >= m.n_elem) {
+          const double a = nu * w.aux[j];
+          acc += a;
+#pragma unroll
+          for (int x = 0; x < kMaxEx; ++x) {
+            const int se = __ldg(m.ex_sp + (size_t)j * kMaxEx + x);
+            if (se >= 0) row[se] += a * __ldg(m.ex_a + (size_t)j * kMaxEx + x);
+          }
+        }
+        dT += nu * w.qT[j];
+      }
+      if (acc != 0.0)
+        for (int c = 0; c < K; ++c) row[c] += acc;
+      dwdT[s] = dT;
+    }
+  }
+  __syncwarp();
+  double hsp = 0.0;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int k = lane + 32 * s;
+    S[s] = 0.0;
+    colH[s] = 0.0;
+    if (k < K) {
+      const double* row = w.J + (size_t)k * ld;
+      double a = 0.0;
+      for (int c = 0; c < K; ++c) a += row[c] * w.C[c];
+      S[s] = a;
+      hsp += sp.hRT[s] * a;
+      double b = 0.0;   // column k: sum_r h_r/RT dwdot_r/dC_k
+      for (int r = 0; r < K; ++r) b += w.hRT[r] * w.J[(size_t)r * ld + k];
+      colH[s] = b;
+    }
+  }
+  const double HS = wsum(hsp) * cs.RT;
+  __syncwarp();
+  const double rho = cs.rho, irho = 1.0 / rho, Wbar = cs.Wbar, cp = cs.cp, Q = cs.Q;
+  const double rc = rho * cp, irc = 1.0 / rc, Qrc2 = Q * irc * irc;
+  double dq = 0.0, dcp = 0.0;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int k = lane + 32 * s;
+    if (k < K) {
+      double* row = w.J + (size_t)k * ld;
+      const double Wk = __ldg(m.W + k), wd = sp.wdot[s];
+      const double ak = Wbar * (wd - S[s]) * irho;
+      for (int c = 0; c < K; ++c) row[c] = Wk * __ldg(m.invW + c) * (row[c] + ak);
+      row[K] = Wk * irho * (dwdT[s] + (wd - S[s]) * cs.invT);
+      // temperature row, column k
+      const double iW = __ldg(m.invW + k);
+      const double dQ = cs.RT * rho * colH[s] - Wbar * HS;   // HS already carries RT
+      w.J[(size_t)K * ld + k] = iW * (-dQ * irc + Qrc2 * rho * (sp.cpR[s] * kR - cp * Wbar));
+      dq += sp.cpR[s] * kR * wd + sp.hRT[s] * cs.RT * (dwdT[s] - S[s] * cs.invT);
+      dcp += y[s] * sp.dcpR[s] * kR * iW;
+    }
+  }
+  dq = wsum(dq);
+  dcp = wsum(dcp);
+  if (lane == 0) w.J[(size_t)K * ld + K] = -dq * irc + Qrc2 * (-rc * cs.invT + rho * dcp);
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------------------------------
+// dense LU of M = I - c J with partial pivoting (ties: lowest row), lane = row
+// ------------------------------------------------------------------------------------------
+template <int NPL>
+__device__ bool lu_factor(const WarpMem& w, int n, double c, int lane) {
+  const int ld = w.ld;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int r = lane + 32 * s;
+    if (r < n) {
+      const double* jr = w.J + (size_t)r * ld;
+      double* lr = w.LU + (size_t)r * ld;
+      for (int cc = 0; cc < n; ++cc) lr[cc] = (r == cc ? 1.0 : 0.0) - c * jr[cc];
+    }
+  }
+  int myperm[NPL];
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) myperm[s] = lane + 32 * s;
+  __syncwarp();
+  bool ok = true;
+  for (int col = 0; col < n; ++col) {
+    double bv = -1.0;
+    int bi = n;
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+      const int r = lane + 32 * s;
+      if (r >= col && r < n) {
+        const double v = fabs(w.LU[(size_t)r * ld + col]);
+        if (v > bv) { bv = v; bi = r; }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(FULLMASK, bv, o);
+      const int oi = __shfl_xor_sync(FULLMASK, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (!(bv > 0.0) || !isfinite(bv)) { ok = false; break; }
+    if (bi != col) {
+      for (int cc = lane; cc < n; cc += 32) {
+        const double t = w.LU[(size_t)col * ld + cc];
+        w.LU[(size_t)col * ld + cc] = w.LU[(size_t)bi * ld + cc];
+        w.LU[(size_t)bi * ld + cc] = t;
+      }
+      // track the permutation: position col <-> bi
+      int pc = 0, pb = 0;
+#pragma unroll
+      for (int s = 0; s < NPL; ++s) {
+        if (lane + 32 * s == col) pc = myperm[s];
+        if (lane + 32 * s == bi) pb = myperm[s];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        pc |= __shfl_xor_sync(FULLMASK, pc, o);
+        pb |= __shfl_xor_sync(FULLMASK, pb, o);
+      }
+#pragma unroll
+      for (int s = 0; s < NPL; ++s) {
+        if (lane + 32 * s == col) myperm[s] = pb;
+        if (lane + 32 * s == bi) myperm[s] = pc;
+      }
+    }
+    __syncwarp();
+    const double inv = 1.0 / w.LU[(size_t)col * ld + col];
+    if (lane == 0) w.invd[col] = inv;
+    const double* pr = w.LU + (size_t)col * ld;
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+      const int r = lane + 32 * s;
+      if (r > col && r < n) {
+        double* lr = w.LU + (size_t)r * ld;
+        const double l = lr[col] * inv;
+        lr[col] = l;
+        for (int cc = col + 1; cc < n; ++cc) lr[cc] -= l * pr[cc];
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int s = 0; s < NPL; ++s)
+    if (lane + 32 * s < n) w.perm[lane + 32 * s] = myperm[s];
+  __syncwarp();
+  return ok;
+}
+
+// x <- M^{-1} x with the factors in w.LU (x distributed: lane = row)
+template <int NPL>
+__device__ void lu_solve(const WarpMem& w, int n, double (&x)[NPL], int lane) {
+  const int ld = w.ld;
+  double b[NPL];
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int r = lane + 32 * s;
+    const int src = r < n ? w.perm[r] : r;
+    double v0 = __shfl_sync(FULLMASK, x[0], src & 31);
+    double v = v0;
+    if (NPL > 1) {
+      const double v1 = __shfl_sync(FULLMASK, x[NPL > 1 ? 1 : 0], src & 31);
+      v = (src >> 5) ? v1 : v0;
+    }
+    b[s] = r < n ? v : 0.0;
+  }
+  for (int col = 0; col < n - 1; ++col) {
+    const double xc = comp_get<NPL>(b, col);
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+      const int r = lane + 32 * s;
+      if (r > col && r < n) b[s] -= w.LU[(size_t)r * ld + col] * xc;
+    }
+  }
+  for (int col = n - 1; col >= 0; --col) {
+    const double xc = comp_get<NPL>(b, col) * w.invd[col];
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+      const int r = lane + 32 * s;
+      if (r == col) b[s] = xc;
+      else if (r < col) b[s] -= w.LU[(size_t)r * ld + col] * xc;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) x[s] = b[s];
+}
+
+// ------------------------------------------------------------------------------------------
+// BDF (Shampine & Reichelt backward-difference form, orders 1..5) with modified Newton
+// ------------------------------------------------------------------------------------------
+constexpr int kMaxOrd = 5;
+constexpr int kNewtonMax = 3;
+constexpr int kJacMaxAge = 20;
+
+__device__ __forceinline__ double bdf_gamma(int k) {
+  // gamma_k = sum_{i=1..k} 1/i
+  switch (k) {
+    case 1: return 1.0;
+    case 2: return 1.5;
+    case 3: return 1.8333333333333333;
+    case 4: return 2.0833333333333333;
+    case 5: return 2.2833333333333333;
+    default: return 2.45;
+  }
+}
+
+// wrms norm of x / scale in FP32 (an error-control heuristic; never feeds the solution)
+template <int NPL>
+__device__ __forceinline__ float wrms(const double (&x)[NPL], const float (&isc)[NPL], int n, int lane) {
+  float a = 0.0f;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    if (lane + 32 * s < n) {
+      float v = fminf(fabsf((float)x[s]) * isc[s], 1e15f);
+      a += v * v;
+    }
+  }
+  return sqrtf(wsumf(a) / (float)n);
+}
+
+// D[0..order] <- (R(f) U)^T D; R(f)_ij = prod_{l=1..i} (l-1-f j)/l, U_ij = (-1)^i C(j, i).
+// Row 0 and column 0 of R U are (1, 0, ...), so D[0] is untouched and only the 5 x 5 block
+// (i, j >= 1) is formed, one entry per lane.
+template <int NPL>
+__device__ void rescale_D(double (&D)[kMaxOrd + 3][NPL], int order, double fct, const WarpMem& w, int lane) {
+  if (lane < 25) {
+    const int i = 1 + lane / 5, j = 1 + lane % 5;
+    double acc = 0.0;
+    if (i <= order && j <= order) {
+      // sum_{l=1..j} R_il (-1)^l C(j, l)
+      double binom = 1.0;
+      for (int l = 1; l <= j; ++l) {
+        binom = binom * (double)(j - l + 1) / (double)l;
+        double r = 1.0;
+        for (int mm = 1; mm <= i; ++mm) r *= ((double)(mm - 1) - fct * (double)l) / (double)mm;
+        acc += ((l & 1) ? -binom : binom) * r;
+      }
+    }
+    w.ru[lane] = acc;
+  }
+  __syncwarp();
+  double Dn[kMaxOrd + 1][NPL];
+#pragma unroll
+  for (int j = 1; j <= kMaxOrd; ++j)
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+      double a = 0.0;
+      if (j <= order) {
+#pragma unroll
+        for (int i = 1; i <= kMaxOrd; ++i)
+          if (i <= order) a += w.ru[(i - 1) * 5 + (j - 1)] * D[i][s];
+      }
+      Dn[j][s] = a;
+    }
+#pragma unroll
+  for (int j = 1; j <= kMaxOrd; ++j)
+#pragma unroll
+    for (int s = 0; s < NPL; ++s)
+      if (j <= order) D[j][s] = Dn[j][s];
+  __syncwarp();
+}
+
+struct DiOpts {
+  double rtol, atol_Y, atol_T;
+  int max_steps;
+};
+
+template <int NPL>
+__device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, double (&z)[NPL],
+                              double dt, const DiOpts& o, int lane, int (&cnt)[4]) {
+  const int n = m.n, K = m.K;
+  cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
+  LaneSp<NPL> sp;
+  CellSc cs;
+  double atol[NPL];
+  float isc[NPL];
+  bool fin = true;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int i = lane + 32 * s;
+    atol[s] = (i == K) ? o.atol_T : o.atol_Y;
+    if (i < n && !isfinite(z[s])) fin = false;
+  }
+  if (__any_sync(FULLMASK, !fin)) return CHEM_CELL_NONFINITE;
+  if (!(dt > 0.0)) return CHEM_CELL_OK;
+  {
+    const double T0 = comp_get<NPL>(z, K);
+    if (!(T0 > 0.0)) return CHEM_CELL_OUT_OF_RANGE;
+  }
+  const double EPS = 2.220446049250313e-16;
+  const float ntol = fmaxf((float)(10.0 * EPS / o.rtol), fminf(0.03f, sqrtf((float)o.rtol)));
+
+  double D[kMaxOrd + 3][NPL];
+  double f[NPL], y[NPL], d[NPL], dy[NPL], psi[NPL];
+  // initial step (Hairer, Norsett & Wanner, Sec. II.4, order 1)
+  rhs_eval<NPL, false>(m, w, pc, z, f, sp, cs, lane);
+  cnt[1]++;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) isc[s] = 1.0f / (float)(atol[s] + o.rtol * fabs(z[s]));
+  const float d0 = wrms<NPL>(z, isc, n, lane), d1 = wrms<NPL>(f, isc, n, lane);
+  double h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6 : 0.01 * (double)d0 / (double)d1;
+  h0 = fmin(h0, dt);
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) y[s] = z[s] + h0 * f[s];
+  rhs_eval<NPL, false>(m, w, pc, y, dy, sp, cs, lane);
+  cnt[1]++;
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) dy[s] -= f[s];
+  const float d2 = (float)((double)wrms<NPL>(dy, isc, n, lane) / h0);
+  const float dm = fmaxf(d1, d2);
+  double h = (dm <= 1e-15f) ? fmax(1e-6, h0 * 1e-3) : (double)sqrtf(0.01f / dm);
+  h = fmin(fmin(100.0 * h0, h), dt);
+  if (!(h > 0.0)) h = 1e-12 * dt;
+
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    D[0][s] = z[s];
+    D[1][s] = h * f[s];
+#pragma unroll
+    for (int j = 2; j < kMaxOrd + 3; ++j) D[j][s] = 0.0;
+  }
+  int order = 1, n_equal = 0, newton_iters = 0, fails = 0;
+  bool need_jac = true, have_lu = false;
+  int jac_age = 0;
+  double c_lu = 0.0;
+  float crate = 0.5f;
+  double t = 0.0;
+  int status = CHEM_CELL_OK;
+
+  while (t < dt) {
+    if (cnt[0] >= o.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
+    const double hmin = 10.0 * EPS * fabs(t) + 1e-300;
+    if (t + h > dt) {
+      const double hn = dt - t;
+      rescale_D<NPL>(D, order, hn / h, w, lane);
+      h = hn;
+      n_equal = 0;
+    }
+    if (h < hmin || fails > 60) { status = CHEM_CELL_STEP_FAIL; break; }
+    double t_new = t + h;
+    if (t_new > dt || dt - t_new < hmin) t_new = dt;
+    // predictor and the history term psi
+    const double ig = 1.0 / bdf_gamma(order);
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+      double yp = D[0][s], ps = 0.0;
+#pragma unroll
+      for (int j = 1; j <= kMaxOrd; ++j)
+        if (j <= order) { yp += D[j][s]; ps += bdf_gamma(j) * D[j][s]; }
+      y[s] = yp;
+      psi[s] = ps * ig;
+      d[s] = 0.0;
+      isc[s] = 1.0f / (float)(atol[s] + o.rtol * fabs(yp));
+    }
+    const double c = h * ig;
+    bool f_at_pred = false;
+    if (need_jac) {
+      rhs_eval<NPL, true>(m, w, pc, y, f, sp, cs, lane);
+      jac_assemble<NPL>(m, w, y, sp, cs, lane);
+      cnt[1]++;
+      cnt[2]++;
+      need_jac = false;
+      jac_age = 0;
+      have_lu = false;
+      f_at_pred = true;   // f(ypred) doubles as the first Newton residual
+    }
+    if (!have_lu || fabs(c / c_lu - 1.0) > 0.3) {
+      if (!lu_factor<NPL>(w, n, c, lane)) {
+        // singular Newton matrix: shrink the step
+        fails++;
+        rescale_D<NPL>(D, order, 0.25, w, lane);
+        h *= 0.25;
+        n_equal = 0;
+        have_lu = false;
+        continue;
+      }
+      cnt[3]++;
+      c_lu = c;
+      have_lu = true;
+      crate = 0.5f;
+    }
+    const double lscale = 2.0 / (1.0 + c / c_lu);
+    bool converged = false;
+    float dn_old = 0.0f;
+    newton_iters = 0;
+    for (int it = 0; it < kNewtonMax; ++it) {
+      if (!(it == 0 && f_at_pred)) {
+        rhs_eval<NPL, false>(m, w, pc, y, f, sp, cs, lane);
+        cnt[1]++;
+      }
+      bool ok = true;
+#pragma unroll
+      for (int s = 0; s < NPL; ++s) {
+        if (!isfinite(f[s])) ok = false;
+        dy[s] = c * f[s] - psi[s] - d[s];
+      }
+      if (__any_sync(FULLMASK, !ok)) break;
+      lu_solve<NPL>(w, n, dy, lane);
+#pragma unroll
+      for (int s = 0; s < NPL; ++s) dy[s] *= lscale;
+      const float dn = wrms<NPL>(dy, isc, n, lane);
+      ++newton_iters;
+      if (it > 0) crate = fmaxf(0.3f * crate, dn / fmaxf(dn_old, 1e-30f));
+#pragma unroll
+      for (int s = 0; s < NPL; ++s) { y[s] += dy[s]; d[s] += dy[s]; }
+      if (dn == 0.0f || (crate < 1.0f && crate / (1.0f - crate) * dn < ntol)) { converged = true; break; }
+      if (it > 0 && dn > 2.0f * dn_old) break;
+      dn_old = dn;
+    }
+    if (!converged) {
+      fails++;
+      if (jac_age > 0) {
+        need_jac = true;       // retry this step with a fresh Jacobian
+      } else {
+        rescale_D<NPL>(D, order, 0.25, w, lane);
+        h *= 0.25;
+        n_equal = 0;
+      }
+      continue;
+    }
+    // local error test
+    const float safety = 0.9f * (2 * kNewtonMax + 1) / (float)(2 * kNewtonMax + newton_iters);
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) isc[s] = 1.0f / (float)(atol[s] + o.rtol * fabs(y[s]));
+    const float en = wrms<NPL>(d, isc, n, lane) / (float)(order + 1);
+    if (!(en <= 1.0f)) {
+      fails++;
+      const float fac = fmaxf(0.2f, safety * exp2f(-log2f(fmaxf(en, 1e-30f)) / (float)(order + 1)));
+      rescale_D<NPL>(D, order, (double)fac, w, lane);
+      h *= (double)fac;
+      n_equal = 0;
+      continue;
+    }
+    // accept: D[order+2] = d - D[order+1]; D[order+1] = d; D[i] += D[i+1]
+    fails = 0;
+    t = t_new;
+    cnt[0]++;
+    n_equal++;
+    jac_age++;
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+#pragma unroll
+      for (int j = 0; j <= kMaxOrd; ++j) {
+        if (j == order) {
+          D[j + 2][s] = d[s] - D[j + 1][s];
+          D[j + 1][s] = d[s];
+        }
+      }
+#pragma unroll
+      for (int j = kMaxOrd; j >= 0; --j)
+        if (j <= order) D[j][s] += D[j + 1][s];
+    }
+    if (jac_age >= kJacMaxAge) need_jac = true;
+    if (n_equal < order + 1) continue;
+    // order and step-size selection
+    double em[NPL], ep[NPL];
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+      em[s] = 0.0;
+      ep[s] = 0.0;
+#pragma unroll
+      for (int j = 0; j <= kMaxOrd + 2; ++j) {
+        if (j == order) em[s] = D[j][s];
+        if (j == order + 2) ep[s] = D[j][s];
+      }
+    }
+    const float nm = order > 1 ? wrms<NPL>(em, isc, n, lane) / (float)order : 0.0f;
+    const float np = order < kMaxOrd ? wrms<NPL>(ep, isc, n, lane) / (float)(order + 2) : 0.0f;
+    const float fm = order > 1 ? (nm == 0.0f ? 1e30f : exp2f(-log2f(nm) / (float)order)) : 0.0f;
+    const float f0 = en == 0.0f ? 1e30f : exp2f(-log2f(en) / (float)(order + 1));
+    const float fp = order < kMaxOrd ? (np == 0.0f ? 1e30f : exp2f(-log2f(np) / (float)(order + 2))) : 0.0f;
+    int delta = 0;
+    float best = f0;
+    if (fm > best) { best = fm; delta = -1; }
+    if (fp > best) { best = fp; delta = 1; }
+    order += delta;
+    const float facf = fminf(10.0f, safety * best);
+    n_equal = 0;
+    // keep h unless the gain is worth a new factorisation (CVODE's threshold of 1.5)
+    if (delta == 0 && facf >= 1.0f && facf < 1.5f) continue;
+    const double fac = (double)facf;
+    rescale_D<NPL>(D, order, fac, w, lane);
+    h *= fac;
+  }
+  if (status == CHEM_CELL_OK) {
+    bool okv = true;
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+      if (lane + 32 * s < n && !isfinite(D[0][s])) okv = false;
+    }
+    if (__any_sync(FULLMASK, !okv)) status = CHEM_CELL_NONFINITE;
+    else {
+#pragma unroll
+      for (int s = 0; s < NPL; ++s) z[s] = D[0][s];
+    }
+  }
+  return status;
+}
+
+// ------------------------------------------------------------------------------------------
+// kernels
+// ------------------------------------------------------------------------------------------
+template <int NPL>
+__device__ __forceinline__ void load_cell(const DevMech& m, int64_t col, int64_t ld, const double* T,
+                                          const double* Y, double (&z)[NPL], int lane) {
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int k = lane + 32 * s;
+    z[s] = 0.0;
+    if (k < m.K) z[s] = Y[(size_t)k * ld + col];
+    else if (k == m.K) z[s] = T[col];
+  }
+}
+
+template <int NPL>
+__global__ void __launch_bounds__(128) di_kernel(DevMech m, int64_t n, int64_t ld, double dt, double* T,
+                                                 const double* p, double* Y, const int32_t* idx, DiOpts o,
+                                                 int32_t* status, int32_t* stats, unsigned int* queue,
+                                                 size_t warp_bytes) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, true, true);
+  while (true) {
+    unsigned int slot = 0;
+    if (lane == 0) slot = atomicAdd(queue, 1u);
+    slot = __shfl_sync(FULLMASK, slot, 0);
+    if ((int64_t)slot >= n) break;
+    const int64_t col = idx ? (int64_t)idx[slot] : (int64_t)slot;
+    double z[NPL];
+    int cnt[4];
+    int st;
+    if (col < 0 || col >= ld) {
+      st = CHEM_CELL_OUT_OF_RANGE;
+      cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
+    } else {
+      load_cell<NPL>(m, col, ld, T, Y, z, lane);
+      st = integrate_cell<NPL>(m, w, p[col], z, dt, o, lane, cnt);
+      if (st == CHEM_CELL_OK) {
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+          const int k = lane + 32 * s;
+          if (k < m.K) Y[(size_t)k * ld + col] = z[s];
+          else if (k == m.K) T[col] = z[s];
+        }
+      }
+    }
+    if (lane == 0) {
+      status[slot] = st;
+      if (stats) {
+        stats[slot] = cnt[0];
+        stats[n + slot] = cnt[1];
+        stats[2 * n + slot] = cnt[2];
+        stats[3 * n + slot] = cnt[3];
+      }
+    }
+  }
+}
+
+template <int NPL>
+__global__ void __launch_bounds__(128) rates_kernel(DevMech m, int64_t n, int64_t ld, const double* T,
+                                                    const double* p, const double* Y, double* wdot,
+                                                    double* hrr, size_t warp_bytes) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, false, false);
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t col = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; col < n; col += nw) {
+    double z[NPL], f[NPL];
+    LaneSp<NPL> sp;
+    CellSc cs;
+    load_cell<NPL>(m, col, ld, T, Y, z, lane);
+    rhs_eval<NPL, false>(m, w, p[col], z, f, sp, cs, lane);
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+      const int k = lane + 32 * s;
+      if (k < m.K) wdot[(size_t)k * ld + col] = sp.wdot[s];
+    }
+    if (hrr && lane == 0) hrr[col] = -cs.Q;
+  }
+}
+
+template <int NPL>
+__global__ void __launch_bounds__(128) jacobian_kernel(DevMech m, int64_t n, int64_t ld, const double* T,
+                                                       const double* p, const double* Y, double* jac,
+                                                       size_t warp_bytes) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, false, true);
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int nn = m.n;
+  for (int64_t col = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; col < n; col += nw) {
+    double z[NPL], f[NPL];
+    LaneSp<NPL> sp;
+    CellSc cs;
+    load_cell<NPL>(m, col, ld, T, Y, z, lane);
+    rhs_eval<NPL, true>(m, w, p[col], z, f, sp, cs, lane);
+    jac_assemble<NPL>(m, w, z, sp, cs, lane);
+    double* out = jac + (size_t)col * nn * nn;
+    for (int e = lane; e < nn * nn; e += 32) out[e] = w.J[(size_t)(e / nn) * w.ld + (e % nn)];
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// launches
+// ------------------------------------------------------------------------------------------
+static int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+static int smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+size_t di_smem_per_warp(const DevMech& m) { return warp_doubles(m.K, m.I, m.n, true, true) * sizeof(double); }
+
+template <typename KernelT>
+static int configure(KernelT kern, size_t warp_bytes, int& warps_per_block, size_t& smem) {
+  const int optin = smem_optin();
+  warps_per_block = 4;
+  while (warps_per_block > 1 && (size_t)warps_per_block * warp_bytes > (size_t)optin) --warps_per_block;
+  smem = (size_t)warps_per_block * warp_bytes;
+  if (smem > (size_t)optin)
+    return set_error(CHEM_E_UNSUPPORTED, "mechanism needs more shared memory per warp than the device has");
+  return cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                    "cudaFuncSetAttribute");
+}
+
+int launch_rates(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                 const double* Y, double* wdot, double* hrr, cudaStream_t s) {
+  const size_t wb = warp_doubles(m.K, m.I, m.n, false, false) * sizeof(double);
+  int wpb;
+  size_t smem;
+  int rc;
+  const int64_t want = (n + 3) / 4;
+  if (m.n <= 32) {
+    if ((rc = configure(rates_kernel<1>, wb, wpb, smem))) return rc;
+    const int grid = (int)std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)sm_count() * 64);
+    rates_kernel<1><<<grid, 32 * wpb, smem, s>>>(m, n, ld, T, p, Y, wdot, hrr, wb);
+  } else {
+    if ((rc = configure(rates_kernel<2>, wb, wpb, smem))) return rc;
+    const int grid = (int)std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)sm_count() * 64);
+    rates_kernel<2><<<grid, 32 * wpb, smem, s>>>(m, n, ld, T, p, Y, wdot, hrr, wb);
+  }
+  (void)want;
+  return cuda_check(cudaGetLastError(), "rates_kernel launch");
+}
+
+int launch_jacobian(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
+                    const double* Y, double* jac, cudaStream_t s) {
+  const size_t wb = warp_doubles(m.K, m.I, m.n, false, true) * sizeof(double);
+  int wpb;
+  size_t smem;
+  int rc;
+  if (m.n <= 32) {
+    if ((rc = configure(jacobian_kernel<1>, wb, wpb, smem))) return rc;
+    const int grid = (int)std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)sm_count() * 32);
+    jacobian_kernel<1><<<grid, 32 * wpb, smem, s>>>(m, n, ld, T, p, Y, jac, wb);
+  } else {
+    if ((rc = configure(jacobian_kernel<2>, wb, wpb, smem))) return rc;
+    const int grid = (int)std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)sm_count() * 32);
+    jacobian_kernel<2><<<grid, 32 * wpb, smem, s>>>(m, n, ld, T, p, Y, jac, wb);
+  }
+  return cuda_check(cudaGetLastError(), "jacobian_kernel launch");
+}
+
+int launch_di(const DevMech& m, int64_t n, int64_t ld, double dt, double* T, const double* p,
+              double* Y, const int32_t* idx, const chem_di_opts& opts, int32_t* status,
+              int32_t* stats, unsigned int* queue, cudaStream_t s) {
+  const size_t wb = di_smem_per_warp(m);
+  DiOpts o{opts.rtol, opts.atol_Y, opts.atol_T, opts.max_steps};
+  int wpb;
+  size_t smem;
+  int rc;
+  if (n > (int64_t)0x7fffffff) return set_error(CHEM_E_ARG, "chem_step_di: too many cells in one call");
+  int dev = 0, per_sm = 0, max_threads_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  if (m.n <= 32) {
+    if ((rc = configure(di_kernel<1>, wb, wpb, smem))) return rc;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, di_kernel<1>, 32 * wpb, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)sm_count() * per_sm);
+    di_kernel<1><<<(int)grid, 32 * wpb, smem, s>>>(m, n, ld, dt, T, p, Y, idx, o, status, stats, queue, wb);
+  } else {
+    if ((rc = configure(di_kernel<2>, wb, wpb, smem))) return rc;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, di_kernel<2>, 32 * wpb, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)sm_count() * per_sm);
+    di_kernel<2><<<(int)grid, 32 * wpb, smem, s>>>(m, n, ld, dt, T, p, Y, idx, o, status, stats, queue, wb);
+  }
+  return cuda_check(cudaGetLastError(), "di_kernel launch");
+}
+
+}  // namespace chem
