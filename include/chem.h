@@ -116,6 +116,26 @@ int chem_step_di(chem_mech mech, int64_t n, int64_t ld, double dt, double* T, co
 /* Device scratch needed by chem_step_di for n cells (bytes). */
 size_t chem_workspace_bytes(chem_mech mech, int64_t n);
 
+/* chem_step_di for callers that cannot allocate device memory (the paper has no
+ * counterpart: this is a library convenience).  Such callers include flow solvers in Fortran
+ * or C that link this ABI directly after giving all free HBM to their own memory pool, and
+ * time-step loops that must avoid cudaMalloc/cudaFree because those calls synchronise the
+ * device.  Same arguments and results as chem_step_di, without the workspace: the scratch
+ * (the cell work-queue counter) lives in a fixed 256-byte device array inside this library,
+ * held by every GPU that loads the library until the process exits.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current.
+ *   - All calls share the one array: the call clears the counter on `stream` before its
+ *     launch, but calls whose work overlaps on the GPU (other streams, other threads) race
+ *     on it and must be serialised by the caller.
+ *   - Returns CHEM_E_ARG if the call needs more scratch than the array holds (more than
+ *     2^31 - 1 cells), otherwise the codes of chem_step_di. */
+int chem_step_di_noalloc(chem_mech mech, int64_t n, int64_t ld, double dt, double* T,
+                         const double* p, double* Y, const int32_t* idx,
+                         const chem_di_opts* opts, int32_t* status, int32_t* stats,
+                         chem_stream stream);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Mixture thermo and transport properties (Sec. 2.1)                                        */
 /* ---------------------------------------------------------------------------------------- */

@@ -51,6 +51,8 @@ def lib(auto_build: bool = False):
         L.chem_jacobian.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
         L.chem_step_di.argtypes = [vp, i64, i64, dbl, vp, vp, vp, vp, C.POINTER(DiOpts), vp, vp,
                                    vp, C.c_size_t, vp]
+        L.chem_step_di_noalloc.argtypes = [vp, i64, i64, dbl, vp, vp, vp, vp, C.POINTER(DiOpts),
+                                           vp, vp, vp]
         L.chem_workspace_bytes.argtypes = [vp, i64]
         L.chem_workspace_bytes.restype = C.c_size_t
         L.thermo_props.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
@@ -146,6 +148,25 @@ def chem_step_di(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0, atol_Y
                               _ptr(idx, torch.int32), C.byref(o), _ptr(status, torch.int32),
                               _ptr(stats, torch.int32), _ptr(workspace),
                               workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def chem_step_di_noalloc(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0, atol_Y=0.0,
+                         atol_T=0.0, max_steps=0, stats=None, n: Optional[int] = None,
+                         stream=None) -> None:
+    """chem_step_di without a workspace, for callers that cannot allocate device memory.
+
+    Its scratch is a fixed device array inside the library shared by every call: calls that
+    overlap on the GPU race on it.
+    """
+    ld = _ld(Y, m)
+    if n is None:
+        n = idx.numel() if idx is not None else ld
+    o = DiOpts(rtol, atol_Y, atol_T, max_steps, 0)
+    _check(lib().chem_step_di_noalloc(m.handle, n, ld, float(dt), _ptr(T, torch.float64),
+                                      _ptr(p, torch.float64), _ptr(Y, torch.float64),
+                                      _ptr(idx, torch.int32), C.byref(o),
+                                      _ptr(status, torch.int32), _ptr(stats, torch.int32),
+                                      _stream(stream)))
 
 
 def thermo_props(m: Mech, T, Y, cp=None, h=None, mu=None, kappa=None, h_in=None, T_out=None,
