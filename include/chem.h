@@ -87,10 +87,12 @@ int chem_jacobian(chem_mech mech, int64_t n, int64_t ld, const double* T, const 
 /* Direct integration (Eq. 2)                                                               */
 /* ---------------------------------------------------------------------------------------- */
 typedef struct {
-  double rtol;      /* relative tolerance (default 1e-9 when <= 0) */
-  double atol_Y;    /* absolute tolerance on mass fractions (default 1e-20 when <= 0) */
-  double atol_T;    /* absolute tolerance on T in K (default 1e-9 when <= 0) */
-  int max_steps;    /* per-cell step budget (default 20000 when <= 0) */
+  double rtol;       /* relative tolerance (default 1e-9 when <= 0) */
+  double atol_Y;     /* absolute tolerance on mass fractions (default 1e-18 when <= 0) */
+  double atol_T;     /* absolute tolerance on T in K (default 1e-9 when <= 0) */
+  double newton_tol; /* Newton stop: estimated remaining correction in units of the local
+                        error test (default 0.1 when <= 0) */
+  int max_steps;     /* per-cell step budget (default 20000 when <= 0) */
   int reserved;
 } chem_di_opts;
 
@@ -151,6 +153,10 @@ int chem_step_di_noalloc(chem_mech mech, int64_t n, int64_t ld, double dt, doubl
 int thermo_props(chem_mech mech, int64_t n, int64_t ld, const double* T, const double* Y,
                  double* cp, double* h, double* mu, double* kappa, const double* h_in,
                  double* T_out, int mixed_precision, chem_stream stream);
+
+/* Testing hook: y[i] = exp(x[i]) by the library's own FP64 exponential (the table-driven
+ * method the kernels use), for comparison with CUDA's exp.  Device pointers, n >= 0. */
+int chem_selftest_exp(chem_mech mech, int64_t n, const double* x, double* y, chem_stream stream);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* chem_last_error(void);

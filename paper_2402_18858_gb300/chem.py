@@ -27,7 +27,7 @@ class ChemError(RuntimeError):
 
 class DiOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol_Y", C.c_double), ("atol_T", C.c_double),
-                ("max_steps", C.c_int), ("reserved", C.c_int)]
+                ("newton_tol", C.c_double), ("max_steps", C.c_int), ("reserved", C.c_int)]
 
 
 def lib(auto_build: bool = False):
@@ -58,6 +58,7 @@ def lib(auto_build: bool = False):
         L.thermo_props.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
         L.chem_last_error.restype = C.c_char_p
         L.chem_fp64_peak_gflops.argtypes = [C.POINTER(dbl), vp]
+        L.chem_selftest_exp.argtypes = [vp, i64, vp, vp, vp]
         _lib = L
         return L
 
@@ -136,13 +137,13 @@ def chem_workspace_bytes(m: Mech, n: int) -> int:
 
 def chem_step_di(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0, atol_Y=0.0, atol_T=0.0,
                  max_steps=0, stats=None, workspace=None, n: Optional[int] = None,
-                 stream=None) -> None:
+                 stream=None, newton_tol=0.0) -> None:
     ld = _ld(Y, m)
     if n is None:
         n = idx.numel() if idx is not None else ld
     if workspace is None:
         raise ValueError("chem_step_di needs a workspace tensor (chem_workspace_bytes)")
-    o = DiOpts(rtol, atol_Y, atol_T, max_steps, 0)
+    o = DiOpts(rtol, atol_Y, atol_T, newton_tol, max_steps, 0)
     _check(lib().chem_step_di(m.handle, n, ld, float(dt), _ptr(T, torch.float64),
                               _ptr(p, torch.float64), _ptr(Y, torch.float64),
                               _ptr(idx, torch.int32), C.byref(o), _ptr(status, torch.int32),
@@ -152,7 +153,7 @@ def chem_step_di(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0, atol_Y
 
 def chem_step_di_noalloc(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0, atol_Y=0.0,
                          atol_T=0.0, max_steps=0, stats=None, n: Optional[int] = None,
-                         stream=None) -> None:
+                         stream=None, newton_tol=0.0) -> None:
     """chem_step_di without a workspace, for callers that cannot allocate device memory.
 
     Its scratch is a fixed device array inside the library shared by every call: calls that
@@ -161,7 +162,7 @@ def chem_step_di_noalloc(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0
     ld = _ld(Y, m)
     if n is None:
         n = idx.numel() if idx is not None else ld
-    o = DiOpts(rtol, atol_Y, atol_T, max_steps, 0)
+    o = DiOpts(rtol, atol_Y, atol_T, newton_tol, max_steps, 0)
     _check(lib().chem_step_di_noalloc(m.handle, n, ld, float(dt), _ptr(T, torch.float64),
                                       _ptr(p, torch.float64), _ptr(Y, torch.float64),
                                       _ptr(idx, torch.int32), C.byref(o),
@@ -183,3 +184,8 @@ def chem_fp64_peak_gflops(stream=None) -> float:
     v = C.c_double()
     _check(lib().chem_fp64_peak_gflops(C.byref(v), _stream(stream)))
     return v.value
+
+
+def chem_selftest_exp(m: Mech, x, y, stream=None) -> None:
+    _check(lib().chem_selftest_exp(m.handle, x.numel(), _ptr(x, torch.float64),
+                                   _ptr(y, torch.float64), _stream(stream)))

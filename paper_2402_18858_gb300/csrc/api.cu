@@ -320,6 +320,8 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
       for (int e = 0; e < E; ++e) acc += (double)hm.comp[(size_t)k * E + e] * Linv[(size_t)e * R + r];
       Pm[(size_t)k * R + r] = acc;
     }
+  std::vector<double> exptab(128);
+  for (int j = 0; j < 128; ++j) exptab[j] = (double)std::exp2((long double)j / 128.0L);
   std::vector<int> refs_pad(refs);
   if (refs_pad.empty()) refs_pad.push_back(0);
 
@@ -355,6 +357,7 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   size_t otroe = add(troe.data(), troe.size() * 8), optr = add(sp_ptr.data(), sp_ptr.size() * 4);
   size_t orxn = add(sp_rxn.data(), sp_rxn.size() * 4), onu = add(sp_nu.data(), sp_nu.size() * 8);
   size_t oref = add(refs_pad.data(), refs_pad.size() * 4), oP = add(Pm.data(), Pm.size() * 8);
+  size_t oexp = add(exptab.data(), exptab.size() * 8);
   std::vector<char> blob(total, 0);
   for (auto& p : pieces) std::memcpy(blob.data() + p.off, p.src, p.bytes);
   void* d = nullptr;
@@ -377,6 +380,7 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   m.troe = (const double*)(b + otroe); m.sp_ptr = (const int*)(b + optr);
   m.sp_rxn = (const int*)(b + orxn); m.sp_nu = (const double*)(b + onu);
   m.n_ref = R; m.ref_sp = (const int*)(b + oref); m.P = (const double*)(b + oP);
+  m.exptab = (const double*)(b + oexp);
   cm->dmem = d;
   cm->K = K; cm->I = I; cm->E = m.E;
   return CHEM_OK;
@@ -462,9 +466,10 @@ int chem_step_di(chem_mech m, int64_t n, int64_t ld, double dt, double* T, const
   chem_di_opts o{};
   if (opts) o = *opts;
   if (!(o.rtol > 0)) o.rtol = 1e-9;
-  if (!(o.atol_Y > 0)) o.atol_Y = 1e-20;
+  if (!(o.atol_Y > 0)) o.atol_Y = 1e-18;
   if (!(o.atol_T > 0)) o.atol_T = 1e-9;
   if (o.max_steps <= 0) o.max_steps = 20000;
+  if (!(o.newton_tol > 0)) o.newton_tol = kDefaultNewtonTol;
   if (!(o.rtol < 1) || !std::isfinite(o.atol_Y) || !std::isfinite(o.atol_T))
     return set_error(CHEM_E_ARG, "chem_step_di: bad tolerances");
   if ((rc = cuda_check(cudaMemsetAsync(workspace, 0, sizeof(unsigned int), (cudaStream_t)stream),
@@ -487,6 +492,14 @@ int thermo_props(chem_mech m, int64_t n, int64_t ld, const double* T, const doub
     return set_error(CHEM_E_ARG, "thermo_props: mixed_precision must be 0 or 1");
   return launch_thermo(m->dev, n, ld, T, Y, cp, h, mu, kappa, h_in, T_out, mixed_precision,
                        (cudaStream_t)stream);
+}
+
+int chem_selftest_exp(chem_mech m, int64_t n, const double* x, double* y, chem_stream stream) {
+  int rc = check_mech(m);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!x || !y))) return set_error(CHEM_E_ARG, "chem_selftest_exp: bad arguments");
+  if (n == 0) return CHEM_OK;
+  return launch_exp_selftest(m->dev, n, x, y, (cudaStream_t)stream);
 }
 
 int chem_fp64_peak_gflops(double* gflops, chem_stream stream) {

@@ -123,16 +123,16 @@ struct CellSc {
 // Troe falloff (Lindemann form with the Troe broadening factor, Gilbert, Luther & Troe 1983)
 // ------------------------------------------------------------------------------------------
 template <bool JAC>
-__device__ __forceinline__ double troe_k(const double* __restrict__ tp, double T, double invT,
-                                         double lnT, double M, double kinf, double dlnkinf,
-                                         double& dkdM, double& dlnk) {
-  const double k0 = exp(tp[0] + tp[1] * lnT - tp[2] * invT);
+__device__ __forceinline__ double troe_k(const double* __restrict__ tp, const double* __restrict__ et,
+                                         double T, double invT, double lnT, double M, double kinf,
+                                         double dlnkinf, double& dkdM, double& dlnk) {
+  const double k0 = exp_t(tp[0] + tp[1] * lnT - tp[2] * invT, et);
   const double a = tp[3], iT3 = tp[4], iT1 = tp[5], T2 = tp[6];
-  const double e3 = exp(-T * iT3), e1 = exp(-T * iT1);
+  const double e3 = exp_t(-T * iT3, et), e1 = exp_t(-T * iT1, et);
   double Fc = (1.0 - a) * e3 + a * e1;
   double dFc = -(1.0 - a) * iT3 * e3 - a * iT1 * e1;
   if (tp[7] != 0.0) {
-    const double e2 = exp(-T2 * invT);
+    const double e2 = exp_t(-T2 * invT, et);
     Fc += e2;
     dFc += T2 * invT * invT * e2;
   }
@@ -145,7 +145,7 @@ __device__ __forceinline__ double troe_k(const double* __restrict__ tp, double T
   const double den = nn - 0.14 * x;
   const double f1 = x / den;
   const double opf = 1.0 + f1 * f1;
-  const double F = exp10(L / opf);
+  const double F = exp_t(2.302585092994046 * (L / opf), et);   // 10^(L/opf)
   const double ipr = 1.0 / (1.0 + Pr);
   const double k = kinf * Pr * ipr * F;
   if (JAC) {
@@ -164,11 +164,12 @@ __device__ __forceinline__ double troe_k(const double* __restrict__ tp, double T
 // right-hand side f(z) of the reactor, z = (Y_1..Y_K, T)  [Eq. 1]
 // ------------------------------------------------------------------------------------------
 template <int NPL, bool JAC>
-__device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, const double (&y)[NPL],
+__device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip, const double (&y)[NPL],
                          double (&f)[NPL], LaneSp<NPL>& sp, CellSc& cs, int lane) {
   const int K = m.K, I = m.I;
   const double T = comp_get<NPL>(y, K);
   const double lnT = log(T), invT = 1.0 / T, RT = kR * T;
+  const double* __restrict__ et = m.exptab;
   double sYW = 0.0;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
@@ -177,7 +178,8 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, const dou
   }
   sYW = wsum(sYW);
   const double Wbar = 1.0 / sYW;
-  const double rho = p * Wbar / RT;
+  const double rho = p * Wbar * invT * (1.0 / kR);
+  const double irho = sYW * RT * ip;        // 1/rho without a division (ip = 1/p)
   double ctot = 0.0, cpp = 0.0;
   const int hi = T >= m.Tmid ? 1 : 0;
 #pragma unroll
@@ -216,7 +218,7 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, const dou
     if (k < K) {
       double gs = w.g[k];
       for (int r = 0; r < R; ++r) gs -= __ldg(m.P + (size_t)k * R + r) * w.g[__ldg(m.ref_sp + r)];
-      const double e = exp(-gs);
+      const double e = exp_t(-gs, et);
       w.eg[k] = e;
       w.ieg[k] = 1.0 / e;
     }
@@ -228,7 +230,7 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, const dou
     const int4 rb = __ldg((const int4*)(m.rsp + 8 * (size_t)j + 4));
     const double2 a01 = __ldg((const double2*)(m.arr + 4 * (size_t)j));
     const double2 a23 = __ldg((const double2*)(m.arr + 4 * (size_t)j + 2));
-    double kf = exp(a01.x + a01.y * lnT - a23.x * invT);
+    double kf = exp_t(a01.x + a01.y * lnT - a23.x * invT, et);
     double dlnkf = 0.0;
     if (JAC) dlnkf = a01.y * invT + a23.x * invT * invT;
     // kr / kf = 1/K_c = exp(sum nu g/RT) (p0/RT)^(-sum nu) = prod_r e_r prod_p (1/e_p) ...
@@ -258,7 +260,7 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, const dou
         Mfac = M;
       } else {
         double dlnk = 0.0;
-        kf = troe_k<JAC>(m.troe + 8 * (size_t)j, T, invT, lnT, M, kf, dlnkf, dkdM, dlnk);
+        kf = troe_k<JAC>(m.troe + 8 * (size_t)j, et, T, invT, lnT, M, kf, dlnkf, dkdM, dlnk);
         dlnkf = dlnk;
       }
     }
@@ -275,7 +277,6 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, const dou
   }
   __syncwarp();
   double Qp = 0.0;
-  const double irho = 1.0 / rho;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
     const int k = lane + 32 * s;
@@ -291,7 +292,7 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, const dou
     }
   }
   const double Q = wsum(Qp) * RT;
-  const double fT = -Q / (rho * cp);
+  const double fT = -Q * irho * (1.0 / cp);
 #pragma unroll
   for (int s = 0; s < NPL; ++s)
     if (lane + 32 * s == K) f[s] = fT;
@@ -604,7 +605,7 @@ __device__ void rescale_D(double (&D)[kMaxOrd + 3][NPL], int order, double fct, 
 }
 
 struct DiOpts {
-  double rtol, atol_Y, atol_T;
+  double rtol, atol_Y, atol_T, newton_tol;
   int max_steps;
 };
 
@@ -631,12 +632,13 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     if (!(T0 > 0.0)) return CHEM_CELL_OUT_OF_RANGE;
   }
   const double EPS = 2.220446049250313e-16;
-  const float ntol = fmaxf((float)(10.0 * EPS / o.rtol), fminf(0.03f, sqrtf((float)o.rtol)));
+  const float ntol = (float)o.newton_tol;
+  const double ip = 1.0 / pc;
 
   double D[kMaxOrd + 3][NPL];
   double f[NPL], y[NPL], d[NPL], dy[NPL], psi[NPL];
   // initial step (Hairer, Norsett & Wanner, Sec. II.4, order 1)
-  rhs_eval<NPL, false>(m, w, pc, z, f, sp, cs, lane);
+  rhs_eval<NPL, false>(m, w, pc, ip, z, f, sp, cs, lane);
   cnt[1]++;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) isc[s] = 1.0f / (float)(atol[s] + o.rtol * fabs(z[s]));
@@ -645,7 +647,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
   h0 = fmin(h0, dt);
 #pragma unroll
   for (int s = 0; s < NPL; ++s) y[s] = z[s] + h0 * f[s];
-  rhs_eval<NPL, false>(m, w, pc, y, dy, sp, cs, lane);
+  rhs_eval<NPL, false>(m, w, pc, ip, y, dy, sp, cs, lane);
   cnt[1]++;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) dy[s] -= f[s];
@@ -698,7 +700,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     const double c = h * ig;
     bool f_at_pred = false;
     if (need_jac) {
-      rhs_eval<NPL, true>(m, w, pc, y, f, sp, cs, lane);
+      rhs_eval<NPL, true>(m, w, pc, ip, y, f, sp, cs, lane);
       jac_assemble<NPL>(m, w, y, sp, cs, lane);
       cnt[1]++;
       cnt[2]++;
@@ -728,7 +730,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     newton_iters = 0;
     for (int it = 0; it < kNewtonMax; ++it) {
       if (!(it == 0 && f_at_pred)) {
-        rhs_eval<NPL, false>(m, w, pc, y, f, sp, cs, lane);
+        rhs_eval<NPL, false>(m, w, pc, ip, y, f, sp, cs, lane);
         cnt[1]++;
       }
       bool ok = true;
@@ -912,7 +914,8 @@ __global__ void __launch_bounds__(128) rates_kernel(DevMech m, int64_t n, int64_
     LaneSp<NPL> sp;
     CellSc cs;
     load_cell<NPL>(m, col, ld, T, Y, z, lane);
-    rhs_eval<NPL, false>(m, w, p[col], z, f, sp, cs, lane);
+    const double pc = p[col];
+    rhs_eval<NPL, false>(m, w, pc, 1.0 / pc, z, f, sp, cs, lane);
 #pragma unroll
     for (int s = 0; s < NPL; ++s) {
       const int k = lane + 32 * s;
@@ -936,7 +939,8 @@ __global__ void __launch_bounds__(128) jacobian_kernel(DevMech m, int64_t n, int
     LaneSp<NPL> sp;
     CellSc cs;
     load_cell<NPL>(m, col, ld, T, Y, z, lane);
-    rhs_eval<NPL, true>(m, w, p[col], z, f, sp, cs, lane);
+    const double pc = p[col];
+    rhs_eval<NPL, true>(m, w, pc, 1.0 / pc, z, f, sp, cs, lane);
     jac_assemble<NPL>(m, w, z, sp, cs, lane);
     double* out = jac + (size_t)col * nn * nn;
     for (int e = lane; e < nn * nn; e += 32) out[e] = w.J[(size_t)(e / nn) * w.ld + (e % nn)];
@@ -944,9 +948,20 @@ __global__ void __launch_bounds__(128) jacobian_kernel(DevMech m, int64_t n, int
   }
 }
 
+__global__ void exp_selftest_kernel(const double* __restrict__ tab, int64_t n, const double* x, double* y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = exp_t(x[i], tab);
+}
+
 // ------------------------------------------------------------------------------------------
 // launches
 // ------------------------------------------------------------------------------------------
+int launch_exp_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  exp_selftest_kernel<<<(int)blocks, 256, 0, s>>>(m.exptab, n, x, y);
+  return cuda_check(cudaGetLastError(), "exp_selftest_kernel launch");
+}
+
 static int sm_count() {
   static int cached = 0;
   if (!cached) {
@@ -1021,7 +1036,7 @@ int launch_di(const DevMech& m, int64_t n, int64_t ld, double dt, double* T, con
               double* Y, const int32_t* idx, const chem_di_opts& opts, int32_t* status,
               int32_t* stats, unsigned int* queue, cudaStream_t s) {
   const size_t wb = di_smem_per_warp(m);
-  DiOpts o{opts.rtol, opts.atol_Y, opts.atol_T, opts.max_steps};
+  DiOpts o{opts.rtol, opts.atol_Y, opts.atol_T, opts.newton_tol, opts.max_steps};
   int wpb;
   size_t smem;
   int rc;

@@ -232,3 +232,24 @@ def test_di_subset_index_and_batch_invariance(lc, gmech, mechs):
 def test_fp64_probe(lc):
     g = lc.chem_fp64_peak_gflops()
     assert 100.0 < g < 100000.0
+
+
+def test_table_exp_against_cuda_exp(lc, gmech):
+    """The kernels' table-driven FP64 exp stays within 2 ulp of CUDA's exp."""
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.uniform(-708, 709.7, 200000), rng.uniform(-1, 1, 100000),
+                        rng.uniform(-50, 50, 100000), [0.0, -0.0, 1e-300, -1e-300, 709.7, -708.0]])
+    xd = _dev(x)
+    y = torch.empty_like(xd)
+    lc.chem_selftest_exp(gmech["h2_9"], xd, y)
+    ref = torch.exp(xd)
+    torch.cuda.synchronize()
+    yy, rr = y.cpu().numpy(), ref.cpu().numpy()
+    ulp = np.abs(yy - rr) / np.spacing(np.abs(rr))
+    assert ulp.max() <= 2.0, (ulp.max(), x[np.argmax(ulp)])
+    spec = _dev(np.array([np.nan, np.inf, -np.inf, -800.0, 800.0]))
+    ys = torch.empty_like(spec)
+    lc.chem_selftest_exp(gmech["h2_9"], spec, ys)
+    torch.cuda.synchronize()
+    v = ys.cpu().numpy()
+    assert np.isnan(v[0]) and v[1] == np.inf and v[2] == 0.0 and v[3] == 0.0 and v[4] == np.inf
