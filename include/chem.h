@@ -158,6 +158,14 @@ int thermo_props(chem_mech mech, int64_t n, int64_t ld, const double* T, const d
  * method the kernels use), for comparison with CUDA's exp.  Device pointers, n >= 0. */
 int chem_selftest_exp(chem_mech mech, int64_t n, const double* x, double* y, chem_stream stream);
 
+/* Testing hook: one tensor-core GEMM of the MLP, out = epi(A B^T) with A [M, K] and B [N, K]
+ * BF16 row-major (K a multiple of 8, 16-byte aligned), FP32 accumulation.  epi 0: GELU(acc +
+ * bias) -> BF16; 1: acc + bias -> FP32; 2: acc * GELU'(z) -> BF16 with z [M, N] BF16;
+ * 3: acc -> FP32.  out is [M, N].  *err (device int, zeroed by the caller) receives a
+ * non-zero site code if a pipeline wait timed out.  Device pointers. */
+int chem_selftest_gemm(int epi, int M, int N, int K, const void* A, const void* B, const float* bias,
+                       const void* z, void* out, int* err, chem_stream stream);
+
 /* Thread-local description of the last error returned on this thread. */
 const char* chem_last_error(void);
 

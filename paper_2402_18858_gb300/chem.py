@@ -59,6 +59,7 @@ def lib(auto_build: bool = False):
         L.chem_last_error.restype = C.c_char_p
         L.chem_fp64_peak_gflops.argtypes = [C.POINTER(dbl), vp]
         L.chem_selftest_exp.argtypes = [vp, i64, vp, vp, vp]
+        L.chem_selftest_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
         _lib = L
         return L
 
@@ -189,3 +190,15 @@ def chem_fp64_peak_gflops(stream=None) -> float:
 def chem_selftest_exp(m: Mech, x, y, stream=None) -> None:
     _check(lib().chem_selftest_exp(m.handle, x.numel(), _ptr(x, torch.float64),
                                    _ptr(y, torch.float64), _stream(stream)))
+
+
+def chem_selftest_gemm(epi: int, A, B, out, bias=None, z=None, err=None, stream=None) -> None:
+    """out = epilogue(A @ B^T) on the tensor cores (A [M,K], B [N,K] BF16; see include/chem.h)."""
+    M, K = A.shape
+    N = B.shape[0]
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib().chem_selftest_gemm(int(epi), M, N, K, _ptr(A, torch.bfloat16), _ptr(B, torch.bfloat16),
+                                    _ptr(bias, torch.float32), _ptr(z, torch.bfloat16), _ptr(out),
+                                    _ptr(err, torch.int32), _stream(stream)))
+    return err

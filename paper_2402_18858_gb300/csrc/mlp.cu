@@ -1,0 +1,280 @@
+// BF16 tensor-core GEMMs for the MLP of the learned reaction step (Sec. 2.2: hidden layers of
+// 1600, 800 and 400 GELU units; the paper runs it in half precision through libTorch,
+// Sec. 2.1).  Here every layer is a hand-written tcgen05 GEMM fed by TMA with the layer's
+// elementwise work fused into the TMEM epilogue.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "gemm_tc.cuh"
+#include "internal.h"
+
+namespace chem {
+
+using bf16 = __nv_bfloat16;
+
+// ------------------------------------------------------------------------------------------
+// GELU (exact erf form, Hendrycks & Gimpel 2016) and its derivative
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float dgelu_f(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
+
+// ------------------------------------------------------------------------------------------
+// GEMM kernel
+// ------------------------------------------------------------------------------------------
+struct GemmEpi {
+  const float* bias;   // [N] or null
+  void* out;           // [M, ldo] BF16 or FP32
+  int ldo;
+  const bf16* z;       // EPI_DGELU: pre-activations [M, ldz]
+  int ldz;
+  bf16* zout;          // EPI_GELU: optional copy of the pre-activations [M, ldo]
+};
+
+template <int BN>
+struct TileCfg {
+  static constexpr int STAGES = BN >= 256 ? 4 : 6;
+  static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  static constexpr size_t A_BYTES = (size_t)tc::BM * tc::BK * 2;
+  static constexpr size_t B_BYTES = (size_t)BN * tc::BK * 2;
+  static constexpr size_t SMEM = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 2) * 8 + 16;
+};
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
+                                                           const __grid_constant__ CUtensorMap tb,
+                                                           GemmEpi e, int M, int N, int K, int* err) {
+  using C = TileCfg<BN>;
+  constexpr int S = C::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + S * C::A_BYTES;
+  uint64_t* full = (uint64_t*)(sB + S * C::B_BYTES);
+  uint64_t* empty = full + S;
+  uint64_t* done = empty + S;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * tc::BM, n0 = blockIdx.y * BN;
+  const int nkb = (K + tc::BK - 1) / tc::BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 2) tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % S;
+      if (kb >= S && !tc::mbar_wait(&empty[s], ((kb / S) & 1) ^ 1, err, 1)) break;
+      tc::mbar_expect_tx(&full[s], (uint32_t)(C::A_BYTES + C::B_BYTES));
+      tc::tma_load_2d(sA + s * C::A_BYTES, &ta, &full[s], kb * tc::BK, m0);
+      tc::tma_load_2d(sB + s * C::B_BYTES, &tb, &full[s], kb * tc::BK, n0);
+    }
+  } else if (threadIdx.x == 32) {
+    // single-thread MMA issue
+    constexpr uint32_t idesc = tc::idesc_bf16_f32<tc::BM, BN>();
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % S;
+      if (!tc::mbar_wait(&full[s], (kb / S) & 1, err, 2)) break;
+      tc::tc_fence_after();
+      const uint64_t da = tc::sw128_desc(sA + s * C::A_BYTES);
+      const uint64_t db = tc::sw128_desc(sB + s * C::B_BYTES);
+#pragma unroll
+      for (int k = 0; k < tc::BK / tc::UMMA_K; ++k)
+        tc::mma_bf16(tmem, da + (uint64_t)((k * tc::UMMA_K * 2) >> 4), db + (uint64_t)((k * tc::UMMA_K * 2) >> 4),
+                     idesc, (kb > 0 || k > 0) ? 1u : 0u);
+      tc::mma_commit(&empty[s]);
+    }
+    tc::mma_commit(done);
+  }
+  __syncwarp();
+  const bool ok = tc::mbar_wait(done, 0, err, 3);
+  tc::tc_fence_after();
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      if (n0 + c0 >= N) break;
+      float v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (row < M) {   // no early exit: the next tcgen05.ld needs the whole warp
+      const int col0 = n0 + c0;
+      const int nv = min(32, N - col0);
+      if (EPI == 0 || EPI == 1) {   // + bias
+        if (e.bias) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] += (i < nv) ? __ldg(e.bias + col0 + i) : 0.0f;
+        }
+      }
+      if (EPI == 0) {
+        // hidden layer forward: out = bf16(GELU(acc + b)); optional pre-activation copy
+        bf16* o = (bf16*)e.out + (size_t)row * e.ldo + col0;
+        bf16* zo = e.zout ? e.zout + (size_t)row * e.ldo + col0 : nullptr;
+        if (nv == 32) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            __align__(16) bf16 t[8], u[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              t[i] = __float2bfloat16_rn(gelu_f(v[8 * q + i]));
+              u[i] = __float2bfloat16_rn(v[8 * q + i]);
+            }
+            *(uint4*)(o + 8 * q) = *(const uint4*)t;
+            if (zo) *(uint4*)(zo + 8 * q) = *(const uint4*)u;
+          }
+        } else {
+          for (int i = 0; i < nv; ++i) {
+            o[i] = __float2bfloat16_rn(gelu_f(v[i]));
+            if (zo) zo[i] = __float2bfloat16_rn(v[i]);
+          }
+        }
+      } else if (EPI == 1 || EPI == 3) {
+        // output layer (acc + b) or weight gradient (acc), FP32
+        float* o = (float*)e.out + (size_t)row * e.ldo + col0;
+        if (nv == 32) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) *(float4*)(o + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+          for (int i = 0; i < nv; ++i) o[i] = v[i];
+        }
+      } else if (EPI == 2) {
+        // hidden-layer backward: dZ = acc * GELU'(z)
+        const bf16* zz = e.z + (size_t)row * e.ldz + col0;
+        bf16* o = (bf16*)e.out + (size_t)row * e.ldo + col0;
+        if (nv == 32) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            __align__(16) bf16 zin[8], t[8];
+            *(uint4*)zin = __ldg((const uint4*)(zz + 8 * q));
+#pragma unroll
+            for (int i = 0; i < 8; ++i) t[i] = __float2bfloat16_rn(v[8 * q + i] * dgelu_f(__bfloat162float(zin[i])));
+            *(uint4*)(o + 8 * q) = *(const uint4*)t;
+          }
+        } else {
+          for (int i = 0; i < nv; ++i) o[i] = __float2bfloat16_rn(v[i] * dgelu_f(__bfloat162float(zz[i])));
+        }
+      }
+      }
+      __syncwarp();
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 2) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------------------------------
+// host: tensor maps and launch
+// ------------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+// 2-D BF16 row-major [rows, cols] with row stride ld (elements); box = 64 columns x box_rows
+static int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return set_error(CHEM_E_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  if (((uintptr_t)base & 15) || ((ld * 2) & 15))
+    return set_error(CHEM_E_ARG, "GEMM operand must be 16-byte aligned with a row stride that is a multiple of 8 elements");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(CHEM_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return CHEM_OK;
+}
+
+template <int BN, int EPI>
+static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int M, int N, int K,
+                         const GemmEpi& e, int* err, cudaStream_t s) {
+  CUtensorMap ta, tb;
+  int rc;
+  if ((rc = make_map(&ta, A, M, K, lda, tc::BM))) return rc;
+  if ((rc = make_map(&tb, B, N, K, ldb, BN))) return rc;
+  constexpr size_t smem = TileCfg<BN>::SMEM;
+  static bool configured = false;
+  if (!configured) {
+    if ((rc = cuda_check(cudaFuncSetAttribute(gemm_bf16_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem), "gemm smem attribute")))
+      return rc;
+    configured = true;
+  }
+  dim3 grid((unsigned)((M + tc::BM - 1) / tc::BM), (unsigned)((N + BN - 1) / BN));
+  gemm_bf16_kernel<BN, EPI><<<grid, 128, smem, s>>>(ta, tb, e, M, N, K, err);
+  return cuda_check(cudaGetLastError(), "gemm_bf16_kernel launch");
+}
+
+// C = A B^T with the epilogue `epi` (0: bias+GELU -> BF16 [+ pre-activation copy],
+// 1: bias -> FP32, 2: * GELU'(z) -> BF16, 3: FP32).  BN is chosen from N.
+int gemm_bf16(int epi, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int M, int N, int K,
+              const GemmEpi& e, int* err, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return CHEM_OK;
+  const int bn = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+#define CHEM_GEMM_CASE(BNV)                                                                    \
+  if (bn == BNV) {                                                                             \
+    switch (epi) {                                                                             \
+      case 0: return launch_gemm_t<BNV, 0>(A, lda, B, ldb, M, N, K, e, err, s);                \
+      case 1: return launch_gemm_t<BNV, 1>(A, lda, B, ldb, M, N, K, e, err, s);                \
+      case 2: return launch_gemm_t<BNV, 2>(A, lda, B, ldb, M, N, K, e, err, s);                \
+      default: return launch_gemm_t<BNV, 3>(A, lda, B, ldb, M, N, K, e, err, s);               \
+    }                                                                                          \
+  }
+  CHEM_GEMM_CASE(32)
+  CHEM_GEMM_CASE(64)
+  CHEM_GEMM_CASE(128)
+  CHEM_GEMM_CASE(256)
+#undef CHEM_GEMM_CASE
+  return set_error(CHEM_E_ARG, "gemm: unsupported tile");
+}
+
+}  // namespace chem
+
+using namespace chem;
+
+extern "C" int chem_selftest_gemm(int epi, int M, int N, int K, const void* A, const void* B, const float* bias,
+                                  const void* z, void* out, int* err, chem_stream stream) {
+  if (M < 0 || N < 0 || K < 0 || !A || !B || !out || !err) return set_error(CHEM_E_ARG, "chem_selftest_gemm: bad arguments");
+  if (epi < 0 || epi > 3 || (epi == 2 && !z)) return set_error(CHEM_E_ARG, "chem_selftest_gemm: bad epilogue");
+  GemmEpi e{};
+  e.bias = bias;
+  e.out = out;
+  e.ldo = N;
+  e.z = (const bf16*)z;
+  e.ldz = N;
+  e.zout = nullptr;
+  return gemm_bf16(epi, (const bf16*)A, K, (const bf16*)B, K, M, N, K, e, err, (cudaStream_t)stream);
+}
