@@ -1,0 +1,134 @@
+"""FP64 oracle of the learned reaction step (Sec. 2.2) -- test infrastructure only.
+
+* Box-Cox transform (Eq. 7; the printed equation is garbled, the stated range [0, 1] ->
+  [-1/lambda, 0] fixes it as F(x) = (x^lambda - 1)/lambda), lambda = 0.1, and its inverse.
+* MLP with GELU hidden layers (exact erf form, Hendrycks & Gimpel 2016) and a linear output,
+  weights W_l [out, in], biases b_l; forward and a hand-written backward pass.
+* Loss of Eq. 11 with L_data (Eq. 8, mean squared error in the normalised output space) and
+  L_mass (Eq. 9, mean over samples of |sum_k Y*_k - 1|); the HRR term (Eq. 10) has weight 0.
+* Adam (Kingma & Ba 2015).
+* Optional emulation of BF16 storage (round to nearest even) of inputs, weights and hidden
+  activations, so that the GPU's BF16 tensor-core forward can be compared element by element.
+
+Parity status: forward, backward, loss gradient and Adam are pinned by the tests in
+tests/test_oracle_mlp.py (finite differences, closed forms, special values).  The loss
+weights W1, W2, W3 of Eq. 11 are unstated in the paper: W1 = 1, W2 = 0.1, W3 = 0 here.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Tuple
+
+import numpy as np
+from scipy.special import erf
+
+LAMBDA = 0.1
+
+
+def bct(x, lam: float = LAMBDA):
+    """Box-Cox transform of mass fractions (x clipped at 0)."""
+    x = np.maximum(np.asarray(x, dtype=np.float64), 0.0)
+    return (np.power(x, lam) - 1.0) / lam
+
+
+def ibct(z, lam: float = LAMBDA):
+    """Inverse Box-Cox: (lam z + 1)^(1/lam), 0 where lam z + 1 <= 0."""
+    t = np.maximum(lam * np.asarray(z, dtype=np.float64) + 1.0, 0.0)
+    return np.power(t, 1.0 / lam)
+
+
+def gelu(x):
+    return 0.5 * x * (1.0 + erf(x / math.sqrt(2.0)))
+
+
+def dgelu(x):
+    return 0.5 * (1.0 + erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+
+
+def round_bf16(x):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = ((u + 0x7FFF + lsb) >> 16) << 16
+    out = u.astype(np.uint32).view(np.float32).astype(np.float64)
+    return np.where(np.isfinite(f), out, f.astype(np.float64))
+
+
+Params = List[Tuple[np.ndarray, np.ndarray]]
+
+
+def unflatten(flat: np.ndarray, dims: List[int]) -> Params:
+    """Flat [W_0, b_0, W_1, b_1, ...] (W_l of shape [dims[l+1], dims[l]]) -> list of (W, b)."""
+    out, o = [], 0
+    for l in range(len(dims) - 1):
+        nw = dims[l + 1] * dims[l]
+        W = flat[o:o + nw].reshape(dims[l + 1], dims[l]).astype(np.float64)
+        o += nw
+        b = flat[o:o + dims[l + 1]].astype(np.float64)
+        o += dims[l + 1]
+        out.append((W, b))
+    return out
+
+
+def flatten(params: Params) -> np.ndarray:
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params])
+
+
+def forward(params: Params, X: np.ndarray, bf16: bool = False):
+    """U = MLP(X); returns (U, cache).  bf16=True rounds W, inputs and hidden activations."""
+    A = round_bf16(X) if bf16 else np.asarray(X, dtype=np.float64)
+    cache = [A]
+    zs = []
+    for l, (W, b) in enumerate(params):
+        Wl = round_bf16(W) if bf16 else W
+        Z = A @ Wl.T + b
+        if l < len(params) - 1:
+            zs.append(Z)
+            A = gelu(Z)
+            if bf16:
+                A = round_bf16(A)
+            cache.append(A)
+        else:
+            return Z, (cache, zs)
+    raise AssertionError("empty network")
+
+
+def backward(params: Params, cache, dU: np.ndarray) -> Params:
+    """Gradients of a scalar loss with dL/dU = dU."""
+    acts, zs = cache
+    grads = [None] * len(params)
+    d = dU
+    for l in range(len(params) - 1, -1, -1):
+        W, _ = params[l]
+        grads[l] = (d.T @ acts[l], d.sum(axis=0))
+        if l > 0:
+            d = (d @ W) * dgelu(zs[l - 1])
+    return grads
+
+
+def loss_and_grad(U, Ut, K, bcty=None, out_mean=None, out_std=None, w_data=1.0, w_mass=0.1):
+    """Eq. 11 with W3 = 0 over the first K output columns; returns (L, L_data, L_mass, dU)."""
+    U = np.asarray(U, dtype=np.float64)
+    B = U.shape[0]
+    d = U[:, :K] - Ut[:, :K]
+    L_data = float((d * d).mean())
+    dU = np.zeros_like(U)
+    dU[:, :K] = w_data * 2.0 * d / (B * K)
+    L_mass = 0.0
+    if bcty is not None and w_mass != 0.0:
+        Ys = ibct(bcty + U[:, :K] * out_std[None, :] + out_mean[None, :])
+        s = Ys.sum(axis=1)
+        L_mass = float(np.abs(s - 1.0).mean())
+        dYs = np.power(np.maximum(Ys, 0.0), 1.0 - LAMBDA) * out_std[None, :]
+        dU[:, :K] += w_mass / B * np.sign(s - 1.0)[:, None] * dYs
+    return w_data * L_data + w_mass * L_mass, L_data, L_mass, dU
+
+
+def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (step number t >= 1); returns (p, m, v)."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -1,0 +1,75 @@
+"""Pins of the FP64 MLP oracle (Sec. 2.2) against facts other than itself."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+
+def test_box_cox_range_and_inverse():
+    # Sec. 2.2: [0, 1] maps to [-1/lambda, 0] with lambda = 0.1
+    assert mlp.bct(1.0) == 0.0
+    assert mlp.bct(0.0) == pytest.approx(-10.0)
+    x = np.logspace(-30, 0, 200)
+    assert np.allclose(mlp.ibct(mlp.bct(x)), x, rtol=1e-10, atol=0)
+    # lambda -> 0 limit is the logarithm (the second branch of Eq. 7)
+    assert mlp.bct(0.37, lam=1e-9) == pytest.approx(math.log(0.37), rel=1e-7)
+
+
+def test_gelu_special_values_and_derivative():
+    assert mlp.gelu(0.0) == 0.0
+    assert mlp.gelu(10.0) == pytest.approx(10.0, rel=1e-15)
+    assert abs(mlp.gelu(-10.0)) < 1e-20
+    # GELU(x) = x Phi(x): at x = 1, Phi(1) = 0.841344746068543 (standard normal table)
+    assert mlp.gelu(1.0) == pytest.approx(0.841344746068543, rel=1e-12)
+    x = np.linspace(-6, 6, 101)
+    h = 1e-6
+    assert np.allclose(mlp.dgelu(x), (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h), rtol=1e-7, atol=1e-9)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(10000) * 10 ** rng.uniform(-6, 6, 10000),
+                        [1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -2.5, 0.0]])
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.round_bf16(x), ref)
+
+
+def _tiny(rng, dims):
+    return [(rng.standard_normal((dims[l + 1], dims[l])) / math.sqrt(dims[l]),
+             rng.standard_normal(dims[l + 1]) * 0.1) for l in range(len(dims) - 1)]
+
+
+def test_backward_against_finite_differences():
+    rng = np.random.default_rng(1)
+    dims = [6, 7, 5, 4]
+    params = _tiny(rng, dims)
+    X = rng.standard_normal((9, 6))
+    Ut = rng.standard_normal((9, 4))
+    bcty = mlp.bct(rng.uniform(1e-6, 0.3, (9, 4)))
+    om, osd = rng.standard_normal(4) * 0.1, rng.uniform(0.5, 2.0, 4)
+
+    def L(flat):
+        p = mlp.unflatten(flat, dims)
+        U, _ = mlp.forward(p, X)
+        return mlp.loss_and_grad(U, Ut, 4, bcty, om, osd, 1.0, 0.1)[0]
+
+    U, cache = mlp.forward(params, X)
+    _, _, _, dU = mlp.loss_and_grad(U, Ut, 4, bcty, om, osd, 1.0, 0.1)
+    g = mlp.flatten(mlp.backward(params, cache, dU))
+    flat = mlp.flatten(params)
+    fd = np.zeros_like(flat)
+    for i in range(flat.size):
+        e = np.zeros_like(flat)
+        e[i] = 1e-6
+        fd[i] = (L(flat + e) - L(flat - e)) / 2e-6
+    assert np.allclose(g, fd, rtol=1e-5, atol=1e-9)
+
+
+def test_adam_first_step_closed_form():
+    # with zero moments, the bias-corrected first step is -lr g / (|g| + eps)
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    p, m, v = mlp.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    assert np.allclose(p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
