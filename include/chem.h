@@ -139,6 +139,79 @@ int chem_step_di_noalloc(chem_mech mech, int64_t n, int64_t ld, double dt, doubl
                          chem_stream stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Learned reaction step (Sec. 2.2: MLP with GELU hidden layers, Box-Cox inputs, Eq. 7,     */
+/* lambda = 0.1; loss Eqs. 8-9; Adam) in BF16 on the tensor cores, with DI fallback         */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct chem_ann_s* chem_ann;
+
+/* Inputs x = [T, p, F(Y_1..Y_K)] (F = Box-Cox), z-scored with the training statistics and
+ * stored BF16 [n, 64] (zero padded).  Outputs u_k = (F(Y_k(t+dt)) - F(Y_k(t)) - mu_k)/sigma_k,
+ * FP32 [n, n_out_pad] with n_out_pad = 32 (K <= 32) or 64.  Normalisation block (floats):
+ * in_mean[n_in], in_std[n_in], in_min[n_in], in_max[n_in], out_mean[K], out_std[K],
+ * n_in = K + 2. */
+int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t seed, chem_ann* out);
+void chem_ann_free(chem_ann ann);
+int chem_ann_info(chem_ann ann, int* n_in, int* n_out, int* n_layers, int* dims /* [n_layers+1] */,
+                  int64_t* n_params);
+int chem_ann_set_norm(chem_ann ann, const float* host_norm);
+int chem_ann_get_norm(chem_ann ann, float* host_norm);
+/* Fit the normalisation (mean, std, min, max of inputs; mean, std of F-increments) on the
+ * training states (T, p, Y0) and their DI results Y1 (device, SoA, ld-strided). */
+int chem_ann_fit_norm(chem_ann ann, int64_t n, int64_t ld, const double* T, const double* p,
+                      const double* Y0, const double* Y1, chem_stream stream);
+/* Normalised BF16 features X [n, 64]; if bcty is not NULL also the raw F(Y) as FP32 [n, K]
+ * (needed by the mass term of the loss). */
+int chem_ann_features(chem_ann ann, int64_t n, int64_t ld, const double* T, const double* p,
+                      const double* Y, void* X, float* bcty, chem_stream stream);
+/* Normalised FP32 targets U [n, n_out_pad] from the states before (Y0) and after (Y1) DI. */
+int chem_ann_targets(chem_ann ann, int64_t n, int64_t ld, const double* Y0, const double* Y1,
+                     float* U, chem_stream stream);
+/* Raw network output U [n, n_out_pad] for features X [n, 64] (workspace as chem_step_ann). */
+int chem_ann_forward(chem_ann ann, const void* X, int64_t n, float* U, void* workspace,
+                     size_t ws_bytes, chem_stream stream);
+
+typedef struct {
+  float lr, beta1, beta2, eps;   /* Adam */
+  float w_data, w_mass;          /* Eq. 11 weights of L_data (Eq. 8) and L_mass (Eq. 9) */
+  int apply;                     /* 0: gradients only (chem_ann_get_params(which = 1)) */
+  int reserved;
+} chem_train_opts;
+
+/* One optimisation step on a minibatch: X [B, 64] BF16, targets Ut [B, n_out_pad] FP32,
+ * bcty [B, K] FP32 raw F(Y) (NULL unless w_mass != 0), B a multiple of 8.  loss_out (device,
+ * nullable) receives {L_tot, L_data, L_mass}.  The library keeps its training buffers. */
+int chem_ann_train_step(chem_ann ann, const void* X, const float* Ut, const float* bcty, int64_t B,
+                        const chem_train_opts* opts, float* loss_out, chem_stream stream);
+/* Flat FP32 parameters (which = 0) or last gradients (which = 1), per layer W [out, in] then b. */
+int chem_ann_get_params(chem_ann ann, int which, float* host, int64_t count);
+int chem_ann_set_params(chem_ann ann, const float* host, int64_t count);
+/* Checkpoint (weights, Adam moments, step, normalisation) and its reload. */
+int chem_ann_save(chem_ann ann, const char* path);
+int chem_ann_load(chem_mech mech, const char* path, chem_ann* out);
+/* Device error flag of the tensor-core pipelines (non-zero: a wait timed out); reading clears it. */
+int chem_ann_error(chem_ann ann, int* host_err);
+
+typedef struct {
+  double range_margin;  /* inputs outside [min - m (max-min), max + m (max-min)] fall back (0.05) */
+  double elem_tol;      /* max relative element-moles change accepted (1e-3) */
+  double T_min, T_max;  /* accepted new temperature range (250, 3500 K) */
+  double dT_max;        /* if > 0, |T_new - T| above it falls back */
+  int no_fallback;      /* 1: flagged cells keep their input state (status 5), no DI */
+  int reserved;
+  chem_di_opts di;      /* options of the fallback direct integration */
+} chem_ann_opts;
+
+/* Learned chemistry step for n cells in place (layout as chem_step_di): features, the MLP
+ * on the tensor cores, the new state (inverse Box-Cox, renormalisation, T from enthalpy
+ * conservation by Newton's method) and its checks; flagged cells are integrated by DI
+ * (status CHEM_CELL_ANN_FALLBACK when DI succeeded, else DI's code).  Workspace:
+ * chem_ann_workspace_bytes(ann, n). */
+int chem_step_ann(chem_mech mech, chem_ann ann, int64_t n, int64_t ld, double dt, double* T,
+                  const double* p, double* Y, const chem_ann_opts* opts, int32_t* status,
+                  void* workspace, size_t ws_bytes, chem_stream stream);
+size_t chem_ann_workspace_bytes(chem_ann ann, int64_t n);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Mixture thermo and transport properties (Sec. 2.1)                                        */
 /* ---------------------------------------------------------------------------------------- */
 /* Per cell: c_p [J/kg/K] and h [J/kg] (mass-weighted NASA-7), Wilke mixture viscosity mu

@@ -202,3 +202,187 @@ def chem_selftest_gemm(epi: int, A, B, out, bias=None, z=None, err=None, stream=
                                     _ptr(bias, torch.float32), _ptr(z, torch.bfloat16), _ptr(out),
                                     _ptr(err, torch.int32), _stream(stream)))
     return err
+
+
+# ------------------------------------------------------------------------------------------
+# learned reaction step
+# ------------------------------------------------------------------------------------------
+class TrainOpts(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("w_data", C.c_float), ("w_mass", C.c_float), ("apply", C.c_int), ("reserved", C.c_int)]
+
+
+class AnnOpts(C.Structure):
+    _fields_ = [("range_margin", C.c_double), ("elem_tol", C.c_double), ("T_min", C.c_double),
+                ("T_max", C.c_double), ("dT_max", C.c_double), ("no_fallback", C.c_int),
+                ("reserved", C.c_int), ("di", DiOpts)]
+
+
+_ann_sigs_done = False
+
+
+def _ann_sigs():
+    global _ann_sigs_done
+    if _ann_sigs_done:
+        return
+    L = lib()
+    vp, i64, i32, fp = C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_float)
+    L.chem_ann_create.argtypes = [vp, C.POINTER(i32), i32, C.c_uint64, C.POINTER(vp)]
+    L.chem_ann_free.argtypes = [vp]
+    L.chem_ann_free.restype = None
+    L.chem_ann_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                C.POINTER(i64)]
+    L.chem_ann_set_norm.argtypes = [vp, fp]
+    L.chem_ann_get_norm.argtypes = [vp, fp]
+    L.chem_ann_fit_norm.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
+    L.chem_ann_features.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+    L.chem_ann_targets.argtypes = [vp, i64, i64, vp, vp, vp, vp]
+    L.chem_ann_forward.argtypes = [vp, vp, i64, vp, vp, C.c_size_t, vp]
+    L.chem_ann_train_step.argtypes = [vp, vp, vp, vp, i64, C.POINTER(TrainOpts), vp, vp]
+    L.chem_ann_get_params.argtypes = [vp, i32, fp, i64]
+    L.chem_ann_set_params.argtypes = [vp, fp, i64]
+    L.chem_ann_save.argtypes = [vp, C.c_char_p]
+    L.chem_ann_load.argtypes = [vp, C.c_char_p, C.POINTER(vp)]
+    L.chem_ann_error.argtypes = [vp, C.POINTER(i32)]
+    L.chem_step_ann.argtypes = [vp, vp, i64, i64, C.c_double, vp, vp, vp, C.POINTER(AnnOpts), vp, vp,
+                                C.c_size_t, vp]
+    L.chem_ann_workspace_bytes.argtypes = [vp, i64]
+    L.chem_ann_workspace_bytes.restype = C.c_size_t
+    _ann_sigs_done = True
+
+
+class Ann:
+    """An MLP of the learned reaction step (owns a chem_ann handle)."""
+
+    def __init__(self, handle: int, mech: Mech):
+        _ann_sigs()
+        self.handle = C.c_void_p(handle)
+        self.mech = mech
+        n_in, n_out, nl = C.c_int(), C.c_int(), C.c_int()
+        dims = (C.c_int * 9)()
+        npar = C.c_int64()
+        _check(lib().chem_ann_info(self.handle, C.byref(n_in), C.byref(n_out), C.byref(nl), dims,
+                                   C.byref(npar)))
+        self.n_in, self.n_out, self.L = n_in.value, n_out.value, nl.value
+        self.dims = [dims[i] for i in range(self.L + 1)]
+        self.n_out_pad = self.dims[-1]
+        self.n_params = npar.value
+        self.norm_size = 4 * self.n_in + 2 * self.n_out
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().chem_ann_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def chem_ann_create(m: Mech, hidden, seed: int = 0) -> Ann:
+    _ann_sigs()
+    h = C.c_void_p()
+    arr = (C.c_int * len(hidden))(*hidden)
+    _check(lib().chem_ann_create(m.handle, arr, len(hidden), int(seed), C.byref(h)))
+    return Ann(h.value, m)
+
+
+def chem_ann_load(m: Mech, path: str) -> Ann:
+    _ann_sigs()
+    h = C.c_void_p()
+    _check(lib().chem_ann_load(m.handle, path.encode(), C.byref(h)))
+    return Ann(h.value, m)
+
+
+def chem_ann_save(a: Ann, path: str) -> None:
+    _check(lib().chem_ann_save(a.handle, path.encode()))
+
+
+def _fptr(arr):
+    return arr.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def chem_ann_get_norm(a: Ann):
+    import numpy as np
+    out = np.zeros(a.norm_size, dtype=np.float32)
+    _check(lib().chem_ann_get_norm(a.handle, _fptr(out)))
+    return out
+
+
+def chem_ann_set_norm(a: Ann, norm) -> None:
+    import numpy as np
+    arr = np.ascontiguousarray(norm, dtype=np.float32)
+    _check(lib().chem_ann_set_norm(a.handle, _fptr(arr)))
+
+
+def chem_ann_fit_norm(a: Ann, T, p, Y0, Y1, n: Optional[int] = None, stream=None) -> None:
+    ld = Y0.shape[1]
+    n = ld if n is None else n
+    f64 = torch.float64
+    _check(lib().chem_ann_fit_norm(a.handle, n, ld, _ptr(T, f64), _ptr(p, f64), _ptr(Y0, f64),
+                                   _ptr(Y1, f64), _stream(stream)))
+
+
+def chem_ann_features(a: Ann, T, p, Y, X, bcty=None, n: Optional[int] = None, stream=None) -> None:
+    ld = Y.shape[1]
+    n = ld if n is None else n
+    f64 = torch.float64
+    _check(lib().chem_ann_features(a.handle, n, ld, _ptr(T, f64), _ptr(p, f64), _ptr(Y, f64),
+                                   _ptr(X, torch.bfloat16), _ptr(bcty, torch.float32), _stream(stream)))
+
+
+def chem_ann_targets(a: Ann, Y0, Y1, U, n: Optional[int] = None, stream=None) -> None:
+    ld = Y0.shape[1]
+    n = ld if n is None else n
+    _check(lib().chem_ann_targets(a.handle, n, ld, _ptr(Y0, torch.float64), _ptr(Y1, torch.float64),
+                                  _ptr(U, torch.float32), _stream(stream)))
+
+
+def chem_ann_workspace_bytes(a: Ann, n: int) -> int:
+    _ann_sigs()
+    return int(lib().chem_ann_workspace_bytes(a.handle, n))
+
+
+def chem_ann_forward(a: Ann, X, U, workspace, stream=None) -> None:
+    _check(lib().chem_ann_forward(a.handle, _ptr(X, torch.bfloat16), X.shape[0], _ptr(U, torch.float32),
+                                  _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                  _stream(stream)))
+
+
+def chem_ann_train_step(a: Ann, X, Ut, bcty=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                        w_data=1.0, w_mass=0.1, apply=True, loss_out=None, stream=None) -> None:
+    o = TrainOpts(lr, beta1, beta2, eps, w_data, w_mass if bcty is not None else 0.0, int(apply), 0)
+    _check(lib().chem_ann_train_step(a.handle, _ptr(X, torch.bfloat16), _ptr(Ut, torch.float32),
+                                     _ptr(bcty, torch.float32), X.shape[0], C.byref(o),
+                                     _ptr(loss_out, torch.float32), _stream(stream)))
+
+
+def chem_ann_get_params(a: Ann, which: int = 0):
+    import numpy as np
+    out = np.zeros(a.n_params, dtype=np.float32)
+    _check(lib().chem_ann_get_params(a.handle, int(which), _fptr(out), a.n_params))
+    return out
+
+
+def chem_ann_set_params(a: Ann, flat) -> None:
+    import numpy as np
+    arr = np.ascontiguousarray(flat, dtype=np.float32)
+    _check(lib().chem_ann_set_params(a.handle, _fptr(arr), arr.size))
+
+
+def chem_ann_error(a: Ann) -> int:
+    v = C.c_int()
+    _check(lib().chem_ann_error(a.handle, C.byref(v)))
+    return v.value
+
+
+def chem_step_ann(m: Mech, a: Ann, dt: float, T, p, Y, status, workspace, range_margin=0.05,
+                  elem_tol=1e-3, T_min=250.0, T_max=3500.0, dT_max=0.0, no_fallback=False,
+                  di_rtol=0.0, di_atol_Y=0.0, n: Optional[int] = None, stream=None) -> None:
+    ld = _ld(Y, m)
+    n = ld if n is None else n
+    o = AnnOpts(range_margin, elem_tol, T_min, T_max, dT_max, int(no_fallback), 0,
+                DiOpts(di_rtol, di_atol_Y, 0.0, 0.0, 0, 0))
+    _check(lib().chem_step_ann(m.handle, a.handle, n, ld, float(dt), _ptr(T, torch.float64),
+                               _ptr(p, torch.float64), _ptr(Y, torch.float64), C.byref(o),
+                               _ptr(status, torch.int32), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _stream(stream)))

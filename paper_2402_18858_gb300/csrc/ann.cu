@@ -1,0 +1,996 @@
+// The learned reaction step (Sec. 2.2): an MLP maps the cell state phi(t) = {T, p, F(Y)}
+// (F = Box-Cox transform, Eq. 7, lambda = 0.1) to the change of the transformed mass
+// fractions over dt, standing in for the direct integration of Eq. 2.  The paper runs it in
+// half precision (Sec. 2.1); here it is BF16 on the tcgen05 tensor cores with FP32
+// accumulation, trained by this file's own forward/backward kernels with the loss of
+// Eqs. 8-9 and Adam.  Cells whose inputs fall outside the training range, whose prediction
+// breaks element conservation or gives a non-physical temperature fall back to direct
+// integration, so the step never returns an unchecked learned state.
+//
+// Reading of the output (the paper writes u* = Y(t+dt) - Y(t); its Eq. 7 transform is applied
+// to the species): the network predicts u_k = (F(Y_k(t+dt)) - F(Y_k(t)) - mu_k) / sigma_k,
+// z-scored over the training set; T(t+dt) follows from enthalpy conservation of the adiabatic
+// constant-pressure cell, h(T(t+dt), Y(t+dt)) = h(T(t), Y(t)), solved by Newton's method.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using bf16 = __nv_bfloat16;
+
+namespace chem {
+
+constexpr float kLambda = 0.1f;     // Box-Cox parameter (Sec. 2.2)
+constexpr int kMaxLayers = 8;
+constexpr int kInPad = 64;          // input features padded to one 64-wide K slab
+constexpr int kStatBlock = 256;
+
+// Box-Cox transform of a mass fraction (Eq. 7 read as (x^lambda - 1)/lambda, x clipped >= 0)
+__device__ __forceinline__ float bct_f(double y) {
+  const float x = (float)fmax(y, 0.0);
+  return x > 0.0f ? (exp2f(kLambda * log2f(x)) - 1.0f) * (1.0f / kLambda) : -1.0f / kLambda;
+}
+// inverse: x = (lambda z + 1)^(1/lambda) = t^10, 0 where t <= 0
+__device__ __forceinline__ float ibct_f(float z) {
+  const float t = fmaxf(kLambda * z + 1.0f, 0.0f);
+  const float t2 = t * t, t4 = t2 * t2, t8 = t4 * t4;
+  return t8 * t2;
+}
+
+}  // namespace chem
+
+using namespace chem;
+
+struct chem_ann_s {
+  int device = 0;
+  chem_mech_s* mech = nullptr;
+  DevMech dm{};
+  int K = 0, n_in = 0, n_out = 0, n_out_pad = 0, L = 0;
+  int dims[kMaxLayers + 1] = {0};
+  int64_t n_params = 0;        // including padding
+  void* dmem = nullptr;        // all parameter-sized device memory
+  float *Wm[kMaxLayers], *bm[kMaxLayers], *gW[kMaxLayers], *gb[kMaxLayers];
+  float *mW[kMaxLayers], *vW[kMaxLayers], *mb[kMaxLayers], *vb[kMaxLayers];
+  bf16 *W[kMaxLayers], *WT[kMaxLayers];
+  float* norm = nullptr;       // device: in_mean, in_std, in_min, in_max [n_in]; out_mean, out_std [n_out]
+  std::vector<float> hnorm;    // host copy
+  int step = 0;
+  int* err = nullptr;          // device GEMM error flag
+  // training scratch
+  void* tmem_ = nullptr;
+  int64_t tcap = 0;
+  float* loss_part = nullptr;
+};
+
+// ------------------------------------------------------------------------------------------
+// kernels
+// ------------------------------------------------------------------------------------------
+namespace {
+
+// raw feature j of cell i: 0 -> T, 1 -> p, 2 + k -> F(Y_k)
+__device__ __forceinline__ float raw_feature(int j, int64_t i, int64_t ld, const double* T, const double* p,
+                                             const double* Y) {
+  if (j == 0) return (float)T[i];
+  if (j == 1) return (float)p[i];
+  return bct_f(Y[(size_t)(j - 2) * ld + i]);
+}
+
+// normalised BF16 features X[i][0..63]; range flag (bit 1) against the training min/max
+__global__ void features_kernel(int64_t n, int64_t ld, const double* T, const double* p, const double* Y, int n_in,
+                                const float* norm, float margin, bf16* X, int32_t* flags, float* bcty, int K) {
+  const float* mean = norm;
+  const float* sd = norm + n_in;
+  const float* mn = norm + 2 * n_in;
+  const float* mx = norm + 3 * n_in;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int flag = 0;
+    __align__(16) bf16 row[kInPad];
+    for (int j = 0; j < kInPad; ++j) {
+      float v = 0.0f;
+      if (j < n_in) {
+        const float r = raw_feature(j, i, ld, T, p, Y);
+        const float span = mx[j] - mn[j];
+        if (!(r >= mn[j] - margin * span && r <= mx[j] + margin * span)) flag = 1;
+        v = (r - mean[j]) / sd[j];
+        if (bcty && j >= 2) bcty[(size_t)i * K + (j - 2)] = r;
+      }
+      row[j] = __float2bfloat16_rn(v);
+    }
+    uint4* dst = (uint4*)(X + (size_t)i * kInPad);
+#pragma unroll
+    for (int q = 0; q < kInPad / 8; ++q) dst[q] = ((const uint4*)row)[q];
+    if (flags) flags[i] = flag;
+  }
+}
+
+// z-scored targets u_k = (F(Y1_k) - F(Y0_k) - mu_k)/sigma_k, padded to n_out_pad columns
+__global__ void targets_kernel(int64_t n, int64_t ld, const double* Y0, const double* Y1, int K, int n_out_pad,
+                               const float* out_mean, const float* out_sd, float* U) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < n_out_pad; ++k) {
+      float v = 0.0f;
+      if (k < K) v = (bct_f(Y1[(size_t)k * ld + i]) - bct_f(Y0[(size_t)k * ld + i]) - out_mean[k]) / out_sd[k];
+      U[(size_t)i * n_out_pad + k] = v;
+    }
+}
+
+// per-block partial statistics of the raw features (n_in) and raw targets (K):
+// sum, sum of squares, min, max -> part[b][c][4] (deterministic: fixed-order tree per block)
+__global__ void stats_partial_kernel(int64_t n, int64_t ld, const double* T, const double* p, const double* Y0,
+                                     const double* Y1, int n_in, int K, double* part) {
+  const int C = n_in + K;
+  __shared__ double sh[4][kStatBlock];
+  for (int c = 0; c < C; ++c) {
+    double s = 0, q = 0, lo = 1e300, hi = -1e300;
+    for (int64_t i = (int64_t)blockIdx.x * kStatBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kStatBlock) {
+      double v;
+      if (c < n_in) v = raw_feature(c, i, ld, T, p, Y0);
+      else v = (double)(bct_f(Y1[(size_t)(c - n_in) * ld + i]) - bct_f(Y0[(size_t)(c - n_in) * ld + i]));
+      s += v;
+      q += v * v;
+      lo = fmin(lo, v);
+      hi = fmax(hi, v);
+    }
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = q;
+    sh[2][threadIdx.x] = lo;
+    sh[3][threadIdx.x] = hi;
+    __syncthreads();
+    for (int o = kStatBlock / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+        sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + o]);
+        sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + o]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0)
+      for (int t = 0; t < 4; ++t) part[((size_t)blockIdx.x * C + c) * 4 + t] = sh[t][0];
+    __syncthreads();
+  }
+}
+
+// network output -> new state; flags: 1 range, 2 non-finite, 4 element residual, 8 T range, 16 |dT|
+__global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const double* p, double* Y,
+                              const float* U, int n_out_pad, const float* out_mean, const float* out_sd,
+                              int32_t* flags, int32_t* status, float elem_tol, float Tmin, float Tmax, float dTmax) {
+  const int K = m.K, E = m.E;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int flag = flags[i];
+    if (flag == 0) {
+      float yn[CHEM_MAX_SPECIES];
+      float eo[kMaxElem], en[kMaxElem];
+      for (int e = 0; e < E; ++e) eo[e] = en[e] = 0.0f;
+      const float T0 = (float)T[i];
+      // enthalpy of the old state (FP32 NASA-7 sums) and old element moles
+      float h0 = 0.0f, ysum = 0.0f;
+      const int hi0 = T0 >= (float)m.Tmid ? 1 : 0;
+      for (int k = 0; k < K; ++k) {
+        const double y = Y[(size_t)k * ld + i];
+        const double* a = m.th + ((size_t)k * 2 + hi0) * kThermoStride;
+        const float hRT = (float)a[5] + T0 * ((float)a[6] + T0 * ((float)a[7] + T0 * ((float)a[8] + T0 * (float)a[9])))
+                          + (float)a[10] / T0;
+        h0 += (float)(y * m.invW[k]) * hRT;
+        for (int e = 0; e < E; ++e) eo[e] += (float)(y * m.compW[(size_t)k * E + e]);
+        const float z = bct_f(y) + U[(size_t)i * n_out_pad + k] * out_sd[k] + out_mean[k];
+        const float v = ibct_f(z);
+        yn[k] = v;
+        ysum += v;
+      }
+      h0 *= T0;   // h/R per kg
+      if (!(ysum > 0.0f) || !isfinite(ysum)) flag |= 2;
+      if (!flag) {
+        const float is = 1.0f / ysum;
+        for (int k = 0; k < K; ++k) {
+          yn[k] *= is;
+          for (int e = 0; e < E; ++e) en[e] += yn[k] * (float)m.compW[(size_t)k * E + e];
+        }
+        float res = 0.0f;
+        for (int e = 0; e < E; ++e)
+          if (eo[e] > 0.0f) res = fmaxf(res, fabsf(en[e] - eo[e]) / eo[e]);
+        if (!(res <= elem_tol)) flag |= 4;
+        // T from h(T, Y_new) = h0 by Newton's method
+        float Tn = T0;
+        for (int it = 0; it < 8; ++it) {
+          const int hi = Tn >= (float)m.Tmid ? 1 : 0;
+          float h = 0.0f, cp = 0.0f;
+          for (int k = 0; k < K; ++k) {
+            const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
+            const float yw = yn[k] * (float)m.invW[k];
+            const float cpR = (float)a[0] + Tn * ((float)a[1] + Tn * ((float)a[2] + Tn * ((float)a[3] + Tn * (float)a[4])));
+            const float hRT = (float)a[5] + Tn * ((float)a[6] + Tn * ((float)a[7] + Tn * ((float)a[8] + Tn * (float)a[9])))
+                              + (float)a[10] / Tn;
+            h += yw * hRT * Tn;
+            cp += yw * cpR;
+          }
+          const float dT = (h - h0) / cp;
+          Tn = fminf(fmaxf(Tn - dT, 200.0f), 6000.0f);
+          if (fabsf(dT) < 1e-4f * Tn) break;
+        }
+        if (!isfinite(Tn)) flag |= 2;
+        else if (Tn < Tmin || Tn > Tmax) flag |= 8;
+        else if (dTmax > 0.0f && fabsf(Tn - T0) > dTmax) flag |= 16;
+        if (!flag) {
+          for (int k = 0; k < K; ++k) Y[(size_t)k * ld + i] = (double)yn[k];
+          T[i] = (double)Tn;
+        }
+      }
+    }
+    flags[i] = flag;
+    status[i] = flag ? CHEM_CELL_ANN_FALLBACK : CHEM_CELL_OK;
+  }
+}
+
+// deterministic compaction of cells with status != 0: per-block counts, scan, write
+constexpr int kCompactBlock = 1024;
+
+__global__ void compact_count_kernel(int64_t n, const int32_t* status, int32_t* blk_count) {
+  __shared__ int ws[32];
+  const int64_t i = (int64_t)blockIdx.x * kCompactBlock + threadIdx.x;
+  const int f = (i < n && status[i] != 0) ? 1 : 0;
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < kCompactBlock / 32; ++w) s += ws[w];
+    blk_count[blockIdx.x] = s;
+  }
+}
+
+__global__ void compact_scan_kernel(int nb, int32_t* blk_count, int32_t* total) {
+  // single thread: exclusive scan in block order (nb <= a few thousand)
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int s = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int c = blk_count[b];
+      blk_count[b] = s;
+      s += c;
+    }
+    *total = s;
+  }
+}
+
+__global__ void compact_write_kernel(int64_t n, const int32_t* status, const int32_t* blk_off, int32_t* idx) {
+  __shared__ int ws[32];
+  const int64_t i = (int64_t)blockIdx.x * kCompactBlock + threadIdx.x;
+  const int f = (i < n && status[i] != 0) ? 1 : 0;
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) ws[w] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int q = 0; q < kCompactBlock / 32; ++q) {
+      const int c = ws[q];
+      ws[q] = s;
+      s += c;
+    }
+  }
+  __syncthreads();
+  if (f) idx[blk_off[blockIdx.x] + ws[w] + __popc(b & ((1u << lane) - 1u))] = (int32_t)i;
+}
+
+// DI statuses of the fallback cells back to the cells: 5 when DI succeeded, else DI's code
+__global__ void scatter_status_kernel(int64_t nmax, const int32_t* n_dev, const int32_t* idx, const int32_t* st_slot,
+                                      int32_t* status) {
+  const int64_t nf = min(nmax, (int64_t)*n_dev);
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nf; s += (int64_t)gridDim.x * blockDim.x)
+    status[idx[s]] = st_slot[s] == CHEM_CELL_OK ? CHEM_CELL_ANN_FALLBACK : st_slot[s];
+}
+
+// training loss (Eqs. 8-9) and its gradient w.r.t. the network output
+//   L = w_data * mean_{b,k}(u - u_t)^2 + w_mass * mean_b |sum_k Y*_k - 1|,
+//   Y*_k = F^-1(F(Y_k) + u_k sigma_k + mu_k)
+// dU (BF16 [B, n_out_pad]) and its transpose dUT ([n_out_pad, B]); per-block loss partials.
+__global__ void loss_grad_kernel(int64_t B, int K, int n_out_pad, const float* Up, const float* Ut, const float* bcty,
+                                 const float* out_mean, const float* out_sd, float w_data, float w_mass,
+                                 bf16* dU, bf16* dUT, float* part) {
+  __shared__ float sh[2][256];
+  float ld = 0.0f, lm = 0.0f;
+  const float cdata = 2.0f * w_data / (float)(B * K);
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (int64_t)gridDim.x * blockDim.x) {
+    float ysum = 0.0f;
+    if (bcty && w_mass != 0.0f)
+      for (int k = 0; k < K; ++k) ysum += ibct_f(bcty[b * K + k] + Up[b * n_out_pad + k] * out_sd[k] + out_mean[k]);
+    const float sgn = ysum > 1.0f ? 1.0f : (ysum < 1.0f ? -1.0f : 0.0f);
+    if (bcty && w_mass != 0.0f) lm += fabsf(ysum - 1.0f);
+    for (int k = 0; k < n_out_pad; ++k) {
+      float g = 0.0f;
+      if (k < K) {
+        const float d = Up[b * n_out_pad + k] - Ut[b * n_out_pad + k];
+        ld += d * d;
+        g = cdata * d;
+        if (bcty && w_mass != 0.0f) {
+          const float ys = ibct_f(bcty[b * K + k] + Up[b * n_out_pad + k] * out_sd[k] + out_mean[k]);
+          // dY*/du = Y*^(1 - lambda) sigma_k
+          g += w_mass / (float)B * sgn * (ys > 0.0f ? exp2f(0.9f * log2f(ys)) : 0.0f) * out_sd[k];
+        }
+      }
+      const bf16 gb = __float2bfloat16_rn(g);
+      dU[b * n_out_pad + k] = gb;
+      dUT[(int64_t)k * B + b] = gb;
+    }
+  }
+  sh[0][threadIdx.x] = ld;
+  sh[1][threadIdx.x] = lm;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sh[0][0] / (float)(B * K);
+    part[2 * blockIdx.x + 1] = sh[1][0] / (float)B;
+  }
+}
+
+__global__ void loss_final_kernel(int nb, const float* part, float w_data, float w_mass, float* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    float a = 0.0f, b = 0.0f;
+    for (int i = 0; i < nb; ++i) {
+      a += part[2 * i];
+      b += part[2 * i + 1];
+    }
+    out[0] = w_data * a + w_mass * b;
+    out[1] = a;
+    out[2] = b;
+  }
+}
+
+// BF16 transpose [R, C] -> [C, R] through 32 x 33 shared tiles
+__global__ void transpose_kernel(const bf16* in, int64_t R, int64_t C, bf16* out) {
+  __shared__ bf16 t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int64_t r = r0 + dy, c = c0 + threadIdx.x;
+    t[dy][threadIdx.x] = (r < R && c < C) ? in[r * C + c] : __float2bfloat16_rn(0.0f);
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int64_t c = c0 + dy, r = r0 + threadIdx.x;
+    if (c < C && r < R) out[c * R + r] = t[threadIdx.x][dy];
+  }
+}
+
+// column sums of a BF16 [B, N] matrix (bias gradients), one thread per column, fixed order
+__global__ void colsum_kernel(const bf16* dZ, int64_t B, int N, float* out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  float s = 0.0f;
+  for (int64_t b = 0; b < B; ++b) s += __bfloat162float(dZ[b * N + c]);
+  out[c] = s;
+}
+
+// Adam (Kingma & Ba 2015) on FP32 masters; refreshes the BF16 copy and its transpose
+__global__ void adam_kernel(int64_t n, int rows, int cols, float* w, const float* g, float* mom, float* vel, float lr,
+                            float b1, float b2, float eps, float bc1, float bc2, bf16* wb, bf16* wt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * mom[i] + (1.0f - b1) * gi;
+    const float vi = b2 * vel[i] + (1.0f - b2) * gi * gi;
+    mom[i] = mi;
+    vel[i] = vi;
+    const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    w[i] = wi;
+    if (wb) {
+      const bf16 q = __float2bfloat16_rn(wi);
+      wb[i] = q;
+      const int r = (int)(i / cols), c = (int)(i % cols);
+      wt[(int64_t)c * rows + r] = q;
+    }
+  }
+}
+
+__global__ void to_bf16_kernel(int64_t n, int rows, int cols, const float* w, bf16* wb, bf16* wt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const bf16 q = __float2bfloat16_rn(w[i]);
+    wb[i] = q;
+    const int r = (int)(i / cols), c = (int)(i % cols);
+    wt[(int64_t)c * rows + r] = q;
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, (int64_t)sms * 32));
+}
+
+// ------------------------------------------------------------------------------------------
+// host helpers
+// ------------------------------------------------------------------------------------------
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+double normal01(uint64_t& s) {
+  // Box-Muller on two uniforms in (0, 1]
+  const double u1 = ((splitmix64(s) >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+  const double u2 = ((splitmix64(s) >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+int check_ann(chem_ann a) {
+  if (!a || !a->dmem) return set_error(CHEM_E_ARG, "null or freed ANN handle");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != a->device) return set_error(CHEM_E_ARG, "ANN was created on another device");
+  return CHEM_OK;
+}
+
+
+// training scratch for a batch of B rows
+struct TrainBufs {
+  bf16 *Z[kMaxLayers], *A[kMaxLayers], *AT[kMaxLayers], *dZ[kMaxLayers], *dZT[kMaxLayers];
+  float* Up;
+};
+
+size_t train_bytes(const chem_ann_s* a, int64_t B) {
+  size_t s = 0;
+  for (int l = 0; l < a->L; ++l) {
+    const size_t w = (size_t)a->dims[l + 1];
+    s += 5 * B * w * 2 + 5 * 256;       // Z, A, AT, dZ, dZT
+  }
+  s += (size_t)B * kInPad * 2 + 256;   // XT
+  s += (size_t)B * a->n_out_pad * 4 + 256;
+  return s;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t seed, chem_ann* out) {
+  if (!mech || !hidden || n_hidden < 1 || n_hidden > kMaxLayers - 1 || !out)
+    return set_error(CHEM_E_ARG, "chem_ann_create: bad arguments");
+  *out = nullptr;
+  chem_ann_s* a = new chem_ann_s();
+  a->mech = mech;
+  a->dm = mech_dev(mech);
+  a->K = a->dm.K;
+  a->n_in = a->K + 2;
+  if (a->n_in > kInPad) { delete a; return set_error(CHEM_E_UNSUPPORTED, "chem_ann_create: more than 62 species"); }
+  a->n_out = a->K;
+  a->n_out_pad = a->K <= 32 ? 32 : 64;
+  a->L = n_hidden + 1;
+  a->dims[0] = kInPad;
+  for (int l = 0; l < n_hidden; ++l) {
+    if (hidden[l] < 8 || hidden[l] % 8 != 0 || hidden[l] > 8192) {
+      delete a;
+      return set_error(CHEM_E_ARG, "chem_ann_create: hidden widths must be multiples of 8 in [8, 8192]");
+    }
+    a->dims[l + 1] = hidden[l];
+  }
+  a->dims[a->L] = a->n_out_pad;
+  int rc = cuda_check(cudaGetDevice(&a->device), "cudaGetDevice");
+  if (rc) { delete a; return rc; }
+  // parameter-sized memory: masters, grads, Adam m/v (FP32) and BF16 W, W^T per layer
+  size_t total = 0;
+  std::vector<size_t> off;
+  auto take = [&](size_t bytes) { off.push_back(total); total += (bytes + 255) & ~size_t(255); };
+  for (int l = 0; l < a->L; ++l) {
+    const size_t nw = (size_t)a->dims[l + 1] * a->dims[l], nb = a->dims[l + 1];
+    for (int t = 0; t < 4; ++t) { take(nw * 4); take(nb * 4); }   // master, grad, m, v
+    take(nw * 2);
+    take(nw * 2);
+    a->n_params += (int64_t)(nw + nb);
+  }
+  take((size_t)(4 * a->n_in + 2 * a->n_out) * 4);   // normalisation
+  take(64);                                           // error flag
+  take(4096 * 8);                                     // loss partials
+  if (cudaMalloc(&a->dmem, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete a;
+    return set_error(CHEM_E_NOMEM, "chem_ann_create: cudaMalloc failed");
+  }
+  cudaMemset(a->dmem, 0, total);
+  char* b = (char*)a->dmem;
+  size_t q = 0;
+  for (int l = 0; l < a->L; ++l) {
+    a->Wm[l] = (float*)(b + off[q++]); a->bm[l] = (float*)(b + off[q++]);
+    a->gW[l] = (float*)(b + off[q++]); a->gb[l] = (float*)(b + off[q++]);
+    a->mW[l] = (float*)(b + off[q++]); a->mb[l] = (float*)(b + off[q++]);
+    a->vW[l] = (float*)(b + off[q++]); a->vb[l] = (float*)(b + off[q++]);
+    a->W[l] = (bf16*)(b + off[q++]); a->WT[l] = (bf16*)(b + off[q++]);
+  }
+  a->norm = (float*)(b + off[q++]);
+  a->err = (int*)(b + off[q++]);
+  a->loss_part = (float*)(b + off[q++]);
+  // initial weights: N(0, 2/fan_in) on the real (unpadded) inputs and outputs, zero biases
+  uint64_t st = seed * 0x9E3779B97F4A7C15ull + 12345;
+  for (int l = 0; l < a->L; ++l) {
+    const int rows = a->dims[l + 1], cols = a->dims[l];
+    const int real_cols = l == 0 ? a->n_in : cols, real_rows = l == a->L - 1 ? a->n_out : rows;
+    std::vector<float> w((size_t)rows * cols, 0.0f);
+    const double sd = std::sqrt(2.0 / real_cols) * (l == a->L - 1 ? 0.5 : 1.0);
+    for (int r = 0; r < real_rows; ++r)
+      for (int c = 0; c < real_cols; ++c) w[(size_t)r * cols + c] = (float)(sd * normal01(st));
+    cudaMemcpy(a->Wm[l], w.data(), w.size() * 4, cudaMemcpyHostToDevice);
+    to_bf16_kernel<<<grid_for((int64_t)w.size(), 256), 256>>>((int64_t)w.size(), rows, cols, a->Wm[l], a->W[l], a->WT[l]);
+  }
+  // identity normalisation until chem_ann_set_norm / chem_ann_fit_norm
+  a->hnorm.assign((size_t)4 * a->n_in + 2 * a->n_out, 0.0f);
+  for (int j = 0; j < a->n_in; ++j) {
+    a->hnorm[a->n_in + j] = 1.0f;
+    a->hnorm[2 * a->n_in + j] = -3e38f;
+    a->hnorm[3 * a->n_in + j] = 3e38f;
+  }
+  for (int k = 0; k < a->n_out; ++k) a->hnorm[4 * a->n_in + a->n_out + k] = 1.0f;
+  cudaMemcpy(a->norm, a->hnorm.data(), a->hnorm.size() * 4, cudaMemcpyHostToDevice);
+  if ((rc = cuda_check(cudaDeviceSynchronize(), "chem_ann_create"))) {
+    cudaFree(a->dmem);
+    delete a;
+    return rc;
+  }
+  *out = a;
+  return CHEM_OK;
+}
+
+void chem_ann_free(chem_ann a) {
+  if (!a) return;
+  if (a->tmem_) cudaFree(a->tmem_);
+  if (a->dmem) cudaFree(a->dmem);
+  a->dmem = nullptr;
+  delete a;
+}
+
+int chem_ann_info(chem_ann a, int* n_in, int* n_out, int* n_layers, int* dims, int64_t* n_params) {
+  if (!a) return set_error(CHEM_E_ARG, "null ANN handle");
+  if (n_in) *n_in = a->n_in;
+  if (n_out) *n_out = a->n_out;
+  if (n_layers) *n_layers = a->L;
+  if (dims)
+    for (int l = 0; l <= a->L; ++l) dims[l] = a->dims[l];
+  if (n_params) *n_params = a->n_params;
+  return CHEM_OK;
+}
+
+int chem_ann_set_norm(chem_ann a, const float* host_norm) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (!host_norm) return set_error(CHEM_E_ARG, "chem_ann_set_norm: null");
+  std::vector<float> v(host_norm, host_norm + a->hnorm.size());
+  for (int j = 0; j < a->n_in; ++j)
+    if (!(v[a->n_in + j] > 0)) v[a->n_in + j] = 1.0f;
+  for (int k = 0; k < a->n_out; ++k)
+    if (!(v[4 * a->n_in + a->n_out + k] > 0)) v[4 * a->n_in + a->n_out + k] = 1.0f;
+  a->hnorm = v;
+  return cuda_check(cudaMemcpy(a->norm, v.data(), v.size() * 4, cudaMemcpyHostToDevice), "chem_ann_set_norm");
+}
+
+int chem_ann_get_norm(chem_ann a, float* host_norm) {
+  if (!a || !host_norm) return set_error(CHEM_E_ARG, "chem_ann_get_norm: null");
+  std::memcpy(host_norm, a->hnorm.data(), a->hnorm.size() * 4);
+  return CHEM_OK;
+}
+
+int chem_ann_fit_norm(chem_ann a, int64_t n, int64_t ld, const double* T, const double* p, const double* Y0,
+                      const double* Y1, chem_stream stream) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (n < 2 || ld < n || !T || !p || !Y0 || !Y1) return set_error(CHEM_E_ARG, "chem_ann_fit_norm: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int C = a->n_in + a->K;
+  const int nb = (int)std::min<int64_t>((n + kStatBlock - 1) / kStatBlock, 1024);
+  double* part = nullptr;
+  if ((rc = cuda_check(cudaMallocAsync((void**)&part, (size_t)nb * C * 4 * 8, s), "fit_norm alloc"))) return rc;
+  stats_partial_kernel<<<nb, kStatBlock, 0, s>>>(n, ld, T, p, Y0, Y1, a->n_in, a->K, part);
+  std::vector<double> hp((size_t)nb * C * 4);
+  rc = cuda_check(cudaMemcpyAsync(hp.data(), part, hp.size() * 8, cudaMemcpyDeviceToHost, s), "fit_norm copy");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "fit_norm sync");
+  cudaFreeAsync(part, s);
+  if (rc) return rc;
+  std::vector<float> v(a->hnorm.size());
+  for (int c = 0; c < C; ++c) {
+    double sm = 0, sq = 0, lo = 1e300, hi = -1e300;
+    for (int b = 0; b < nb; ++b) {
+      const double* q = &hp[((size_t)b * C + c) * 4];
+      sm += q[0];
+      sq += q[1];
+      lo = std::min(lo, q[2]);
+      hi = std::max(hi, q[3]);
+    }
+    const double mean = sm / n, var = std::max(sq / n - mean * mean, 0.0);
+    const double sd = std::sqrt(var) > 1e-12 * std::max(1.0, std::fabs(mean)) ? std::sqrt(var) : 1.0;
+    if (c < a->n_in) {
+      v[c] = (float)mean;
+      v[a->n_in + c] = (float)sd;
+      v[2 * a->n_in + c] = (float)lo;
+      v[3 * a->n_in + c] = (float)hi;
+    } else {
+      const int k = c - a->n_in;
+      v[4 * a->n_in + k] = (float)mean;
+      v[4 * a->n_in + a->n_out + k] = (float)sd;
+    }
+  }
+  return chem_ann_set_norm(a, v.data());
+}
+
+int chem_ann_features(chem_ann a, int64_t n, int64_t ld, const double* T, const double* p, const double* Y, void* X,
+                      float* bcty, chem_stream stream) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (n < 0 || ld < n || (n > 0 && (!T || !p || !Y || !X))) return set_error(CHEM_E_ARG, "chem_ann_features: bad arguments");
+  if (n == 0) return CHEM_OK;
+  features_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, ld, T, p, Y, a->n_in, a->norm, 0.0f,
+                                                                     (bf16*)X, nullptr, bcty, a->K);
+  return cuda_check(cudaGetLastError(), "features_kernel launch");
+}
+
+int chem_ann_targets(chem_ann a, int64_t n, int64_t ld, const double* Y0, const double* Y1, float* U,
+                     chem_stream stream) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (n < 0 || ld < n || (n > 0 && (!Y0 || !Y1 || !U))) return set_error(CHEM_E_ARG, "chem_ann_targets: bad arguments");
+  if (n == 0) return CHEM_OK;
+  const float* om = a->norm + 4 * a->n_in;
+  targets_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, ld, Y0, Y1, a->K, a->n_out_pad, om,
+                                                                    om + a->n_out, U);
+  return cuda_check(cudaGetLastError(), "targets_kernel launch");
+}
+
+// forward pass over rows [0, M) of X (BF16 [M, 64]) into U (FP32 [M, n_out_pad]), through
+// BF16 activation buffers act[l] ([M, dims[l+1]]); optionally keeping pre-activations zs[l]
+static int forward_rows(chem_ann a, const bf16* X, int64_t M, bf16* const* act, bf16* const* zs, float* U,
+                        cudaStream_t s) {
+  int rc;
+  const bf16* in = X;
+  int64_t ld_in = kInPad;
+  for (int l = 0; l < a->L; ++l) {
+    const int N = a->dims[l + 1], Kd = a->dims[l];
+    GemmEpi e{};
+    e.bias = a->bm[l];
+    if (l < a->L - 1) {
+      e.out = act[l];
+      e.ldo = N;
+      e.zout = zs ? zs[l] : nullptr;
+      if ((rc = gemm_bf16(0, in, ld_in, a->W[l], Kd, (int)M, N, Kd, e, a->err, s))) return rc;
+      in = act[l];
+      ld_in = N;
+    } else {
+      e.out = U;
+      e.ldo = N;
+      if ((rc = gemm_bf16(1, in, ld_in, a->W[l], Kd, (int)M, N, Kd, e, a->err, s))) return rc;
+    }
+  }
+  return CHEM_OK;
+}
+
+// rows of the activation chunk used by inference (keeps a chunk's activations in L2)
+static int64_t infer_chunk(const chem_ann_s* a) {
+  (void)a;
+  return 32768;
+}
+
+size_t chem_ann_workspace_bytes(chem_ann a, int64_t n) {
+  if (!a || n < 0) return 0;
+  const int64_t mc = std::min<int64_t>(std::max<int64_t>(n, 1), infer_chunk(a));
+  size_t s = 0;
+  s += (size_t)n * kInPad * 2 + 256;                 // X
+  s += (size_t)n * a->n_out_pad * 4 + 256;           // U
+  for (int l = 0; l < a->L - 1; ++l) s += (size_t)mc * a->dims[l + 1] * 2 + 256;
+  s += 3 * ((size_t)n * 4 + 256);                     // flags, idx, DI slot status
+  s += ((size_t)(n / kCompactBlock + 2) * 4 + 256) + 256 + 256;   // block counts, total, queue
+  return s;
+}
+
+int chem_ann_forward(chem_ann a, const void* X, int64_t n, float* U, void* workspace, size_t ws_bytes,
+                     chem_stream stream) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!X || !U))) return set_error(CHEM_E_ARG, "chem_ann_forward: bad arguments");
+  if (n == 0) return CHEM_OK;
+  if (!workspace || ws_bytes < chem_ann_workspace_bytes(a, n))
+    return set_error(CHEM_E_WORKSPACE, "chem_ann_forward: workspace smaller than chem_ann_workspace_bytes()");
+  const int64_t mc = std::min<int64_t>(n, infer_chunk(a));
+  char* w = (char*)workspace;
+  bf16* act[kMaxLayers];
+  size_t o = (size_t)n * kInPad * 2 + 256 + (size_t)n * a->n_out_pad * 4 + 256;
+  for (int l = 0; l < a->L - 1; ++l) {
+    act[l] = (bf16*)(w + ((o + 255) & ~size_t(255)));
+    o = ((o + 255) & ~size_t(255)) + (size_t)mc * a->dims[l + 1] * 2;
+  }
+  for (int64_t r0 = 0; r0 < n; r0 += mc) {
+    const int64_t m = std::min(mc, n - r0);
+    if ((rc = forward_rows(a, (const bf16*)X + r0 * kInPad, m, act, nullptr, U + r0 * a->n_out_pad,
+                           (cudaStream_t)stream)))
+      return rc;
+  }
+  return CHEM_OK;
+}
+
+int chem_ann_error(chem_ann a, int* host_err) {
+  if (!a || !host_err) return set_error(CHEM_E_ARG, "chem_ann_error: null");
+  int rc = cuda_check(cudaMemcpy(host_err, a->err, sizeof(int), cudaMemcpyDeviceToHost), "chem_ann_error");
+  if (!rc) cudaMemset(a->err, 0, sizeof(int));
+  return rc;
+}
+
+int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, double* T, const double* p,
+                  double* Y, const chem_ann_opts* opts, int32_t* status, void* workspace, size_t ws_bytes,
+                  chem_stream stream) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (!mech || mech != a->mech) return set_error(CHEM_E_ARG, "chem_step_ann: the ANN belongs to another mechanism");
+  if (n < 0 || ld < n) return set_error(CHEM_E_ARG, "chem_step_ann: need 0 <= n <= ld");
+  if (n == 0) return CHEM_OK;
+  if (!T || !p || !Y || !status) return set_error(CHEM_E_ARG, "chem_step_ann: null array");
+  if (n > (int64_t)0x7fffffff) return set_error(CHEM_E_ARG, "chem_step_ann: too many cells");
+  if (!workspace || ws_bytes < chem_ann_workspace_bytes(a, n))
+    return set_error(CHEM_E_WORKSPACE, "chem_step_ann: workspace smaller than chem_ann_workspace_bytes()");
+  chem_ann_opts o{};
+  if (opts) o = *opts;
+  if (!(o.range_margin >= 0)) o.range_margin = 0.05;
+  if (!(o.elem_tol > 0)) o.elem_tol = 1e-3;
+  if (!(o.T_min > 0)) o.T_min = 250.0;
+  if (!(o.T_max > 0)) o.T_max = 3500.0;
+  di_fill_defaults(o.di);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t mc = std::min<int64_t>(n, infer_chunk(a));
+  char* w = (char*)workspace;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  bf16* X = (bf16*)(w + off);
+  off = al(off + (size_t)n * kInPad * 2);
+  float* U = (float*)(w + off);
+  off = al(off + (size_t)n * a->n_out_pad * 4);
+  bf16* act[kMaxLayers];
+  for (int l = 0; l < a->L - 1; ++l) {
+    act[l] = (bf16*)(w + off);
+    off = al(off + (size_t)mc * a->dims[l + 1] * 2);
+  }
+  int32_t* flags = (int32_t*)(w + off);
+  off = al(off + (size_t)n * 4);
+  int32_t* idx = (int32_t*)(w + off);
+  off = al(off + (size_t)n * 4);
+  int32_t* st_slot = (int32_t*)(w + off);
+  off = al(off + (size_t)n * 4);
+  const int nb = (int)((n + kCompactBlock - 1) / kCompactBlock);
+  int32_t* blk = (int32_t*)(w + off);
+  off = al(off + (size_t)(nb + 1) * 4);
+  int32_t* nflag = (int32_t*)(w + off);
+  off = al(off + 4);
+  unsigned int* queue = (unsigned int*)(w + off);
+
+  // 1. features and range flags
+  features_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, ld, T, p, Y, a->n_in, a->norm, (float)o.range_margin, X, flags,
+                                                  nullptr, a->K);
+  if ((rc = cuda_check(cudaGetLastError(), "features_kernel launch"))) return rc;
+  // 2. MLP on the tensor cores, chunk by chunk
+  for (int64_t r0 = 0; r0 < n; r0 += mc) {
+    const int64_t m = std::min(mc, n - r0);
+    if ((rc = forward_rows(a, X + r0 * kInPad, m, act, nullptr, U + r0 * a->n_out_pad, s))) return rc;
+  }
+  // 3. new state, checks
+  const float* om = a->norm + 4 * a->n_in;
+  update_kernel<<<grid_for(n, 128), 128, 0, s>>>(a->dm, n, ld, T, p, Y, U, a->n_out_pad, om, om + a->n_out, flags,
+                                                status, (float)o.elem_tol, (float)o.T_min, (float)o.T_max,
+                                                (float)o.dT_max);
+  if ((rc = cuda_check(cudaGetLastError(), "update_kernel launch"))) return rc;
+  if (!o.no_fallback) {
+    // 4. compaction of flagged cells (deterministic order) and direct integration of those
+    compact_count_kernel<<<nb, kCompactBlock, 0, s>>>(n, status, blk);
+    compact_scan_kernel<<<1, 32, 0, s>>>(nb, blk, nflag);
+    compact_write_kernel<<<nb, kCompactBlock, 0, s>>>(n, status, blk, idx);
+    if ((rc = cuda_check(cudaMemsetAsync(queue, 0, 4, s), "queue reset"))) return rc;
+    if ((rc = launch_di(a->dm, n, ld, dt, T, p, Y, idx, o.di, st_slot, nullptr, queue, s, nflag))) return rc;
+    scatter_status_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, nflag, idx, st_slot, status);
+    if ((rc = cuda_check(cudaGetLastError(), "fallback launch"))) return rc;
+  }
+  return CHEM_OK;
+}
+
+int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float* bcty, int64_t B,
+                        const chem_train_opts* opts, float* loss_out, chem_stream stream) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (B < 8 || B > (1 << 20) || B % 8 != 0 || !Xv || !Ut || !opts)
+    return set_error(CHEM_E_ARG, "chem_ann_train_step: bad arguments (B must be a multiple of 8)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bf16* X = (const bf16*)Xv;
+  if (B > a->tcap) {
+    if (a->tmem_) { cudaStreamSynchronize(s); cudaFree(a->tmem_); a->tmem_ = nullptr; a->tcap = 0; }
+    if (cudaMalloc(&a->tmem_, train_bytes(a, B)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(CHEM_E_NOMEM, "chem_ann_train_step: cudaMalloc of training buffers failed");
+    }
+    a->tcap = B;
+  }
+  // carve training buffers
+  TrainBufs t{};
+  char* w = (char*)a->tmem_;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { void* p = w + off; off = (off + bytes + 255) & ~size_t(255); return p; };
+  for (int l = 0; l < a->L; ++l) {
+    const size_t n = (size_t)B * a->dims[l + 1];
+    t.Z[l] = (bf16*)take(n * 2);
+    t.A[l] = (bf16*)take(n * 2);
+    t.AT[l] = (bf16*)take(n * 2);
+    t.dZ[l] = (bf16*)take(n * 2);
+    t.dZT[l] = (bf16*)take(n * 2);
+  }
+  bf16* XT = (bf16*)take((size_t)B * kInPad * 2);
+  t.Up = (float*)take((size_t)B * a->n_out_pad * 4);
+  // forward (pre-activations kept for GELU')
+  bf16* act[kMaxLayers];
+  bf16* zs[kMaxLayers];
+  for (int l = 0; l < a->L; ++l) { act[l] = t.A[l]; zs[l] = t.Z[l]; }
+  if ((rc = forward_rows(a, X, B, act, zs, t.Up, s))) return rc;
+  // loss and dU
+  const float* om = a->norm + 4 * a->n_in;
+  const int nbl = (int)std::min<int64_t>((B + 255) / 256, 2048);
+  const int Lo = a->L - 1;
+  loss_grad_kernel<<<nbl, 256, 0, s>>>(B, a->K, a->n_out_pad, t.Up, Ut, bcty, om, om + a->n_out, opts->w_data,
+                                      opts->w_mass, t.dZ[Lo], t.dZT[Lo], a->loss_part);
+  if (loss_out) loss_final_kernel<<<1, 32, 0, s>>>(nbl, a->loss_part, opts->w_data, opts->w_mass, loss_out);
+  // backward
+  dim3 tb(32, 8);
+  for (int l = Lo; l >= 0; --l) {
+    const int N = a->dims[l + 1], Kd = a->dims[l];
+    // input activations of layer l, transposed: [Kd, B]
+    const bf16* inT;
+    if (l == 0) {
+      transpose_kernel<<<dim3((kInPad + 31) / 32, (unsigned)((B + 31) / 32)), tb, 0, s>>>(X, B, kInPad, XT);
+      inT = XT;
+    } else {
+      transpose_kernel<<<dim3((unsigned)((Kd + 31) / 32), (unsigned)((B + 31) / 32)), tb, 0, s>>>(t.A[l - 1], B, Kd,
+                                                                                                  t.AT[l - 1]);
+      inT = t.AT[l - 1];
+    }
+    if (l != Lo)
+      transpose_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)((B + 31) / 32)), tb, 0, s>>>(t.dZ[l], B, N, t.dZT[l]);
+    // dW_l [N, Kd] = dZ_l^T [N, B] (A_{l-1}^T [Kd, B])^T
+    GemmEpi e{};
+    e.out = a->gW[l];
+    e.ldo = Kd;
+    if ((rc = gemm_bf16(3, t.dZT[l], B, inT, B, N, Kd, (int)B, e, a->err, s))) return rc;
+    colsum_kernel<<<(N + 127) / 128, 128, 0, s>>>(t.dZ[l], B, N, a->gb[l]);
+    if (l > 0) {
+      // dZ_{l-1} [B, Kd] = (dZ_l [B, N] W_l [N, Kd]) * GELU'(Z_{l-1}); B operand = W_l^T [Kd, N]
+      GemmEpi e2{};
+      e2.out = t.dZ[l - 1];
+      e2.ldo = Kd;
+      e2.z = t.Z[l - 1];
+      e2.ldz = Kd;
+      if ((rc = gemm_bf16(2, t.dZ[l], N, a->WT[l], N, (int)B, Kd, N, e2, a->err, s))) return rc;
+    }
+  }
+  if ((rc = cuda_check(cudaGetLastError(), "training launches"))) return rc;
+  if (!opts->apply) return CHEM_OK;
+  // Adam
+  a->step++;
+  const float bc1 = 1.0f - std::pow(opts->beta1, (float)a->step), bc2 = 1.0f - std::pow(opts->beta2, (float)a->step);
+  for (int l = 0; l < a->L; ++l) {
+    const int rows = a->dims[l + 1], cols = a->dims[l];
+    const int64_t nw = (int64_t)rows * cols;
+    adam_kernel<<<grid_for(nw, 256), 256, 0, s>>>(nw, rows, cols, a->Wm[l], a->gW[l], a->mW[l], a->vW[l], opts->lr,
+                                                   opts->beta1, opts->beta2, opts->eps, bc1, bc2, a->W[l], a->WT[l]);
+    adam_kernel<<<grid_for(rows, 256), 256, 0, s>>>(rows, rows, 1, a->bm[l], a->gb[l], a->mb[l], a->vb[l], opts->lr,
+                                                    opts->beta1, opts->beta2, opts->eps, bc1, bc2, nullptr, nullptr);
+  }
+  return cuda_check(cudaGetLastError(), "adam launch");
+}
+
+// parameters/gradients as one flat FP32 host array: per layer W [dims[l+1], dims[l]] then b
+int chem_ann_get_params(chem_ann a, int which, float* host, int64_t count) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (!host || count != a->n_params || which < 0 || which > 1) return set_error(CHEM_E_ARG, "chem_ann_get_params: bad arguments");
+  cudaDeviceSynchronize();
+  float* p = host;
+  for (int l = 0; l < a->L; ++l) {
+    const size_t nw = (size_t)a->dims[l + 1] * a->dims[l], nb = a->dims[l + 1];
+    if ((rc = cuda_check(cudaMemcpy(p, which ? a->gW[l] : a->Wm[l], nw * 4, cudaMemcpyDeviceToHost), "get params"))) return rc;
+    p += nw;
+    if ((rc = cuda_check(cudaMemcpy(p, which ? a->gb[l] : a->bm[l], nb * 4, cudaMemcpyDeviceToHost), "get params"))) return rc;
+    p += nb;
+  }
+  return CHEM_OK;
+}
+
+int chem_ann_set_params(chem_ann a, const float* host, int64_t count) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (!host || count != a->n_params) return set_error(CHEM_E_ARG, "chem_ann_set_params: bad arguments");
+  const float* p = host;
+  for (int l = 0; l < a->L; ++l) {
+    const int rows = a->dims[l + 1], cols = a->dims[l];
+    const size_t nw = (size_t)rows * cols;
+    if ((rc = cuda_check(cudaMemcpy(a->Wm[l], p, nw * 4, cudaMemcpyHostToDevice), "set params"))) return rc;
+    p += nw;
+    if ((rc = cuda_check(cudaMemcpy(a->bm[l], p, rows * 4, cudaMemcpyHostToDevice), "set params"))) return rc;
+    p += rows;
+    to_bf16_kernel<<<grid_for((int64_t)nw, 256), 256>>>((int64_t)nw, rows, cols, a->Wm[l], a->W[l], a->WT[l]);
+  }
+  return cuda_check(cudaDeviceSynchronize(), "set params");
+}
+
+// checkpoint: header, dims, normalisation, Adam step, then masters and Adam moments
+int chem_ann_save(chem_ann a, const char* path) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  FILE* f = path ? std::fopen(path, "wb") : nullptr;
+  if (!f) return set_error(CHEM_E_ARG, "chem_ann_save: cannot open file");
+  cudaDeviceSynchronize();
+  const char magic[8] = {'C', 'H', 'E', 'M', 'A', 'N', 'N', '1'};
+  int hdr[4] = {a->K, a->L, a->step, (int)a->hnorm.size()};
+  std::fwrite(magic, 1, 8, f);
+  std::fwrite(hdr, 4, 4, f);
+  std::fwrite(a->dims, 4, a->L + 1, f);
+  std::fwrite(a->hnorm.data(), 4, a->hnorm.size(), f);
+  for (int l = 0; l < a->L; ++l) {
+    const size_t nw = (size_t)a->dims[l + 1] * a->dims[l], nb = a->dims[l + 1];
+    const float* parts[6] = {a->Wm[l], a->bm[l], a->mW[l], a->mb[l], a->vW[l], a->vb[l]};
+    const size_t sizes[6] = {nw, nb, nw, nb, nw, nb};
+    for (int q = 0; q < 6; ++q) {
+      std::vector<float> h(sizes[q]);
+      cudaMemcpy(h.data(), parts[q], sizes[q] * 4, cudaMemcpyDeviceToHost);
+      std::fwrite(h.data(), 4, h.size(), f);
+    }
+  }
+  const bool ok = std::ferror(f) == 0;
+  std::fclose(f);
+  return ok ? CHEM_OK : set_error(CHEM_E_ARG, "chem_ann_save: write failed");
+}
+
+int chem_ann_load(chem_mech mech, const char* path, chem_ann* out) {
+  if (!mech || !path || !out) return set_error(CHEM_E_ARG, "chem_ann_load: bad arguments");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_error(CHEM_E_ARG, std::string("chem_ann_load: cannot open ") + path);
+  char magic[8];
+  int hdr[4];
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, "CHEMANN1", 8) != 0 || std::fread(hdr, 4, 4, f) != 4 ||
+      hdr[1] < 2 || hdr[1] > kMaxLayers) {
+    std::fclose(f);
+    return set_error(CHEM_E_PARSE, "chem_ann_load: not an ANN checkpoint");
+  }
+  int dims[kMaxLayers + 1];
+  if (std::fread(dims, 4, hdr[1] + 1, f) != (size_t)hdr[1] + 1 || hdr[0] != mech_dev(mech).K) {
+    std::fclose(f);
+    return set_error(CHEM_E_PARSE, "chem_ann_load: checkpoint does not match the mechanism");
+  }
+  chem_ann a = nullptr;
+  int rc = chem_ann_create(mech, dims + 1, hdr[1] - 1, 0, &a);
+  if (rc) { std::fclose(f); return rc; }
+  std::vector<float> norm(hdr[3]);
+  bool ok = hdr[3] == (int)a->hnorm.size() && std::fread(norm.data(), 4, norm.size(), f) == norm.size();
+  for (int l = 0; ok && l < a->L; ++l) {
+    const size_t nw = (size_t)a->dims[l + 1] * a->dims[l], nb = a->dims[l + 1];
+    float* parts[6] = {a->Wm[l], a->bm[l], a->mW[l], a->mb[l], a->vW[l], a->vb[l]};
+    const size_t sizes[6] = {nw, nb, nw, nb, nw, nb};
+    for (int q = 0; ok && q < 6; ++q) {
+      std::vector<float> h(sizes[q]);
+      ok = std::fread(h.data(), 4, h.size(), f) == h.size();
+      if (ok) cudaMemcpy(parts[q], h.data(), h.size() * 4, cudaMemcpyHostToDevice);
+    }
+    const int rows = a->dims[l + 1], cols = a->dims[l];
+    to_bf16_kernel<<<grid_for((int64_t)nw, 256), 256>>>((int64_t)nw, rows, cols, a->Wm[l], a->W[l], a->WT[l]);
+  }
+  std::fclose(f);
+  if (!ok) { chem_ann_free(a); return set_error(CHEM_E_PARSE, "chem_ann_load: truncated checkpoint"); }
+  a->step = hdr[2];
+  if ((rc = chem_ann_set_norm(a, norm.data()))) { chem_ann_free(a); return rc; }
+  *out = a;
+  return cuda_check(cudaDeviceSynchronize(), "chem_ann_load");
+}
+
+}  // extern "C"

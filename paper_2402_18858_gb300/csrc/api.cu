@@ -191,6 +191,8 @@ struct chem_mech_s {
 
 using namespace chem;
 
+const DevMech& chem::mech_dev(chem_mech m) { return m->dev; }
+
 // Pack the host mechanism into one device allocation and point DevMech at its pieces.
 static int upload(const HostMech& hm, chem_mech_s* cm) {
   const int K = (int)hm.species.size(), I = (int)hm.rxn.size();
@@ -322,6 +324,9 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
     }
   std::vector<double> exptab(128);
   for (int j = 0; j < 128; ++j) exptab[j] = (double)std::exp2((long double)j / 128.0L);
+  std::vector<double> compW((size_t)K * E);
+  for (int k = 0; k < K; ++k)
+    for (int e = 0; e < E; ++e) compW[(size_t)k * E + e] = hm.comp[(size_t)k * E + e] / hm.W[k];
   std::vector<int> refs_pad(refs);
   if (refs_pad.empty()) refs_pad.push_back(0);
 
@@ -357,7 +362,7 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   size_t otroe = add(troe.data(), troe.size() * 8), optr = add(sp_ptr.data(), sp_ptr.size() * 4);
   size_t orxn = add(sp_rxn.data(), sp_rxn.size() * 4), onu = add(sp_nu.data(), sp_nu.size() * 8);
   size_t oref = add(refs_pad.data(), refs_pad.size() * 4), oP = add(Pm.data(), Pm.size() * 8);
-  size_t oexp = add(exptab.data(), exptab.size() * 8);
+  size_t oexp = add(exptab.data(), exptab.size() * 8), ocw = add(compW.data(), compW.size() * 8);
   std::vector<char> blob(total, 0);
   for (auto& p : pieces) std::memcpy(blob.data() + p.off, p.src, p.bytes);
   void* d = nullptr;
@@ -381,6 +386,7 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   m.sp_rxn = (const int*)(b + orxn); m.sp_nu = (const double*)(b + onu);
   m.n_ref = R; m.ref_sp = (const int*)(b + oref); m.P = (const double*)(b + oP);
   m.exptab = (const double*)(b + oexp);
+  m.compW = (const double*)(b + ocw);
   cm->dmem = d;
   cm->K = K; cm->I = I; cm->E = m.E;
   return CHEM_OK;
@@ -446,6 +452,18 @@ int chem_jacobian(chem_mech m, int64_t n, int64_t ld, const double* T, const dou
   return launch_jacobian(m->dev, n, ld, T, p, Y, jac, (cudaStream_t)stream);
 }
 
+}  // extern "C"
+
+void chem::di_fill_defaults(chem_di_opts& o) {
+  if (!(o.rtol > 0)) o.rtol = 1e-9;
+  if (!(o.atol_Y > 0)) o.atol_Y = 1e-18;
+  if (!(o.atol_T > 0)) o.atol_T = 1e-9;
+  if (o.max_steps <= 0) o.max_steps = 20000;
+  if (!(o.newton_tol > 0)) o.newton_tol = kDefaultNewtonTol;
+}
+
+extern "C" {
+
 size_t chem_workspace_bytes(chem_mech m, int64_t n) {
   (void)m;
   (void)n;
@@ -465,11 +483,7 @@ int chem_step_di(chem_mech m, int64_t n, int64_t ld, double dt, double* T, const
     return set_error(CHEM_E_WORKSPACE, "chem_step_di: workspace missing or smaller than chem_workspace_bytes()");
   chem_di_opts o{};
   if (opts) o = *opts;
-  if (!(o.rtol > 0)) o.rtol = 1e-9;
-  if (!(o.atol_Y > 0)) o.atol_Y = 1e-18;
-  if (!(o.atol_T > 0)) o.atol_T = 1e-9;
-  if (o.max_steps <= 0) o.max_steps = 20000;
-  if (!(o.newton_tol > 0)) o.newton_tol = kDefaultNewtonTol;
+  di_fill_defaults(o);
   if (!(o.rtol < 1) || !std::isfinite(o.atol_Y) || !std::isfinite(o.atol_T))
     return set_error(CHEM_E_ARG, "chem_step_di: bad tolerances");
   if ((rc = cuda_check(cudaMemsetAsync(workspace, 0, sizeof(unsigned int), (cudaStream_t)stream),

@@ -861,15 +861,17 @@ template <int NPL>
 __global__ void __launch_bounds__(128) di_kernel(DevMech m, int64_t n, int64_t ld, double dt, double* T,
                                                  const double* p, double* Y, const int32_t* idx, DiOpts o,
                                                  int32_t* status, int32_t* stats, unsigned int* queue,
-                                                 size_t warp_bytes) {
+                                                 size_t warp_bytes, const int32_t* n_dev) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, true, true);
+  // n_dev (optional): the number of entries of idx actually filled, known only on the device
+  const int64_t n_eff = n_dev ? min(n, (int64_t)max(*n_dev, 0)) : n;
   while (true) {
     unsigned int slot = 0;
     if (lane == 0) slot = atomicAdd(queue, 1u);
     slot = __shfl_sync(FULLMASK, slot, 0);
-    if ((int64_t)slot >= n) break;
+    if ((int64_t)slot >= n_eff) break;
     const int64_t col = idx ? (int64_t)idx[slot] : (int64_t)slot;
     double z[NPL];
     int cnt[4];
@@ -1034,7 +1036,7 @@ int launch_jacobian(const DevMech& m, int64_t n, int64_t ld, const double* T, co
 
 int launch_di(const DevMech& m, int64_t n, int64_t ld, double dt, double* T, const double* p,
               double* Y, const int32_t* idx, const chem_di_opts& opts, int32_t* status,
-              int32_t* stats, unsigned int* queue, cudaStream_t s) {
+              int32_t* stats, unsigned int* queue, cudaStream_t s, const int32_t* n_dev) {
   const size_t wb = di_smem_per_warp(m);
   DiOpts o{opts.rtol, opts.atol_Y, opts.atol_T, opts.newton_tol, opts.max_steps};
   int wpb;
@@ -1049,13 +1051,13 @@ int launch_di(const DevMech& m, int64_t n, int64_t ld, double dt, double* T, con
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, di_kernel<1>, 32 * wpb, smem);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)sm_count() * per_sm);
-    di_kernel<1><<<(int)grid, 32 * wpb, smem, s>>>(m, n, ld, dt, T, p, Y, idx, o, status, stats, queue, wb);
+    di_kernel<1><<<(int)grid, 32 * wpb, smem, s>>>(m, n, ld, dt, T, p, Y, idx, o, status, stats, queue, wb, n_dev);
   } else {
     if ((rc = configure(di_kernel<2>, wb, wpb, smem))) return rc;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, di_kernel<2>, 32 * wpb, smem);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)sm_count() * per_sm);
-    di_kernel<2><<<(int)grid, 32 * wpb, smem, s>>>(m, n, ld, dt, T, p, Y, idx, o, status, stats, queue, wb);
+    di_kernel<2><<<(int)grid, 32 * wpb, smem, s>>>(m, n, ld, dt, T, p, Y, idx, o, status, stats, queue, wb, n_dev);
   }
   return cuda_check(cudaGetLastError(), "di_kernel launch");
 }

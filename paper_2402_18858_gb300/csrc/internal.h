@@ -1,5 +1,6 @@
 // Internal declarations shared by the libchem translation units (not part of the C ABI).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -44,6 +45,7 @@ struct DevMech {
   const int* ref_sp;       // [n_ref]
   const double* P;         // [K][n_ref]
   const double* exptab;    // [128] 2^(j/128), the table of the FP64 exponential below
+  const double* compW;     // [K][E] element counts divided by the molar mass (mol/kg)
 };
 
 // FP64 exponential by the table-driven method (P. T. P. Tang, "Table-driven implementation of
@@ -79,6 +81,7 @@ __device__ __forceinline__ double exp_t(double x, const double* __restrict__ tab
 constexpr int kMaxElem = 8;
 
 struct HostMech;   // parsed mechanism (host)
+const DevMech& mech_dev(chem_mech m);
 
 // error reporting (thread-local message)
 int set_error(int code, const std::string& msg);
@@ -91,7 +94,20 @@ int launch_jacobian(const DevMech& m, int64_t n, int64_t ld, const double* T, co
                     const double* Y, double* jac, cudaStream_t s);
 int launch_di(const DevMech& m, int64_t n, int64_t ld, double dt, double* T, const double* p,
               double* Y, const int32_t* idx, const chem_di_opts& o, int32_t* status,
-              int32_t* stats, unsigned int* queue, cudaStream_t s);
+              int32_t* stats, unsigned int* queue, cudaStream_t s, const int32_t* n_dev = nullptr);
+void di_fill_defaults(chem_di_opts& o);
+
+// mlp.cu: C = A B^T on the tensor cores with a fused epilogue
+struct GemmEpi {
+  const float* bias;           // [N] or null
+  void* out;                   // [M, ldo] BF16 or FP32
+  int ldo;
+  const __nv_bfloat16* z;      // epilogue 2: pre-activations [M, ldz]
+  int ldz;
+  __nv_bfloat16* zout;         // epilogue 0: optional copy of the pre-activations [M, ldo]
+};
+int gemm_bf16(int epi, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int M, int N,
+              int K, const GemmEpi& e, int* err, cudaStream_t s);
 size_t di_smem_per_warp(const DevMech& m);
 
 int launch_exp_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s);

@@ -28,15 +28,6 @@ __device__ __forceinline__ float dgelu_f(float x) {
 // ------------------------------------------------------------------------------------------
 // GEMM kernel
 // ------------------------------------------------------------------------------------------
-struct GemmEpi {
-  const float* bias;   // [N] or null
-  void* out;           // [M, ldo] BF16 or FP32
-  int ldo;
-  const bf16* z;       // EPI_DGELU: pre-activations [M, ldz]
-  int ldz;
-  bf16* zout;          // EPI_GELU: optional copy of the pre-activations [M, ldo]
-};
-
 template <int BN>
 struct TileCfg {
   static constexpr int STAGES = BN >= 256 ? 4 : 6;

@@ -1,0 +1,134 @@
+"""GPU parity of the learned reaction step against the FP64 MLP oracle.
+
+* forward: the BF16 tensor-core MLP against the oracle's forward with BF16 storage emulated
+  (inputs, weights, hidden activations rounded to BF16): differences come only from FP32 vs
+  FP64 accumulation and from activations that sit on a BF16 rounding boundary; bound
+  max |dU| <= 2e-3 max|U| + 1e-3 and RMS(dU) <= 1e-3 RMS(U);
+* gradients: GPU backward (BF16 GEMMs, BF16 dZ and pre-activations) against the FP64 backward
+  of the same emulated forward: relative norm error per tensor <= 3e-2 (BF16 storage of dZ);
+* training is deterministic: a checkpoint reloaded and trained on gives the same losses bit
+  for bit as the original.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import mlp  # noqa: E402
+from paper_2402_18858_gb300 import workload as w  # noqa: E402
+
+HIDDEN = [1600, 800, 400]
+
+
+@pytest.fixture(scope="module")
+def lc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_18858_gb300 import build, chem
+    build.build()
+    chem.lib()
+    return chem
+
+
+@pytest.fixture(scope="module")
+def setup(lc, mechs):
+    m, path = mechs["c_30"]
+    gm = lc.chem_load_mech(path)
+    ann = lc.chem_ann_create(gm, HIDDEN, seed=7)
+    st = w.make_states(m, 2048, 55)
+    dev = torch.device("cuda")
+    T = torch.as_tensor(st.T, device=dev)
+    p = torch.as_tensor(st.p, device=dev)
+    Y0 = torch.as_tensor(st.Y, device=dev)
+    # a perturbed copy stands in for Y(t + dt) when fitting the normalisation
+    noise = torch.as_tensor(np.random.default_rng(1).standard_normal(st.Y.shape), device=dev)
+    Y1 = (Y0 * (1.0 + 0.01 * noise)).contiguous()
+    lc.chem_ann_fit_norm(ann, T, p, Y0, Y1)
+    X = torch.empty((2048, 64), dtype=torch.bfloat16, device=dev)
+    bcty = torch.empty((2048, m.n_species), dtype=torch.float32, device=dev)
+    lc.chem_ann_features(ann, T, p, Y0, X, bcty=bcty)
+    U = torch.empty((2048, ann.n_out_pad), dtype=torch.float32, device=dev)
+    lc.chem_ann_targets(ann, Y0, Y1, U)
+    torch.cuda.synchronize()
+    return gm, ann, st, X, bcty, U
+
+
+def test_features_and_targets(lc, setup, mechs):
+    gm, ann, st, X, bcty, U = setup
+    m, _ = mechs["c_30"]
+    norm = lc.chem_ann_get_norm(ann)
+    n_in = ann.n_in
+    raw = np.concatenate([st.T[:, None], st.p[:, None], mlp.bct(st.Y).T], axis=1)
+    ref = (raw - norm[:n_in]) / norm[n_in:2 * n_in]
+    got = X.float().cpu().numpy()[:, :n_in]
+    assert np.allclose(got, mlp.round_bf16(ref), rtol=2 ** -7, atol=2e-3)
+    assert (X.float().cpu().numpy()[:, n_in:] == 0).all()
+    assert np.allclose(bcty.cpu().numpy(), mlp.bct(st.Y).T, rtol=1e-5, atol=1e-5)
+
+
+def test_forward_parity(lc, setup):
+    gm, ann, st, X, bcty, U = setup
+    n = X.shape[0]
+    Ug = torch.empty((n, ann.n_out_pad), dtype=torch.float32, device="cuda")
+    ws = torch.empty(lc.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device="cuda")
+    lc.chem_ann_forward(ann, X, Ug, ws)
+    torch.cuda.synchronize()
+    assert lc.chem_ann_error(ann) == 0
+    params = mlp.unflatten(lc.chem_ann_get_params(ann), ann.dims)
+    Uo, _ = mlp.forward(params, X.float().cpu().numpy().astype(np.float64), bf16=True)
+    d = Ug.cpu().numpy() - Uo
+    assert np.abs(d).max() <= 2e-3 * np.abs(Uo).max() + 1e-3
+    assert np.sqrt((d ** 2).mean()) <= 1e-3 * np.sqrt((Uo ** 2).mean())
+
+
+def test_gradient_parity(lc, setup):
+    gm, ann, st, X, bcty, U = setup
+    B = 512
+    lc.chem_ann_train_step(ann, X[:B].contiguous(), U[:B].contiguous(), bcty[:B].contiguous(), apply=False)
+    torch.cuda.synchronize()
+    assert lc.chem_ann_error(ann) == 0
+    g_gpu = mlp.unflatten(lc.chem_ann_get_params(ann, which=1), ann.dims)
+    params = mlp.unflatten(lc.chem_ann_get_params(ann), ann.dims)
+    norm = lc.chem_ann_get_norm(ann)
+    K = ann.n_out
+    om, osd = norm[4 * ann.n_in:4 * ann.n_in + K].astype(np.float64), norm[4 * ann.n_in + K:].astype(np.float64)
+    Uo, cache = mlp.forward(params, X[:B].float().cpu().numpy().astype(np.float64), bf16=True)
+    _, _, _, dU = mlp.loss_and_grad(Uo, U[:B].cpu().numpy().astype(np.float64), K,
+                                    bcty[:B].cpu().numpy().astype(np.float64), om, osd, 1.0, 0.1)
+    g_or = mlp.backward(params, cache, dU)
+    for l, ((gw, gb), (ow, ob)) in enumerate(zip(g_gpu, g_or)):
+        assert np.linalg.norm(gw - ow) <= 3e-2 * np.linalg.norm(ow), l
+        assert np.linalg.norm(gb - ob) <= 3e-2 * np.linalg.norm(ob) + 1e-12, l
+
+
+def test_training_is_deterministic_and_resumable(lc, setup, tmp_path, mechs):
+    gm, ann0, st, X, bcty, U = setup
+    ann = lc.chem_ann_create(gm, HIDDEN, seed=3)
+    lc.chem_ann_set_norm(ann, lc.chem_ann_get_norm(ann0))
+    loss = torch.zeros(3, dtype=torch.float32, device="cuda")
+    B = 1024
+    hist = []
+    for it in range(30):
+        s = (it * B) % 2048
+        lc.chem_ann_train_step(ann, X[s:s + B].contiguous(), U[s:s + B].contiguous(), bcty[s:s + B].contiguous(),
+                               lr=1e-3, loss_out=loss)
+        hist.append(float(loss[0].item()))
+    assert hist[-1] < 0.8 * hist[0]
+    assert lc.chem_ann_error(ann) == 0
+    path = str(tmp_path / "ann.ckpt")
+    lc.chem_ann_save(ann, path)
+    ann2 = lc.chem_ann_load(gm, path)
+    assert np.array_equal(lc.chem_ann_get_params(ann), lc.chem_ann_get_params(ann2))
+    la, lb = [], []
+    for it in range(5):
+        s = (it * B) % 2048
+        lc.chem_ann_train_step(ann, X[s:s + B].contiguous(), U[s:s + B].contiguous(), bcty[s:s + B].contiguous(),
+                               lr=1e-3, loss_out=loss)
+        la.append(float(loss[0].item()))
+        lc.chem_ann_train_step(ann2, X[s:s + B].contiguous(), U[s:s + B].contiguous(), bcty[s:s + B].contiguous(),
+                               lr=1e-3, loss_out=loss)
+        lb.append(float(loss[0].item()))
+    assert la == lb
