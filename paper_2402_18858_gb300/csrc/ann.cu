@@ -197,6 +197,49 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
         for (int e = 0; e < E; ++e)
           if (eo[e] > 0.0f) res = fmaxf(res, fabsf(en[e] - eo[e]) / eo[e]);
         if (!(res <= elem_tol)) flag |= 4;
+        if (!flag) {
+          // accepted: project onto exact element conservation, min sum_k dY_k^2 / w_k with
+          // w_k = Y_k subject to sum_k c_ke (Y_k + dY_k) = E_old_e (c = composition / W):
+          // dY = diag(w) C^T lam, (C diag(w) C^T) lam = E_old - C Y
+          float Mx[kMaxElem][kMaxElem + 1];
+          for (int a1 = 0; a1 < E; ++a1) {
+            for (int a2 = 0; a2 < E; ++a2) Mx[a1][a2] = 0.0f;
+            Mx[a1][E] = eo[a1] - en[a1];
+          }
+          for (int k = 0; k < K; ++k) {
+            const float wk = yn[k];
+            for (int a1 = 0; a1 < E; ++a1) {
+              const float c1 = (float)m.compW[(size_t)k * E + a1] * wk;
+              for (int a2 = 0; a2 < E; ++a2) Mx[a1][a2] += c1 * (float)m.compW[(size_t)k * E + a2];
+            }
+          }
+          // Gauss-Jordan on the E x E system; elements absent from the cell are left alone
+          float lam[kMaxElem];
+          for (int a1 = 0; a1 < E; ++a1) lam[a1] = 0.0f;
+          bool sing = false;
+          for (int c = 0; c < E; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < E; ++r)
+              if (fabsf(Mx[r][c]) > fabsf(Mx[piv][c])) piv = r;
+            if (!(fabsf(Mx[piv][c]) > 1e-30f)) { sing = true; continue; }
+            if (piv != c)
+              for (int j = 0; j <= E; ++j) { const float t = Mx[c][j]; Mx[c][j] = Mx[piv][j]; Mx[piv][j] = t; }
+            const float d = 1.0f / Mx[c][c];
+            for (int j = 0; j <= E; ++j) Mx[c][j] *= d;
+            for (int r = 0; r < E; ++r) {
+              if (r == c) continue;
+              const float f = Mx[r][c];
+              for (int j = 0; j <= E; ++j) Mx[r][j] -= f * Mx[c][j];
+            }
+          }
+          for (int c = 0; c < E; ++c) lam[c] = (fabsf(Mx[c][c] - 1.0f) < 1e-3f) ? Mx[c][E] : 0.0f;
+          (void)sing;
+          for (int k = 0; k < K; ++k) {
+            float cl = 0.0f;
+            for (int e = 0; e < E; ++e) cl += (float)m.compW[(size_t)k * E + e] * lam[e];
+            yn[k] = fmaxf(yn[k] * (1.0f + cl), 0.0f);
+          }
+        }
         // T from h(T, Y_new) = h0 by Newton's method
         float Tn = T0;
         for (int it = 0; it < 8; ++it) {

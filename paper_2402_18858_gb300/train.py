@@ -1,0 +1,184 @@
+"""Offline pipeline of the learned reaction step (Sec. 2.2, Fig. 2): generate states, integrate
+them over dt with the GPU direct integration to get the targets (the paper uses CVODE), fit the
+normalisation, train the MLP with the library's own kernels, and evaluate the learned step with
+its DI fallback.  Every numerical step runs in libchem's kernels; this module only allocates
+tensors and sequences the calls.
+
+    python -m paper_2402_18858_gb300.train --train-cells 4000000 --epochs 40 --out ann.ckpt
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import tempfile
+import time
+from typing import Dict, Optional
+
+import numpy as np
+import torch
+
+from . import build, chem, workload as wl
+
+HIDDEN_30 = [1600, 800, 400]
+HIDDEN_53 = [2000, 1000, 500]
+
+
+def di_states(gm, m: wl.Mechanism, n: int, seed: int, dt: float, device="cuda", chunk: int = 1 << 20):
+    """Seeded states and their DI results over dt (device tensors, SoA)."""
+    st = wl.make_states(m, n, seed)
+    dev = torch.device(device)
+    T0 = torch.as_tensor(st.T, device=dev)
+    p = torch.as_tensor(st.p, device=dev)
+    Y0 = torch.as_tensor(st.Y, device=dev)
+    T1, Y1 = T0.clone(), Y0.clone()
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = torch.zeros(chem.chem_workspace_bytes(gm, n), dtype=torch.uint8, device=dev)
+    chem.chem_step_di(gm, dt, T1, p, Y1, status, workspace=ws)
+    torch.cuda.synchronize()
+    return dict(T0=T0, p=p, Y0=Y0, T1=T1, Y1=Y1, status=status, states=st)
+
+
+def prepare(ann, data, fit: bool = True):
+    """Normalisation (if fit), BF16 features, raw Box-Cox inputs and normalised targets."""
+    ok = data["status"] == 0
+    T0, p, Y0, Y1 = data["T0"], data["p"], data["Y0"], data["Y1"]
+    if not bool(ok.all()):
+        keep = torch.nonzero(ok).flatten()
+        T0, p = T0[keep].contiguous(), p[keep].contiguous()
+        Y0, Y1 = Y0[:, keep].contiguous(), Y1[:, keep].contiguous()
+    n = T0.numel()
+    if fit:
+        chem.chem_ann_fit_norm(ann, T0, p, Y0, Y1)
+    X = torch.empty((n, 64), dtype=torch.bfloat16, device=T0.device)
+    bcty = torch.empty((n, ann.n_out), dtype=torch.float32, device=T0.device)
+    U = torch.empty((n, ann.n_out_pad), dtype=torch.float32, device=T0.device)
+    chem.chem_ann_features(ann, T0, p, Y0, X, bcty=bcty)
+    chem.chem_ann_targets(ann, Y0, Y1, U)
+    torch.cuda.synchronize()
+    return X, bcty, U
+
+
+def train(ann, X, bcty, U, epochs: int = 20, batch: int = 8192, lr: float = 1e-3, lr_min: float = 2e-5,
+          w_data: float = 1.0, w_mass: float = 0.1, log_every: int = 0) -> Dict:
+    """Adam over minibatches (contiguous slices, offset each epoch), cosine learning rate."""
+    n = X.shape[0] - X.shape[0] % 8
+    batch = min(batch, n) - min(batch, n) % 8
+    steps_per_epoch = max(1, n // batch)
+    total = epochs * steps_per_epoch
+    loss = torch.zeros(3, dtype=torch.float32, device=X.device)
+    hist = []
+    t0 = time.perf_counter()
+    step = 0
+    for e in range(epochs):
+        off = (e * 7919 * 8) % max(n - batch * steps_per_epoch + 1, 1)
+        for s in range(steps_per_epoch):
+            a = off + s * batch
+            cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / max(total - 1, 1)))
+            chem.chem_ann_train_step(ann, X[a:a + batch], U[a:a + batch], bcty[a:a + batch], lr=cur,
+                                     w_data=w_data, w_mass=w_mass, loss_out=loss)
+            step += 1
+            if log_every and step % log_every == 0:
+                hist.append((step, float(loss[1].item())))
+        hist.append((step, float(loss[1].item())))
+    torch.cuda.synchronize()
+    if chem.chem_ann_error(ann) != 0:
+        raise RuntimeError("tensor-core pipeline timed out during training")
+    return dict(steps=step, seconds=time.perf_counter() - t0, loss_history=hist,
+                samples_per_s=step * batch / (time.perf_counter() - t0))
+
+
+def errors(T, Y, Tref, Yref, ok=None) -> Dict:
+    """T error (max, p99) and per-species RMS normalised by the reference range (reading 13)."""
+    T, Y, Tref, Yref = (x.cpu().numpy() if torch.is_tensor(x) else x for x in (T, Y, Tref, Yref))
+    if ok is not None:
+        T, Y, Tref, Yref = T[ok], Y[:, ok], Tref[ok], Yref[:, ok]
+    dT = np.abs(T - Tref)
+    rng = Yref.max(axis=1) - Yref.min(axis=1)
+    rms = np.sqrt(((Y - Yref) ** 2).mean(axis=1)) / np.where(rng > 0, rng, 1.0)
+    return dict(T_max_K=float(dT.max()) if dT.size else 0.0, T_p99_K=float(np.percentile(dT, 99)) if dT.size else 0.0,
+                species_nrms_max=float(rms.max()) if rms.size else 0.0,
+                species_nrms_mean=float(rms.mean()) if rms.size else 0.0)
+
+
+def evaluate(gm, ann, data, dt: float, repeats: int = 3, **ann_opts) -> Dict:
+    """ANN+fallback vs DI on the same cells: error (vs the DI result, itself within 1e-6 of
+    the FP64 oracle) and throughput (CUDA events, best of `repeats`)."""
+    T0, p, Y0, T1, Y1 = data["T0"], data["p"], data["Y0"], data["T1"], data["Y1"]
+    n = T0.numel()
+    dev = T0.device
+    T, Y = T0.clone(), Y0.clone()
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = torch.empty(chem.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device=dev)
+    dws = torch.zeros(chem.chem_workspace_bytes(gm, n), dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+    best_ann, best_di = 1e30, 1e30
+    for _ in range(repeats):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        chem.chem_step_ann(gm, ann, dt, T, p, Y, status, ws, **ann_opts)
+        e1.record(s)
+        torch.cuda.synchronize()
+        best_ann = min(best_ann, e0.elapsed_time(e1))
+    st = status.cpu().numpy()
+    Ta, Ya = T.clone(), Y.clone()
+    for _ in range(max(1, repeats - 1)):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        st_di = torch.empty(n, dtype=torch.int32, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        chem.chem_step_di(gm, dt, T, p, Y, st_di, workspace=dws)
+        e1.record(s)
+        torch.cuda.synchronize()
+        best_di = min(best_di, e0.elapsed_time(e1))
+    ok_ref = data["status"].cpu().numpy() == 0
+    learned = (st == 0) & ok_ref
+    out = dict(cells=n, fallback_fraction=float((st != 0).mean()), ann_ms=best_ann, di_ms=best_di,
+               ann_cells_per_s=n / (best_ann * 1e-3), di_cells_per_s=n / (best_di * 1e-3),
+               speedup_vs_di=best_di / best_ann, failed=int(((st != 0) & (st != 5)).sum()))
+    out["all_cells"] = errors(Ta, Ya, T1, Y1, ok_ref)
+    out["learned_cells"] = errors(Ta, Ya, T1, Y1, learned)
+    ident = errors(T0, Y0, T1, Y1, ok_ref)     # the state left unchanged, for scale
+    out["identity_map"] = ident
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kind", default="c_30")
+    ap.add_argument("--mech-seed", type=int, default=1)
+    ap.add_argument("--train-cells", type=int, default=4_000_000)
+    ap.add_argument("--eval-cells", type=int, default=2_000_000)
+    ap.add_argument("--dt", type=float, default=5e-6)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--eval-seed", type=int, default=3)
+    ap.add_argument("--out", default="")
+    args = ap.parse_args()
+    build.build()
+    m = wl.make_mechanism(args.kind, args.mech_seed)
+    path = wl.mechanism_file(args.kind, args.mech_seed, os.path.join(tempfile.gettempdir(), "chem_mech"))
+    gm = chem.chem_load_mech(path)
+    ann = chem.chem_ann_create(gm, HIDDEN_30 if m.n_species <= 32 else HIDDEN_53, seed=args.seed)
+    t0 = time.perf_counter()
+    data = di_states(gm, m, args.train_cells, args.seed, args.dt)
+    gen_s = time.perf_counter() - t0
+    X, bcty, U = prepare(ann, data)
+    del data
+    tr = train(ann, X, bcty, U, epochs=args.epochs, batch=args.batch, lr=args.lr)
+    if args.out:
+        chem.chem_ann_save(ann, args.out)
+    del X, bcty, U
+    ev = evaluate(gm, ann, di_states(gm, m, args.eval_cells, args.eval_seed, args.dt), args.dt)
+    tr.pop("loss_history", None)
+    print(json.dumps(dict(data_generation_s=gen_s, train=tr, eval=ev)))
+
+
+if __name__ == "__main__":
+    main()
