@@ -193,7 +193,8 @@ int chem_ann_error(chem_ann ann, int* host_err);
 
 typedef struct {
   double range_margin;  /* inputs outside [min - m (max-min), max + m (max-min)] fall back (0.05) */
-  double elem_tol;      /* max relative element-moles change accepted (1e-3) */
+  double elem_tol;      /* max relative change of element moles accepted before the prediction
+                           is projected onto exact element conservation (1e-2) */
   double T_min, T_max;  /* accepted new temperature range (250, 3500 K) */
   double dT_max;        /* if > 0, |T_new - T| above it falls back */
   int no_fallback;      /* 1: flagged cells keep their input state (status 5), no DI */
@@ -201,15 +202,61 @@ typedef struct {
   chem_di_opts di;      /* options of the fallback direct integration */
 } chem_ann_opts;
 
-/* Learned chemistry step for n cells in place (layout as chem_step_di): features, the MLP
+/* Learned chemistry step for n cells in place (layout and idx as chem_step_di: NULL, or the
+ * n cell columns to process; status[] is per entry): features, the MLP
  * on the tensor cores, the new state (inverse Box-Cox, renormalisation, T from enthalpy
  * conservation by Newton's method) and its checks; flagged cells are integrated by DI
  * (status CHEM_CELL_ANN_FALLBACK when DI succeeded, else DI's code).  Workspace:
  * chem_ann_workspace_bytes(ann, n). */
 int chem_step_ann(chem_mech mech, chem_ann ann, int64_t n, int64_t ld, double dt, double* T,
-                  const double* p, double* Y, const chem_ann_opts* opts, int32_t* status,
-                  void* workspace, size_t ws_bytes, chem_stream stream);
+                  const double* p, double* Y, const int32_t* idx, const chem_ann_opts* opts,
+                  int32_t* status, void* workspace, size_t ws_bytes, chem_stream stream);
 size_t chem_ann_workspace_bytes(chem_ann ann, int64_t n);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Serving loop: continuous batching of chemistry-step requests (the paper keeps fields      */
+/* device-resident and bounds GPU memory with a dynamic inference batch, Sec. 2.1)          */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct chem_server_s* chem_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;  /* device memory the server may hold (arenas + workspaces) */
+  int n_streams;            /* concurrent batches in flight (1..16) */
+  int max_batch_cells;      /* cells per launch and per request (index-list capacity) */
+  double starvation_s;      /* > 0: once the oldest waiting request has waited this long,
+                               nothing newer is admitted past it */
+} chem_server_opts;
+
+typedef struct {
+  int64_t submitted, completed, failed, cells, batches;
+  double mean_batch_requests;
+  double p50_ms, p99_ms, mean_ms, max_ms;   /* latency: submit -> results in host memory */
+  double wall_s, cells_per_s, hbm_bytes;
+} chem_server_stats;
+
+/* A background host thread admits requests into per-class device arenas (first-fit column
+ * ranges within the HBM budget), launches one batch per idle stream over all admitted
+ * requests of the oldest waiting request's class, mode and dt (index list), copies results
+ * back and frees the columns.  Host arrays passed to chem_server_submit must stay valid until
+ * the request completes (pinned memory gives asynchronous copies).  Per-cell results do not
+ * depend on the batch composition. */
+int chem_server_create(const chem_server_opts* opts, chem_server* out);
+/* Register a class: a mechanism (and optionally a trained ANN for mode 1) with an arena of
+ * capacity_cells columns.  Classes are added before the first submit. */
+int chem_server_add_class(chem_server server, chem_mech mech, chem_ann ann, int64_t capacity_cells,
+                          int* class_id);
+/* Queue one request: mode 0 = direct integration, 1 = learned step with fallback; n cells
+ * of host SoA state T[n], p[n], Y[K][n] (species-major, ld = n); results to T_out, Y_out,
+ * status_out (host).  Non-blocking. */
+int chem_server_submit(chem_server server, int class_id, int mode, double dt, int64_t n,
+                       const double* T, const double* p, const double* Y, double* T_out,
+                       double* Y_out, int32_t* status_out, int64_t* request_id);
+/* Block until the request completes or timeout_s passes; *done = 1 if complete, *result =
+ * the request's API result (CHEM_OK, or the error code of its launch). */
+int chem_server_wait(chem_server server, int64_t request_id, double timeout_s, int* done,
+                     int* result);
+int chem_server_get_stats(chem_server server, chem_server_stats* stats);
+void chem_server_free(chem_server server);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Mixture thermo and transport properties (Sec. 2.1)                                        */

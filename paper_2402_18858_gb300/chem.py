@@ -244,8 +244,8 @@ def _ann_sigs():
     L.chem_ann_save.argtypes = [vp, C.c_char_p]
     L.chem_ann_load.argtypes = [vp, C.c_char_p, C.POINTER(vp)]
     L.chem_ann_error.argtypes = [vp, C.POINTER(i32)]
-    L.chem_step_ann.argtypes = [vp, vp, i64, i64, C.c_double, vp, vp, vp, C.POINTER(AnnOpts), vp, vp,
-                                C.c_size_t, vp]
+    L.chem_step_ann.argtypes = [vp, vp, i64, i64, C.c_double, vp, vp, vp, vp, C.POINTER(AnnOpts), vp,
+                                vp, C.c_size_t, vp]
     L.chem_ann_workspace_bytes.argtypes = [vp, i64]
     L.chem_ann_workspace_bytes.restype = C.c_size_t
     _ann_sigs_done = True
@@ -375,14 +375,115 @@ def chem_ann_error(a: Ann) -> int:
     return v.value
 
 
-def chem_step_ann(m: Mech, a: Ann, dt: float, T, p, Y, status, workspace, range_margin=0.05,
-                  elem_tol=1e-3, T_min=250.0, T_max=3500.0, dT_max=0.0, no_fallback=False,
+def chem_step_ann(m: Mech, a: Ann, dt: float, T, p, Y, status, workspace, idx=None, range_margin=0.05,
+                  elem_tol=1e-2, T_min=250.0, T_max=3500.0, dT_max=0.0, no_fallback=False,
                   di_rtol=0.0, di_atol_Y=0.0, n: Optional[int] = None, stream=None) -> None:
     ld = _ld(Y, m)
-    n = ld if n is None else n
+    if n is None:
+        n = idx.numel() if idx is not None else ld
     o = AnnOpts(range_margin, elem_tol, T_min, T_max, dT_max, int(no_fallback), 0,
                 DiOpts(di_rtol, di_atol_Y, 0.0, 0.0, 0, 0))
     _check(lib().chem_step_ann(m.handle, a.handle, n, ld, float(dt), _ptr(T, torch.float64),
-                               _ptr(p, torch.float64), _ptr(Y, torch.float64), C.byref(o),
+                               _ptr(p, torch.float64), _ptr(Y, torch.float64), _ptr(idx, torch.int32),
+                               C.byref(o),
                                _ptr(status, torch.int32), _ptr(workspace),
                                workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------
+# serving loop
+# ------------------------------------------------------------------------------------------
+class ServerOpts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("n_streams", C.c_int), ("max_batch_cells", C.c_int),
+                ("starvation_s", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("cells", C.c_int64), ("batches", C.c_int64), ("mean_batch_requests", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("max_ms", C.c_double), ("wall_s", C.c_double), ("cells_per_s", C.c_double),
+                ("hbm_bytes", C.c_double)]
+
+
+_srv_sigs_done = False
+
+
+def _srv_sigs():
+    global _srv_sigs_done
+    if _srv_sigs_done:
+        return
+    L = lib()
+    vp = C.c_void_p
+    L.chem_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(vp)]
+    L.chem_server_add_class.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(C.c_int)]
+    L.chem_server_submit.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_int64, vp, vp, vp, vp, vp, vp,
+                                     C.POINTER(C.c_int64)]
+    L.chem_server_wait.argtypes = [vp, C.c_int64, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.chem_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    L.chem_server_free.argtypes = [vp]
+    L.chem_server_free.restype = None
+    _srv_sigs_done = True
+
+
+class Server:
+    """A chemistry-step server (owns a chem_server handle and keeps its host buffers alive)."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+        self.keep = {}
+        self.classes = []
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().chem_server_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def chem_server_create(hbm_budget_bytes: int, n_streams: int = 2, max_batch_cells: int = 1 << 21,
+                       starvation_s: float = 0.0) -> Server:
+    _srv_sigs()
+    o = ServerOpts(int(hbm_budget_bytes), int(n_streams), int(max_batch_cells), float(starvation_s))
+    h = C.c_void_p()
+    _check(lib().chem_server_create(C.byref(o), C.byref(h)))
+    return Server(h.value)
+
+
+def chem_server_add_class(sv: Server, m: Mech, ann=None, capacity_cells: int = 1 << 20) -> int:
+    cid = C.c_int()
+    _check(lib().chem_server_add_class(sv.handle, m.handle, ann.handle if ann is not None else None,
+                                       int(capacity_cells), C.byref(cid)))
+    sv.classes.append((m, ann))
+    return cid.value
+
+
+def chem_server_submit(sv: Server, class_id: int, mode: int, dt: float, T, p, Y, T_out, Y_out, status_out) -> int:
+    """Host numpy/torch-CPU arrays (contiguous, float64 / int32); kept alive by the server."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(a) for a in (T, p, Y)]
+    for a in (T_out, Y_out, status_out):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("output arrays must be contiguous")
+    rid = C.c_int64()
+    n = arrs[0].shape[0]
+    _check(lib().chem_server_submit(sv.handle, int(class_id), int(mode), float(dt), n,
+                                    *[a.ctypes.data_as(C.c_void_p) for a in arrs],
+                                    T_out.ctypes.data_as(C.c_void_p), Y_out.ctypes.data_as(C.c_void_p),
+                                    status_out.ctypes.data_as(C.c_void_p), C.byref(rid)))
+    sv.keep[rid.value] = (arrs, T_out, Y_out, status_out)
+    return rid.value
+
+
+def chem_server_wait(sv: Server, request_id: int, timeout_s: float = 60.0):
+    done, res = C.c_int(), C.c_int()
+    _check(lib().chem_server_wait(sv.handle, int(request_id), float(timeout_s), C.byref(done), C.byref(res)))
+    return bool(done.value), res.value
+
+
+def chem_server_stats(sv: Server) -> dict:
+    st = ServerStats()
+    _check(lib().chem_server_get_stats(sv.handle, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in ServerStats._fields_}

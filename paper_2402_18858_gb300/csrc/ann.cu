@@ -84,18 +84,20 @@ __device__ __forceinline__ float raw_feature(int j, int64_t i, int64_t ld, const
 
 // normalised BF16 features X[i][0..63]; range flag (bit 1) against the training min/max
 __global__ void features_kernel(int64_t n, int64_t ld, const double* T, const double* p, const double* Y, int n_in,
-                                const float* norm, float margin, bf16* X, int32_t* flags, float* bcty, int K) {
+                                const float* norm, float margin, bf16* X, int32_t* flags, float* bcty, int K,
+                                const int32_t* idx) {
   const float* mean = norm;
   const float* sd = norm + n_in;
   const float* mn = norm + 2 * n_in;
   const float* mx = norm + 3 * n_in;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int flag = 0;
+    const int64_t col = idx ? (int64_t)idx[i] : i;
     __align__(16) bf16 row[kInPad];
     for (int j = 0; j < kInPad; ++j) {
       float v = 0.0f;
       if (j < n_in) {
-        const float r = raw_feature(j, i, ld, T, p, Y);
+        const float r = raw_feature(j, col, ld, T, p, Y);
         const float span = mx[j] - mn[j];
         if (!(r >= mn[j] - margin * span && r <= mx[j] + margin * span)) flag = 1;
         v = (r - mean[j]) / sd[j];
@@ -161,10 +163,13 @@ __global__ void stats_partial_kernel(int64_t n, int64_t ld, const double* T, con
 // network output -> new state; flags: 1 range, 2 non-finite, 4 element residual, 8 T range, 16 |dT|
 __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const double* p, double* Y,
                               const float* U, int n_out_pad, const float* out_mean, const float* out_sd,
-                              int32_t* flags, int32_t* status, float elem_tol, float Tmin, float Tmax, float dTmax) {
+                              int32_t* flags, int32_t* status, float elem_tol, float Tmin, float Tmax, float dTmax,
+                              const int32_t* idx) {
   const int K = m.K, E = m.E;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int flag = flags[i];
+  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < n;
+       slot += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx ? (int64_t)idx[slot] : slot;   // cell column; U, flags, status by slot
+    int flag = flags[slot];
     if (flag == 0) {
       float yn[CHEM_MAX_SPECIES];
       float eo[kMaxElem], en[kMaxElem];
@@ -180,7 +185,7 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
                           + (float)a[10] / T0;
         h0 += (float)(y * m.invW[k]) * hRT;
         for (int e = 0; e < E; ++e) eo[e] += (float)(y * m.compW[(size_t)k * E + e]);
-        const float z = bct_f(y) + U[(size_t)i * n_out_pad + k] * out_sd[k] + out_mean[k];
+        const float z = bct_f(y) + U[(size_t)slot * n_out_pad + k] * out_sd[k] + out_mean[k];
         const float v = ibct_f(z);
         yn[k] = v;
         ysum += v;
@@ -216,12 +221,11 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
           // Gauss-Jordan on the E x E system; elements absent from the cell are left alone
           float lam[kMaxElem];
           for (int a1 = 0; a1 < E; ++a1) lam[a1] = 0.0f;
-          bool sing = false;
           for (int c = 0; c < E; ++c) {
             int piv = c;
             for (int r = c + 1; r < E; ++r)
               if (fabsf(Mx[r][c]) > fabsf(Mx[piv][c])) piv = r;
-            if (!(fabsf(Mx[piv][c]) > 1e-30f)) { sing = true; continue; }
+            if (!(fabsf(Mx[piv][c]) > 1e-30f)) continue;   // element absent from the cell
             if (piv != c)
               for (int j = 0; j <= E; ++j) { const float t = Mx[c][j]; Mx[c][j] = Mx[piv][j]; Mx[piv][j] = t; }
             const float d = 1.0f / Mx[c][c];
@@ -233,7 +237,6 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
             }
           }
           for (int c = 0; c < E; ++c) lam[c] = (fabsf(Mx[c][c] - 1.0f) < 1e-3f) ? Mx[c][E] : 0.0f;
-          (void)sing;
           for (int k = 0; k < K; ++k) {
             float cl = 0.0f;
             for (int e = 0; e < E; ++e) cl += (float)m.compW[(size_t)k * E + e] * lam[e];
@@ -267,8 +270,8 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
         }
       }
     }
-    flags[i] = flag;
-    status[i] = flag ? CHEM_CELL_ANN_FALLBACK : CHEM_CELL_OK;
+    flags[slot] = flag;
+    status[slot] = flag ? CHEM_CELL_ANN_FALLBACK : CHEM_CELL_OK;
   }
 }
 
@@ -302,7 +305,8 @@ __global__ void compact_scan_kernel(int nb, int32_t* blk_count, int32_t* total) 
   }
 }
 
-__global__ void compact_write_kernel(int64_t n, const int32_t* status, const int32_t* blk_off, int32_t* idx) {
+__global__ void compact_write_kernel(int64_t n, const int32_t* status, const int32_t* blk_off, int32_t* slots,
+                                     int32_t* cols, const int32_t* idx) {
   __shared__ int ws[32];
   const int64_t i = (int64_t)blockIdx.x * kCompactBlock + threadIdx.x;
   const int f = (i < n && status[i] != 0) ? 1 : 0;
@@ -319,15 +323,19 @@ __global__ void compact_write_kernel(int64_t n, const int32_t* status, const int
     }
   }
   __syncthreads();
-  if (f) idx[blk_off[blockIdx.x] + ws[w] + __popc(b & ((1u << lane) - 1u))] = (int32_t)i;
+  if (f) {
+    const int q = blk_off[blockIdx.x] + ws[w] + __popc(b & ((1u << lane) - 1u));
+    slots[q] = (int32_t)i;
+    cols[q] = idx ? idx[i] : (int32_t)i;
+  }
 }
 
 // DI statuses of the fallback cells back to the cells: 5 when DI succeeded, else DI's code
-__global__ void scatter_status_kernel(int64_t nmax, const int32_t* n_dev, const int32_t* idx, const int32_t* st_slot,
+__global__ void scatter_status_kernel(int64_t nmax, const int32_t* n_dev, const int32_t* slots, const int32_t* st_slot,
                                       int32_t* status) {
   const int64_t nf = min(nmax, (int64_t)*n_dev);
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nf; s += (int64_t)gridDim.x * blockDim.x)
-    status[idx[s]] = st_slot[s] == CHEM_CELL_OK ? CHEM_CELL_ANN_FALLBACK : st_slot[s];
+    status[slots[s]] = st_slot[s] == CHEM_CELL_OK ? CHEM_CELL_ANN_FALLBACK : st_slot[s];
 }
 
 // training loss (Eqs. 8-9) and its gradient w.r.t. the network output
@@ -674,7 +682,7 @@ int chem_ann_features(chem_ann a, int64_t n, int64_t ld, const double* T, const 
   if (n < 0 || ld < n || (n > 0 && (!T || !p || !Y || !X))) return set_error(CHEM_E_ARG, "chem_ann_features: bad arguments");
   if (n == 0) return CHEM_OK;
   features_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, ld, T, p, Y, a->n_in, a->norm, 0.0f,
-                                                                     (bf16*)X, nullptr, bcty, a->K);
+                                                                     (bf16*)X, nullptr, bcty, a->K, nullptr);
   return cuda_check(cudaGetLastError(), "features_kernel launch");
 }
 
@@ -730,7 +738,7 @@ size_t chem_ann_workspace_bytes(chem_ann a, int64_t n) {
   s += (size_t)n * kInPad * 2 + 256;                 // X
   s += (size_t)n * a->n_out_pad * 4 + 256;           // U
   for (int l = 0; l < a->L - 1; ++l) s += (size_t)mc * a->dims[l + 1] * 2 + 256;
-  s += 3 * ((size_t)n * 4 + 256);                     // flags, idx, DI slot status
+  s += 4 * ((size_t)n * 4 + 256);                     // flags, slots, cell columns, DI slot status
   s += ((size_t)(n / kCompactBlock + 2) * 4 + 256) + 256 + 256;   // block counts, total, queue
   return s;
 }
@@ -768,8 +776,8 @@ int chem_ann_error(chem_ann a, int* host_err) {
 }
 
 int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, double* T, const double* p,
-                  double* Y, const chem_ann_opts* opts, int32_t* status, void* workspace, size_t ws_bytes,
-                  chem_stream stream) {
+                  double* Y, const int32_t* idx_in, const chem_ann_opts* opts, int32_t* status, void* workspace,
+                  size_t ws_bytes, chem_stream stream) {
   int rc = check_ann(a);
   if (rc) return rc;
   if (!mech || mech != a->mech) return set_error(CHEM_E_ARG, "chem_step_ann: the ANN belongs to another mechanism");
@@ -782,7 +790,7 @@ int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, 
   chem_ann_opts o{};
   if (opts) o = *opts;
   if (!(o.range_margin >= 0)) o.range_margin = 0.05;
-  if (!(o.elem_tol > 0)) o.elem_tol = 1e-3;
+  if (!(o.elem_tol > 0)) o.elem_tol = 1e-2;
   if (!(o.T_min > 0)) o.T_min = 250.0;
   if (!(o.T_max > 0)) o.T_max = 3500.0;
   di_fill_defaults(o.di);
@@ -802,7 +810,9 @@ int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, 
   }
   int32_t* flags = (int32_t*)(w + off);
   off = al(off + (size_t)n * 4);
-  int32_t* idx = (int32_t*)(w + off);
+  int32_t* slots = (int32_t*)(w + off);
+  off = al(off + (size_t)n * 4);
+  int32_t* cols = (int32_t*)(w + off);
   off = al(off + (size_t)n * 4);
   int32_t* st_slot = (int32_t*)(w + off);
   off = al(off + (size_t)n * 4);
@@ -815,7 +825,7 @@ int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, 
 
   // 1. features and range flags
   features_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, ld, T, p, Y, a->n_in, a->norm, (float)o.range_margin, X, flags,
-                                                  nullptr, a->K);
+                                                  nullptr, a->K, idx_in);
   if ((rc = cuda_check(cudaGetLastError(), "features_kernel launch"))) return rc;
   // 2. MLP on the tensor cores, chunk by chunk
   for (int64_t r0 = 0; r0 < n; r0 += mc) {
@@ -826,16 +836,16 @@ int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, 
   const float* om = a->norm + 4 * a->n_in;
   update_kernel<<<grid_for(n, 128), 128, 0, s>>>(a->dm, n, ld, T, p, Y, U, a->n_out_pad, om, om + a->n_out, flags,
                                                 status, (float)o.elem_tol, (float)o.T_min, (float)o.T_max,
-                                                (float)o.dT_max);
+                                                (float)o.dT_max, idx_in);
   if ((rc = cuda_check(cudaGetLastError(), "update_kernel launch"))) return rc;
   if (!o.no_fallback) {
     // 4. compaction of flagged cells (deterministic order) and direct integration of those
     compact_count_kernel<<<nb, kCompactBlock, 0, s>>>(n, status, blk);
     compact_scan_kernel<<<1, 32, 0, s>>>(nb, blk, nflag);
-    compact_write_kernel<<<nb, kCompactBlock, 0, s>>>(n, status, blk, idx);
+    compact_write_kernel<<<nb, kCompactBlock, 0, s>>>(n, status, blk, slots, cols, idx_in);
     if ((rc = cuda_check(cudaMemsetAsync(queue, 0, 4, s), "queue reset"))) return rc;
-    if ((rc = launch_di(a->dm, n, ld, dt, T, p, Y, idx, o.di, st_slot, nullptr, queue, s, nflag))) return rc;
-    scatter_status_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, nflag, idx, st_slot, status);
+    if ((rc = launch_di(a->dm, n, ld, dt, T, p, Y, cols, o.di, st_slot, nullptr, queue, s, nflag))) return rc;
+    scatter_status_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, nflag, slots, st_slot, status);
     if ((rc = cuda_check(cudaGetLastError(), "fallback launch"))) return rc;
   }
   return CHEM_OK;
