@@ -166,6 +166,135 @@ def run_reference(args, cfg, m, m_path):
 
 
 # ------------------------------------------------------------------------------------------
+# learned step (ANN + DI fallback): train on DI-generated states, then time inference
+# ------------------------------------------------------------------------------------------
+ANN_WORKLOAD = "ann_c_30sp_2m"
+ANN_ELEM_TOL = 1e-2
+
+
+def mlp_flops_per_cell(dims) -> int:
+    return sum(2 * dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+
+
+def run_ann(args, m, gm, di_rate):
+    import torch
+    from paper_2402_18858_gb300 import chem, train as tr
+    dt = wl.WORKLOADS[WORKLOAD]["dt"]
+    t0 = time.perf_counter()
+    data = tr.di_states(gm, m, args.ann_train_cells, 2, dt)
+    gen_s = time.perf_counter() - t0
+    ann = chem.chem_ann_create(gm, tr.HIDDEN_30, seed=2)
+    X, bcty, U = tr.prepare(ann, data)
+    del data
+    trn = tr.train(ann, X, bcty, U, epochs=args.ann_epochs, batch=8192, lr=1e-3)
+    del X, bcty, U
+    # accuracy against DI on held-out cells (DI is within 1e-6 of the FP64 oracle)
+    ev_data = tr.di_states(gm, m, 100_000, 3, dt)
+    ev = tr.evaluate(gm, ann, ev_data, dt, repeats=1, elem_tol=ANN_ELEM_TOL)
+    del ev_data
+    # throughput of ANN + fallback on the full inference batch (2 M cells), and the MLP alone
+    n = args.ann_cells
+    st = wl.make_states(m, n, 3)
+    dev = torch.device("cuda")
+    T0 = torch.as_tensor(st.T, device=dev)
+    p = torch.as_tensor(st.p, device=dev)
+    Y0 = torch.as_tensor(st.Y, device=dev)
+    T, Y = T0.clone(), Y0.clone()
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = torch.empty(chem.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+    best, best_mlp = 1e30, 1e30
+    X = torch.empty((n, 64), dtype=torch.bfloat16, device=dev)
+    Uo = torch.empty((n, ann.n_out_pad), dtype=torch.float32, device=dev)
+    chem.chem_ann_features(ann, T0, p, Y0, X)
+    for _ in range(3):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(s)
+        chem.chem_step_ann(gm, ann, dt, T, p, Y, status, ws, elem_tol=ANN_ELEM_TOL)
+        e1.record(s)
+        chem.chem_ann_forward(ann, X, Uo, ws)
+        e2.record(s)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+        best_mlp = min(best_mlp, e1.elapsed_time(e2))
+    fb = float((status != 0).float().mean().item())
+    mlp_tf = mlp_flops_per_cell(ann.dims) * n / (best_mlp * 1e-3) / 1e12
+    rate = n / (best * 1e-3)
+    report = {"workload": f"{ANN_WORKLOAD}: MLP {ann.dims}, BF16 tcgen05, {n} cells, dt {dt}",
+              "train_cells": args.ann_train_cells, "train_epochs": args.ann_epochs,
+              "data_generation_s": gen_s, "train_s": trn["seconds"], "train_samples_per_s": trn["samples_per_s"],
+              "cells_per_s": rate, "ms": best, "fallback_fraction": fb, "speedup_vs_di": rate / di_rate,
+              "elem_tol": ANN_ELEM_TOL,
+              "error_vs_di_100k_heldout": {"fallback_fraction": ev["fallback_fraction"], **ev["all_cells"]},
+              "mlp_ms": best_mlp, "mlp_tflops": mlp_tf, "mlp_cells_per_s": n / (best_mlp * 1e-3)}
+    roof = {"bound": "tensor", "achieved": mlp_tf, "peak": 1937.2, "unit": "TFLOP/s", "frac": mlp_tf / 1937.2,
+            "traffic": None, "kernel": "gemm_bf16_kernel (MLP forward, 2 M cells)",
+            "peak_source": "MEASURED_PEAKS bf16_tflops (burst)"}
+    return {"report": report, "roofline": roof, "ann": ann}
+
+
+# ------------------------------------------------------------------------------------------
+# serving: Poisson arrivals of mixed requests through continuous batching
+# ------------------------------------------------------------------------------------------
+def run_serve(args, m30, g30, ann_leg, di_rate30):
+    import torch
+    from paper_2402_18858_gb300 import chem, train as tr
+    m9 = wl.make_mechanism("h2_9", 0)
+    g9 = chem.chem_load_mech(wl.mechanism_file("h2_9", 0, MECH_DIR))
+    # 9-species classes: a small learned step trained the same way
+    d9 = tr.di_states(g9, m9, 200_000, 12, 1e-6)
+    a9 = chem.chem_ann_create(g9, [256, 128], seed=4)
+    X, bcty, U = tr.prepare(a9, d9)
+    tr.train(a9, X, bcty, U, epochs=10, batch=8192, lr=1e-3)
+    del X, bcty, U
+    ev9 = tr.evaluate(g9, a9, d9, 1e-6, repeats=1)
+    di_rate9 = ev9["di_cells_per_s"]
+    a30 = ann_leg["ann"] if ann_leg else None
+    rate_ann30 = ann_leg["report"]["cells_per_s"] if ann_leg else di_rate30
+    rng = np.random.default_rng(4)
+    R = args.serve_requests
+    lo, hi = 1e3, 5e4
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), R)).astype(int)
+    kind = rng.random(R) < 0.5            # True: 30 species
+    mode = (rng.random(R) < 0.5).astype(int)
+    if a30 is None:
+        mode[kind] = 0
+    svc = np.where(kind, np.where(mode == 1, 1.0 / rate_ann30, 1.0 / di_rate30),
+                   np.where(mode == 1, 1.0 / ev9["ann_cells_per_s"], 1.0 / di_rate9)) * sizes
+    lam = 0.7 / svc.mean()                 # arrivals at 70 % of the measured capacity
+    gaps = rng.exponential(1.0 / lam, R)
+    sv = chem.chem_server_create(hbm_budget_bytes=8 << 30, n_streams=2, max_batch_cells=1 << 20)
+    c30 = chem.chem_server_add_class(sv, g30, a30, capacity_cells=1 << 20)
+    c9 = chem.chem_server_add_class(sv, g9, a9, capacity_cells=1 << 20)
+    reqs = []
+    t0 = time.perf_counter()
+    for i in range(R):
+        mm, cls, dt = (m30, c30, wl.WORKLOADS[WORKLOAD]["dt"]) if kind[i] else (m9, c9, 1e-6)
+        st = wl.make_states(mm, int(sizes[i]), 50_000 + i)
+        To = np.empty(sizes[i])
+        Yo = np.empty((mm.n_species, sizes[i]))
+        so = np.empty(sizes[i], dtype=np.int32)
+        target = t0 + gaps[:i + 1].sum()
+        while time.perf_counter() < target:
+            time.sleep(min(1e-3, max(0.0, target - time.perf_counter())))
+        reqs.append(chem.chem_server_submit(sv, cls, int(mode[i]), dt, st.T, st.p, st.Y, To, Yo, so))
+    for r in reqs:
+        done, res = chem.chem_server_wait(sv, r, 600.0)
+        if not done or res != 0:
+            raise RuntimeError(f"serving request {r} did not complete ({done}, {res})")
+    stt = chem.chem_server_stats(sv)
+    del sv
+    return {"workload": f"{R} requests, cells log-uniform [{int(lo)}, {int(hi)}], 50/50 9-/30-species, "
+                        f"50/50 DI/ANN, Poisson arrivals at 70 % of measured capacity ({lam:.2f}/s)",
+            "p50_ms": stt["p50_ms"], "p99_ms": stt["p99_ms"], "mean_ms": stt["mean_ms"], "max_ms": stt["max_ms"],
+            "cells_per_s": stt["cells_per_s"], "batches": stt["batches"],
+            "mean_batch_requests": stt["mean_batch_requests"], "wall_s": stt["wall_s"],
+            "failed": stt["failed"]}
+
+
+# ------------------------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -176,6 +305,12 @@ def main():
     ap.add_argument("--ref-cells", type=int, default=1024)
     ap.add_argument("--cpu-cells", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ann", action="store_true", help="skip the learned-step leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--ann-train-cells", type=int, default=500_000)
+    ap.add_argument("--ann-epochs", type=int, default=24)
+    ap.add_argument("--ann-cells", type=int, default=2_000_000)
+    ap.add_argument("--serve-requests", type=int, default=200)
     args = ap.parse_args()
 
     cfg = dict(wl.WORKLOADS[WORKLOAD])
@@ -295,6 +430,10 @@ def main():
     h2d = hT.numel() * 8 + hY.numel() * 8
     d2h = oT.numel() * 8 + oY.numel() * 8 + ost.numel() * 4
 
+    di_rate = N / (di_ms * 1e-3)
+    ann = None if args.no_ann else run_ann(args, m, gm, di_rate)
+    serve = None if (args.no_serve or world > 1) else run_serve(args, m, gm, ann, di_rate)
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
@@ -325,9 +464,12 @@ def main():
                                 "frac": th_gbs / 6780.0, "peak_source": "MEASURED_PEAKS hbm_gbs"},
             "e2e": {"value": N * world / (e2e_ms * 1e-3), "unit": "cells/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 2 * args.steps,  # di_kernel + thermo_kernel per step
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "ann": ann["report"] if ann else None,
+            "tensor_roofline": ann["roofline"] if ann else None,
+            "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -63,6 +63,7 @@ struct WarpMem {
   double* kre;    // I   effective reverse coefficient
   double* aux;    // I   d q / d [M] factor (third-body: q0, Troe: dk/dM (fwd - rev/Kc))
   double* qT;     // I   d q / d T at fixed C
+  double* tr;     // 14 per Troe reaction: exponentials, F_cent, P_r, logs, k, dk/d[M], dln k/dT
   double* invd;   // n   reciprocal pivots
   double* ru;     // 25  step-size change matrix
   int* perm;      // n   row permutation of the LU
@@ -71,16 +72,18 @@ struct WarpMem {
 
 __host__ __device__ inline int pad_ld(int n) { return n | 1; }
 
-// doubles per warp: matrices (optional) + species + reactions + small vectors
-__host__ __device__ inline size_t warp_doubles(int K, int I, int n, bool mats, bool jac) {
+constexpr int kTroeSlots = 14;
+
+// doubles per warp: matrices (optional) + species + reactions + Troe scratch + small vectors
+__host__ __device__ inline size_t warp_doubles(int K, int I, int n, int nT, bool mats, bool jac) {
   size_t ld = pad_ld(n);
   size_t d = (mats ? 2 * (size_t)n * ld : (jac ? (size_t)n * ld : 0));
-  d += 5 * (size_t)K + (jac ? 5 : 1) * (size_t)(I > 0 ? I : 1);
+  d += 5 * (size_t)K + (jac ? 5 : 1) * (size_t)(I > 0 ? I : 1) + (size_t)kTroeSlots * nT;
   d += (size_t)n + 32 + (size_t)(n + 1) / 2 + 2;
   return (d + 1) & ~size_t(1);   // keep 16-byte alignment per warp
 }
 
-__device__ __forceinline__ WarpMem carve(double* base, int K, int I, int n, bool mats, bool jac) {
+__device__ __forceinline__ WarpMem carve(double* base, int K, int I, int n, int nT, bool mats, bool jac) {
   WarpMem w;
   w.ld = pad_ld(n);
   double* p = base;
@@ -103,6 +106,7 @@ __device__ __forceinline__ WarpMem carve(double* base, int K, int I, int n, bool
   } else {
     w.kfe = w.kre = w.aux = w.qT = nullptr;
   }
+  w.tr = p; p += (size_t)kTroeSlots * nT;
   w.invd = p; p += n;
   w.ru = p; p += 32;
   w.perm = (int*)p;
@@ -120,44 +124,85 @@ struct CellSc {
 };
 
 // ------------------------------------------------------------------------------------------
-// Troe falloff (Lindemann form with the Troe broadening factor, Gilbert, Luther & Troe 1983)
+// Troe falloff (Lindemann form with the Troe broadening factor, Gilbert, Luther & Troe 1983),
+// evaluated for all falloff reactions of a cell at once with the transcendental functions
+// spread over the lanes: five exponentials per reaction (k_inf, k_0 and the three F_cent
+// terms), then P_r and F_cent, then the two base-10 logarithms, then F and k.  Results in
+// w.tr: [10] k, [11] dk/d[M], [12] d ln k/dT at fixed [M].
 // ------------------------------------------------------------------------------------------
 template <bool JAC>
-__device__ __forceinline__ double troe_k(const double* __restrict__ tp, const double* __restrict__ et,
-                                         double T, double invT, double lnT, double M, double kinf,
-                                         double dlnkinf, double& dkdM, double& dlnk) {
-  const double k0 = exp_t(tp[0] + tp[1] * lnT - tp[2] * invT, et);
-  const double a = tp[3], iT3 = tp[4], iT1 = tp[5], T2 = tp[6];
-  const double e3 = exp_t(-T * iT3, et), e1 = exp_t(-T * iT1, et);
-  double Fc = (1.0 - a) * e3 + a * e1;
-  double dFc = -(1.0 - a) * iT3 * e3 - a * iT1 * e1;
-  if (tp[7] != 0.0) {
-    const double e2 = exp_t(-T2 * invT, et);
-    Fc += e2;
-    dFc += T2 * invT * invT * e2;
+__device__ __forceinline__ void troe_phase(const DevMech& m, const WarpMem& w, double T, double invT, double lnT,
+                                           double ctot, int lane) {
+  const int nT = m.I - m.n_tb_end;
+  const double* __restrict__ et = m.exptab;
+  for (int t = lane; t < 5 * nT; t += 32) {
+    const int jt = t / 5, q = t - 5 * jt, j = m.n_tb_end + jt;
+    const double* tp = m.troe + 8 * (size_t)j;
+    double arg;
+    if (q == 0) {
+      const double* a = m.arr + 4 * (size_t)j;
+      arg = __ldg(a) + __ldg(a + 1) * lnT - __ldg(a + 2) * invT;
+    } else if (q == 1) {
+      arg = __ldg(tp) + __ldg(tp + 1) * lnT - __ldg(tp + 2) * invT;
+    } else if (q == 2) {
+      arg = -T * __ldg(tp + 4);
+    } else if (q == 3) {
+      arg = -T * __ldg(tp + 5);
+    } else {
+      arg = __ldg(tp + 7) != 0.0 ? -__ldg(tp + 6) * invT : -1e300;   // absent T** term -> 0
+    }
+    w.tr[kTroeSlots * jt + q] = exp_t(arg, et);
   }
-  double Pr = k0 * M / kinf;
-  Pr = fmax(Pr, 1e-300);
-  const double L = log10(Fc);
-  const double c = -0.4 - 0.67 * L;
-  const double nn = 0.75 - 1.27 * L;
-  const double x = log10(Pr) + c;
-  const double den = nn - 0.14 * x;
-  const double f1 = x / den;
-  const double opf = 1.0 + f1 * f1;
-  const double F = exp_t(2.302585092994046 * (L / opf), et);   // 10^(L/opf)
-  const double ipr = 1.0 / (1.0 + Pr);
-  const double k = kinf * Pr * ipr * F;
-  if (JAC) {
-    const double df1dx = nn / (den * den);
-    const double gg = -L * 2.0 * f1 / (opf * opf) * df1dx;          // d log F / d log Pr
-    dkdM = k0 * F * (ipr * ipr + gg * ipr);
-    const double df1dL = df1dx * (-0.67) + (-x / (den * den)) * (-1.27);
-    const double dlogFdL = 1.0 / opf - L * 2.0 * f1 / (opf * opf) * df1dL;
-    const double dlnk0 = tp[1] * invT + tp[2] * invT * invT;
-    dlnk = dlnkinf + (ipr + gg) * (dlnk0 - dlnkinf) + dlogFdL * dFc / Fc;
+  __syncwarp();
+  for (int jt = lane; jt < nT; jt += 32) {
+    const int j = m.n_tb_end + jt;
+    const double* tp = m.troe + 8 * (size_t)j;
+    double* r = w.tr + kTroeSlots * jt;
+    double M = ctot;
+#pragma unroll
+    for (int e = 0; e < kMaxEx; ++e) {
+      const int se = __ldg(m.ex_sp + (size_t)j * kMaxEx + e);
+      if (se >= 0) M += __ldg(m.ex_a + (size_t)j * kMaxEx + e) * w.C[se];
+    }
+    const double a = __ldg(tp + 3);
+    r[5] = (1.0 - a) * r[2] + a * r[3] + r[4];
+    r[6] = fmax(r[1] * M / r[0], 1e-300);
   }
-  return k;
+  __syncwarp();
+  for (int t = lane; t < 2 * nT; t += 32) {
+    const int jt = t >> 1, q = t & 1;
+    w.tr[kTroeSlots * jt + 8 + q] = log10(w.tr[kTroeSlots * jt + 5 + q]);
+  }
+  __syncwarp();
+  for (int jt = lane; jt < nT; jt += 32) {
+    const int j = m.n_tb_end + jt;
+    double* r = w.tr + kTroeSlots * jt;
+    const double kinf = r[0], k0 = r[1], Fc = r[5], Pr = r[6], L = r[8];
+    const double c = -0.4 - 0.67 * L;
+    const double nn = 0.75 - 1.27 * L;
+    const double x = r[9] + c;
+    const double den = nn - 0.14 * x;
+    const double f1 = x / den;
+    const double opf = 1.0 + f1 * f1;
+    const double F = exp_t(2.302585092994046 * (L / opf), et);   // 10^(L/opf)
+    const double ipr = 1.0 / (1.0 + Pr);
+    r[10] = kinf * Pr * ipr * F;
+    if (JAC) {
+      const double* tp = m.troe + 8 * (size_t)j;
+      const double* ar = m.arr + 4 * (size_t)j;
+      const double aa = __ldg(tp + 3), iT3 = __ldg(tp + 4), iT1 = __ldg(tp + 5);
+      const double dFc = -(1.0 - aa) * iT3 * r[2] - aa * iT1 * r[3] + __ldg(tp + 6) * invT * invT * r[4];
+      const double df1dx = nn / (den * den);
+      const double gg = -L * 2.0 * f1 / (opf * opf) * df1dx;          // d log F / d log Pr
+      r[11] = k0 * F * (ipr * ipr + gg * ipr);
+      const double df1dL = df1dx * (-0.67) + (-x / (den * den)) * (-1.27);
+      const double dlogFdL = 1.0 / opf - L * 2.0 * f1 / (opf * opf) * df1dL;
+      const double dlnkinf = __ldg(ar + 1) * invT + __ldg(ar + 2) * invT * invT;
+      const double dlnk0 = __ldg(tp + 1) * invT + __ldg(tp + 2) * invT * invT;
+      r[12] = dlnkinf + (ipr + gg) * (dlnk0 - dlnkinf) + dlogFdL * dFc / Fc;
+    }
+  }
+  __syncwarp();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -224,15 +269,23 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
     }
   }
   __syncwarp();
-  const double P0RT = kP0 / RT, RTP0 = RT / kP0;
+  if (I > m.n_tb_end) troe_phase<JAC>(m, w, T, invT, lnT, ctot, lane);
+  const double P0RT = (kP0 / kR) * invT, RTP0 = RT * (1.0 / kP0);
   for (int j = lane; j < I; j += 32) {
     const int4 ra = __ldg((const int4*)(m.rsp + 8 * (size_t)j));
     const int4 rb = __ldg((const int4*)(m.rsp + 8 * (size_t)j + 4));
     const double2 a01 = __ldg((const double2*)(m.arr + 4 * (size_t)j));
     const double2 a23 = __ldg((const double2*)(m.arr + 4 * (size_t)j + 2));
-    double kf = exp_t(a01.x + a01.y * lnT - a23.x * invT, et);
-    double dlnkf = 0.0;
-    if (JAC) dlnkf = a01.y * invT + a23.x * invT * invT;
+    const bool falloff = j >= m.n_tb_end;
+    double kf, dlnkf = 0.0, dkdM = 0.0;
+    if (!falloff) {
+      kf = exp_t(a01.x + a01.y * lnT - a23.x * invT, et);
+      if (JAC) dlnkf = a01.y * invT + a23.x * invT * invT;
+    } else {
+      const double* r = w.tr + kTroeSlots * (j - m.n_tb_end);
+      kf = r[10];
+      if (JAC) { dkdM = r[11]; dlnkf = r[12]; }
+    }
     // kr / kf = 1/K_c = exp(sum nu g/RT) (p0/RT)^(-sum nu) = prod_r e_r prod_p (1/e_p) ...
     double fwd = w.C[ra.x], ratio = w.eg[ra.x], sh = 0.0;
     if (JAC) sh = -w.hRT[ra.x];
@@ -248,21 +301,15 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
     else if (dnu == 1) ratio *= RTP0;
     else if (dnu == -2) ratio *= P0RT * P0RT;
     else if (dnu == 2) ratio *= RTP0 * RTP0;
-    double Mfac = 1.0, dkdM = 0.0;
-    if (j >= m.n_elem) {
+    double Mfac = 1.0;
+    if (j >= m.n_elem && !falloff) {
       double M = ctot;
 #pragma unroll
       for (int e = 0; e < kMaxEx; ++e) {
         const int se = __ldg(m.ex_sp + (size_t)j * kMaxEx + e);
         if (se >= 0) M += __ldg(m.ex_a + (size_t)j * kMaxEx + e) * w.C[se];
       }
-      if (j < m.n_tb_end) {
-        Mfac = M;
-      } else {
-        double dlnk = 0.0;
-        kf = troe_k<JAC>(m.troe + 8 * (size_t)j, et, T, invT, lnT, M, kf, dlnkf, dkdM, dlnk);
-        dlnkf = dlnk;
-      }
+      Mfac = M;
     }
     const double kr = kf * ratio;
     const double q0 = kf * fwd - kr * rev;
@@ -864,7 +911,7 @@ __global__ void __launch_bounds__(128) di_kernel(DevMech m, int64_t n, int64_t l
                                                  size_t warp_bytes, const int32_t* n_dev) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, true, true);
+  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, m.I - m.n_tb_end, true, true);
   // n_dev (optional): the number of entries of idx actually filled, known only on the device
   const int64_t n_eff = n_dev ? min(n, (int64_t)max(*n_dev, 0)) : n;
   while (true) {
@@ -909,7 +956,7 @@ __global__ void __launch_bounds__(128) rates_kernel(DevMech m, int64_t n, int64_
                                                     double* hrr, size_t warp_bytes) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, false, false);
+  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, m.I - m.n_tb_end, false, false);
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t col = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; col < n; col += nw) {
     double z[NPL], f[NPL];
@@ -933,7 +980,7 @@ __global__ void __launch_bounds__(128) jacobian_kernel(DevMech m, int64_t n, int
                                                        size_t warp_bytes) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, false, true);
+  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, m.I - m.n_tb_end, false, true);
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int nn = m.n;
   for (int64_t col = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; col < n; col += nw) {
@@ -982,7 +1029,7 @@ static int smem_optin() {
   return v;
 }
 
-size_t di_smem_per_warp(const DevMech& m) { return warp_doubles(m.K, m.I, m.n, true, true) * sizeof(double); }
+size_t di_smem_per_warp(const DevMech& m) { return warp_doubles(m.K, m.I, m.n, m.I - m.n_tb_end, true, true) * sizeof(double); }
 
 template <typename KernelT>
 static int configure(KernelT kern, size_t warp_bytes, int& warps_per_block, size_t& smem) {
@@ -998,7 +1045,7 @@ static int configure(KernelT kern, size_t warp_bytes, int& warps_per_block, size
 
 int launch_rates(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                  const double* Y, double* wdot, double* hrr, cudaStream_t s) {
-  const size_t wb = warp_doubles(m.K, m.I, m.n, false, false) * sizeof(double);
+  const size_t wb = warp_doubles(m.K, m.I, m.n, m.I - m.n_tb_end, false, false) * sizeof(double);
   int wpb;
   size_t smem;
   int rc;
@@ -1018,7 +1065,7 @@ int launch_rates(const DevMech& m, int64_t n, int64_t ld, const double* T, const
 
 int launch_jacobian(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p,
                     const double* Y, double* jac, cudaStream_t s) {
-  const size_t wb = warp_doubles(m.K, m.I, m.n, false, true) * sizeof(double);
+  const size_t wb = warp_doubles(m.K, m.I, m.n, m.I - m.n_tb_end, false, true) * sizeof(double);
   int wpb;
   size_t smem;
   int rc;

@@ -59,11 +59,10 @@ __device__ __forceinline__ double exp_t(double x, const double* __restrict__ tab
   const double kL1 = 0x1.62e42ff000000p-8;           // ln 2 / 128, high part (32 bits)
   const double kL2 = -3.2819649005320973e-13;        // ln 2 / 128 - kL1
   const double kMagic = 6755399441055744.0;          // 1.5 * 2^52: rounds to an integer
-  const double xc = fmin(fmax(x, -708.0), 709.78);
-  const double t = fma(xc, kInvL, kMagic);
+  const double t = fma(x, kInvL, kMagic);
   const double nd = t - kMagic;
   const int nn = (int)(unsigned int)(unsigned long long)__double_as_longlong(t);
-  const double r = fma(-nd, kL2, fma(-nd, kL1, xc));
+  const double r = fma(-nd, kL2, fma(-nd, kL1, x));
   double pr = fma(r, 1.0 / 720.0, 1.0 / 120.0);
   pr = fma(pr, r, 1.0 / 24.0);
   pr = fma(pr, r, 1.0 / 6.0);
@@ -73,9 +72,12 @@ __device__ __forceinline__ double exp_t(double x, const double* __restrict__ tab
   const double tj = __ldg(tab + (nn & 127));
   double res = fma(tj, pr, tj);
   res = __longlong_as_double(__double_as_longlong(res) + ((long long)(nn >> 7) << 52));
-  if (x < -708.0) res = 0.0;
-  if (x > 709.78) res = __longlong_as_double(0x7ff0000000000000LL);
-  if (x != x) res = x;
+  // |x| >= 708, inf and NaN, detected on the exponent bits (integer pipe, rare branch)
+  if (((unsigned int)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu) >= 0x40862000u) {
+    if (x != x) res = x;
+    else if (x < -708.0) res = 0.0;
+    else if (x > 709.78) res = __longlong_as_double(0x7ff0000000000000LL);
+  }
   return res;
 }
 constexpr int kMaxElem = 8;
