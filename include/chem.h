@@ -185,8 +185,9 @@ int chem_ann_train_step(chem_ann ann, const void* X, const float* Ut, const floa
 /* Flat FP32 parameters (which = 0) or last gradients (which = 1), per layer W [out, in] then b. */
 int chem_ann_get_params(chem_ann ann, int which, float* host, int64_t count);
 int chem_ann_set_params(chem_ann ann, const float* host, int64_t count);
-/* Checkpoint (weights, Adam moments, step, normalisation) and its reload. */
-int chem_ann_save(chem_ann ann, const char* path);
+/* Checkpoint (weights, normalisation, Adam step and, if with_moments, the Adam moments; a
+ * checkpoint without moments resumes Adam from zero moments) and its reload. */
+int chem_ann_save(chem_ann ann, const char* path, int with_moments);
 int chem_ann_load(chem_mech mech, const char* path, chem_ann* out);
 /* Device error flag of the tensor-core pipelines (non-zero: a wait timed out); reading clears it. */
 int chem_ann_error(chem_ann ann, int* host_err);

@@ -241,7 +241,7 @@ def _ann_sigs():
     L.chem_ann_train_step.argtypes = [vp, vp, vp, vp, i64, C.POINTER(TrainOpts), vp, vp]
     L.chem_ann_get_params.argtypes = [vp, i32, fp, i64]
     L.chem_ann_set_params.argtypes = [vp, fp, i64]
-    L.chem_ann_save.argtypes = [vp, C.c_char_p]
+    L.chem_ann_save.argtypes = [vp, C.c_char_p, i32]
     L.chem_ann_load.argtypes = [vp, C.c_char_p, C.POINTER(vp)]
     L.chem_ann_error.argtypes = [vp, C.POINTER(i32)]
     L.chem_step_ann.argtypes = [vp, vp, i64, i64, C.c_double, vp, vp, vp, vp, C.POINTER(AnnOpts), vp,
@@ -293,8 +293,8 @@ def chem_ann_load(m: Mech, path: str) -> Ann:
     return Ann(h.value, m)
 
 
-def chem_ann_save(a: Ann, path: str) -> None:
-    _check(lib().chem_ann_save(a.handle, path.encode()))
+def chem_ann_save(a: Ann, path: str, with_moments: bool = True) -> None:
+    _check(lib().chem_ann_save(a.handle, path.encode(), int(bool(with_moments))))
 
 
 def _fptr(arr):

@@ -977,23 +977,23 @@ int chem_ann_set_params(chem_ann a, const float* host, int64_t count) {
 }
 
 // checkpoint: header, dims, normalisation, Adam step, then masters and Adam moments
-int chem_ann_save(chem_ann a, const char* path) {
+int chem_ann_save(chem_ann a, const char* path, int with_moments) {
   int rc = check_ann(a);
   if (rc) return rc;
   FILE* f = path ? std::fopen(path, "wb") : nullptr;
   if (!f) return set_error(CHEM_E_ARG, "chem_ann_save: cannot open file");
   cudaDeviceSynchronize();
-  const char magic[8] = {'C', 'H', 'E', 'M', 'A', 'N', 'N', '1'};
-  int hdr[4] = {a->K, a->L, a->step, (int)a->hnorm.size()};
+  const char magic[8] = {'C', 'H', 'E', 'M', 'A', 'N', 'N', '2'};
+  int hdr[5] = {a->K, a->L, a->step, (int)a->hnorm.size(), with_moments ? 1 : 0};
   std::fwrite(magic, 1, 8, f);
-  std::fwrite(hdr, 4, 4, f);
+  std::fwrite(hdr, 4, 5, f);
   std::fwrite(a->dims, 4, a->L + 1, f);
   std::fwrite(a->hnorm.data(), 4, a->hnorm.size(), f);
   for (int l = 0; l < a->L; ++l) {
     const size_t nw = (size_t)a->dims[l + 1] * a->dims[l], nb = a->dims[l + 1];
     const float* parts[6] = {a->Wm[l], a->bm[l], a->mW[l], a->mb[l], a->vW[l], a->vb[l]};
     const size_t sizes[6] = {nw, nb, nw, nb, nw, nb};
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < (with_moments ? 6 : 2); ++q) {
       std::vector<float> h(sizes[q]);
       cudaMemcpy(h.data(), parts[q], sizes[q] * 4, cudaMemcpyDeviceToHost);
       std::fwrite(h.data(), 4, h.size(), f);
@@ -1010,8 +1010,8 @@ int chem_ann_load(chem_mech mech, const char* path, chem_ann* out) {
   FILE* f = std::fopen(path, "rb");
   if (!f) return set_error(CHEM_E_ARG, std::string("chem_ann_load: cannot open ") + path);
   char magic[8];
-  int hdr[4];
-  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, "CHEMANN1", 8) != 0 || std::fread(hdr, 4, 4, f) != 4 ||
+  int hdr[5];
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, "CHEMANN2", 8) != 0 || std::fread(hdr, 4, 5, f) != 5 ||
       hdr[1] < 2 || hdr[1] > kMaxLayers) {
     std::fclose(f);
     return set_error(CHEM_E_PARSE, "chem_ann_load: not an ANN checkpoint");
@@ -1030,7 +1030,7 @@ int chem_ann_load(chem_mech mech, const char* path, chem_ann* out) {
     const size_t nw = (size_t)a->dims[l + 1] * a->dims[l], nb = a->dims[l + 1];
     float* parts[6] = {a->Wm[l], a->bm[l], a->mW[l], a->mb[l], a->vW[l], a->vb[l]};
     const size_t sizes[6] = {nw, nb, nw, nb, nw, nb};
-    for (int q = 0; ok && q < 6; ++q) {
+    for (int q = 0; ok && q < (hdr[4] ? 6 : 2); ++q) {   // without moments: Adam restarts from zero
       std::vector<float> h(sizes[q]);
       ok = std::fread(h.data(), 4, h.size(), f) == h.size();
       if (ok) cudaMemcpy(parts[q], h.data(), h.size() * 4, cudaMemcpyHostToDevice);

@@ -160,6 +160,7 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--eval-seed", type=int, default=3)
     ap.add_argument("--out", default="")
+    ap.add_argument("--with-moments", action="store_true", help="keep the Adam moments (resumable)")
     args = ap.parse_args()
     build.build()
     m = wl.make_mechanism(args.kind, args.mech_seed)
@@ -171,13 +172,13 @@ def main():
     gen_s = time.perf_counter() - t0
     X, bcty, U = prepare(ann, data)
     del data
-    tr = train(ann, X, bcty, U, epochs=args.epochs, batch=args.batch, lr=args.lr)
+    tr = train(ann, X, bcty, U, epochs=args.epochs, batch=args.batch, lr=args.lr, log_every=500)
     if args.out:
-        chem.chem_ann_save(ann, args.out)
+        chem.chem_ann_save(ann, args.out, with_moments=args.with_moments)
     del X, bcty, U
     ev = evaluate(gm, ann, di_states(gm, m, args.eval_cells, args.eval_seed, args.dt), args.dt)
-    tr.pop("loss_history", None)
-    print(json.dumps(dict(data_generation_s=gen_s, train=tr, eval=ev)))
+    hist = tr.pop("loss_history", None)
+    print(json.dumps(dict(data_generation_s=gen_s, train=tr, eval=ev, loss_history=hist[-20:] if hist else None)))
 
 
 if __name__ == "__main__":
