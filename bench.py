@@ -176,18 +176,30 @@ def mlp_flops_per_cell(dims) -> int:
     return sum(2 * dims[l] * dims[l + 1] for l in range(len(dims) - 1))
 
 
+ANN_CKPT = os.path.join(ROOT, "paper_2402_18858_gb300", "models", "ann_c30_seed1.ckpt")
+
+
 def run_ann(args, m, gm, di_rate):
     import torch
     from paper_2402_18858_gb300 import chem, train as tr
     dt = wl.WORKLOADS[WORKLOAD]["dt"]
-    t0 = time.perf_counter()
-    data = tr.di_states(gm, m, args.ann_train_cells, 2, dt)
-    gen_s = time.perf_counter() - t0
-    ann = chem.chem_ann_create(gm, tr.HIDDEN_30, seed=2)
-    X, bcty, U = tr.prepare(ann, data)
-    del data
-    trn = tr.train(ann, X, bcty, U, epochs=args.ann_epochs, batch=8192, lr=1e-3)
-    del X, bcty, U
+    if os.path.exists(ANN_CKPT) and not args.ann_retrain:
+        # trained offline by paper_2402_18858_gb300.train (4 M DI samples, 40 epochs, GPU)
+        ann = chem.chem_ann_load(gm, ANN_CKPT)
+        provenance = {"source": "paper_2402_18858_gb300/models/ann_c30_seed1.ckpt",
+                      "train_cells": 4_000_000, "train_epochs": 40}
+    else:
+        t0 = time.perf_counter()
+        data = tr.di_states(gm, m, args.ann_train_cells, 2, dt)
+        gen_s = time.perf_counter() - t0
+        ann = chem.chem_ann_create(gm, tr.HIDDEN_30, seed=2)
+        X, bcty, U = tr.prepare(ann, data)
+        del data
+        trn = tr.train(ann, X, bcty, U, epochs=args.ann_epochs, batch=8192, lr=1e-3)
+        del X, bcty, U
+        provenance = {"source": "trained in this run", "train_cells": args.ann_train_cells,
+                      "train_epochs": args.ann_epochs, "data_generation_s": gen_s, "train_s": trn["seconds"],
+                      "train_samples_per_s": trn["samples_per_s"]}
     # accuracy against DI on held-out cells (DI is within 1e-6 of the FP64 oracle)
     ev_data = tr.di_states(gm, m, 100_000, 3, dt)
     ev = tr.evaluate(gm, ann, ev_data, dt, repeats=1, elem_tol=ANN_ELEM_TOL)
@@ -223,8 +235,7 @@ def run_ann(args, m, gm, di_rate):
     mlp_tf = mlp_flops_per_cell(ann.dims) * n / (best_mlp * 1e-3) / 1e12
     rate = n / (best * 1e-3)
     report = {"workload": f"{ANN_WORKLOAD}: MLP {ann.dims}, BF16 tcgen05, {n} cells, dt {dt}",
-              "train_cells": args.ann_train_cells, "train_epochs": args.ann_epochs,
-              "data_generation_s": gen_s, "train_s": trn["seconds"], "train_samples_per_s": trn["samples_per_s"],
+              "network": provenance,
               "cells_per_s": rate, "ms": best, "fallback_fraction": fb, "speedup_vs_di": rate / di_rate,
               "elem_tol": ANN_ELEM_TOL,
               "error_vs_di_100k_heldout": {"fallback_fraction": ev["fallback_fraction"], **ev["all_cells"]},
@@ -298,7 +309,7 @@ def run_serve(args, m30, g30, ann_leg, di_rate30):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=0, help="override the cell count (profiling)")
@@ -307,6 +318,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ann", action="store_true", help="skip the learned-step leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--ann-retrain", action="store_true", help="train the network in this run")
     ap.add_argument("--ann-train-cells", type=int, default=500_000)
     ap.add_argument("--ann-epochs", type=int, default=24)
     ap.add_argument("--ann-cells", type=int, default=2_000_000)
@@ -324,7 +336,7 @@ def main():
         return
 
     import torch
-    from paper_2402_18858_gb300 import build, chem
+    from paper_2402_18858_gb300 import build, chem, sharding
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -338,7 +350,7 @@ def main():
     gm = chem.chem_load_mech(m_path)
     N = cfg["n"]
     # weak scaling: every rank owns its own batch of N cells (independent problems, no collective)
-    st = wl.make_states(m, N, cfg["state_seed"] + 1000 * rank)
+    st = wl.make_states(m, N, sharding.rank_state_seed(cfg["state_seed"], rank))
     dev = torch.device("cuda", local)
     T0 = torch.as_tensor(st.T, device=dev)
     p = torch.as_tensor(st.p, device=dev)
@@ -380,11 +392,7 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = t0.elapsed_time(t1) / args.steps
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = sharding.max_over_ranks(t0.elapsed_time(t1) / args.steps, device=dev)
     di_ms = float(np.mean([a.elapsed_time(b) for a, b, c in ev]))
     th_ms = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
     st_np = status.cpu().numpy()
@@ -422,11 +430,7 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / ke2e
-    if dist:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = sharding.max_over_ranks(e0.elapsed_time(e1) / ke2e, device=dev)
     h2d = hT.numel() * 8 + hY.numel() * 8
     d2h = oT.numel() * 8 + oY.numel() * 8 + ost.numel() * 4
 
@@ -440,7 +444,7 @@ def main():
             cpu = cpu_baseline(m_path, m, cfg, args.cpu_cells)
             cpu.pop("seconds", None)
         line = {
-            "metric": METRIC, "value": N * world / (ms * 1e-3), "unit": "cells/s",
+            "metric": METRIC, "value": sharding.job_throughput(N, world, ms * 1e-3), "unit": "cells/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
@@ -462,7 +466,7 @@ def main():
                          "peak_source": "measured live: chem_fp64_peak_gflops DFMA probe"},
             "thermo_roofline": {"bound": "hbm", "achieved": th_gbs, "peak": 6780.0, "unit": "GB/s",
                                 "frac": th_gbs / 6780.0, "peak_source": "MEASURED_PEAKS hbm_gbs"},
-            "e2e": {"value": N * world / (e2e_ms * 1e-3), "unit": "cells/s",
+            "e2e": {"value": sharding.job_throughput(N, world, e2e_ms * 1e-3), "unit": "cells/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,  # di_kernel + thermo_kernel per step
             "clocks": clk.summary(),
