@@ -9,47 +9,96 @@
 // kept for reference and parity.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 
 namespace chem {
 
-// mass-specific c_p (J/kg/K) and h (J/kg) at T
-__device__ __forceinline__ void cp_h(const DevMech& m, double T, const double* __restrict__ Y,
-                                     int64_t ld, int64_t i, double& cp, double& h) {
-  const int hi = T >= m.Tmid ? 1 : 0;
-  const double invT = 1.0 / T;
-  double c = 0.0, e = 0.0;
-  for (int k = 0; k < m.K; ++k) {
-    const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
-    const double yw = Y[(size_t)k * ld + i] * __ldg(m.invW + k);
-    const double cpR = __ldg(a + 0) + T * (__ldg(a + 1) + T * (__ldg(a + 2) + T * (__ldg(a + 3) + T * __ldg(a + 4))));
-    const double hRT = __ldg(a + 5) + T * (__ldg(a + 6) + T * (__ldg(a + 7) + T * (__ldg(a + 8) + T * __ldg(a + 9))))
-                       + __ldg(a + 10) * invT;
-    c += yw * cpR;
-    e += yw * hRT;
-  }
-  cp = c * kR;
-  h = e * kR * T;
+// Shared-memory copy of the tables one block needs: NASA-7 coefficients transposed to
+// [range][coefficient][species] (cp/R: a1..a5, h/RT: a6 is the only extra term), the
+// transport fits and the Wilke constants.
+template <typename real>
+struct ThermoSmem {
+  double* c;     // [2][6][K]  a1..a5 and a6 per range
+  real* tr;      // [8][K]     ln mu (4), ln lambda (4)
+  real* wA;      // [K][K]
+  real* wB;      // [K][K]
+};
+
+template <typename real>
+__host__ __device__ inline size_t thermo_smem_bytes(int K, bool transport) {
+  size_t b = (size_t)12 * K * sizeof(double);
+  if (transport) b += ((size_t)8 * K + 2 * (size_t)K * K) * sizeof(real);
+  return b;
 }
 
-template <bool MIXED>
+// mixture c_p (J/kg/K) and h (J/kg): the species sums are folded into mixture polynomial
+// coefficients A_i = sum_k (Y_k / W_k) a_ik (one FMA per coefficient and species), then
+// c_p = R sum_i A_i T^i and h = R T (sum_i A_i T^i / (i+1) + A_5 / T)
+template <int KC>
+__device__ __forceinline__ void mix_cp_h(const double* __restrict__ c, int K, double T, double Tmid,
+                                         const double* yw, double& cp, double& h) {
+  const double* cr = c + (T >= Tmid ? 6 * K : 0);
+  double A0 = 0, A1 = 0, A2 = 0, A3 = 0, A4 = 0, A5 = 0;
+#pragma unroll
+  for (int k = 0; k < (KC ? KC : K); ++k) {
+    const double y = yw[k];
+    A0 = fma(y, cr[k], A0);
+    A1 = fma(y, cr[K + k], A1);
+    A2 = fma(y, cr[2 * K + k], A2);
+    A3 = fma(y, cr[3 * K + k], A3);
+    A4 = fma(y, cr[4 * K + k], A4);
+    A5 = fma(y, cr[5 * K + k], A5);
+  }
+  cp = kR * (A0 + T * (A1 + T * (A2 + T * (A3 + T * A4))));
+  h = kR * (T * (A0 + T * (A1 * 0.5 + T * (A2 * (1.0 / 3.0) + T * (A3 * 0.25 + T * A4 * 0.2)))) + A5);
+}
+
+template <int KC, bool MIXED>
 __global__ void __launch_bounds__(128) thermo_kernel(DevMech m, int64_t n, int64_t ld, const double* T,
                                                      const double* Y, double* cp_out, double* h_out,
-                                                     double* mu_out, double* kappa_out,
-                                                     const double* h_in, double* T_out) {
+                                                     double* mu_out, double* kappa_out, const double* h_in,
+                                                     double* T_out) {
   using real = typename std::conditional<MIXED, float, double>::type;
+  extern __shared__ double tsm[];
+  const int K = KC ? KC : m.K;
+  const bool transport = mu_out || kappa_out;
+  ThermoSmem<real> S;
+  S.c = tsm;
+  S.tr = (real*)(tsm + 12 * K);
+  S.wA = S.tr + 8 * K;
+  S.wB = S.wA + K * K;
+  for (int i = threadIdx.x; i < 12 * K; i += blockDim.x) {
+    const int rg = i / (6 * K), q = (i / K) % 6, k = i % K;
+    const double* a = m.th + ((size_t)k * 2 + rg) * kThermoStride;
+    S.c[i] = __ldg(a + (q < 5 ? q : 10));     // cp/R coefficients a1..a5, then a6
+  }
+  if (transport) {
+    for (int i = threadIdx.x; i < 8 * K; i += blockDim.x) S.tr[i] = (real)__ldg(m.tr + (size_t)(i % K) * 8 + i / K);
+    for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
+      S.wA[i] = (real)__ldg(m.wA + i);
+      S.wB[i] = (real)__ldg(m.wB + i);
+    }
+  }
+  __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int K = m.K;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    double Tc = T[i];
-    double cp, h;
+    double yw[KC ? KC : CHEM_MAX_SPECIES];
+    double sYW = 0.0;
+#pragma unroll
+    for (int k = 0; k < (KC ? KC : K); ++k) {
+      yw[k] = Y[(size_t)k * ld + i] * __ldg(m.invW + k);
+      sYW += yw[k];
+    }
+    double Tc = T[i], cp, h;
     if (h_in) {
       const double ht = h_in[i];
       for (int it = 0; it < 50; ++it) {
-        cp_h(m, Tc, Y, ld, i, cp, h);
+        mix_cp_h<KC>(S.c, K, Tc, m.Tmid, yw, cp, h);
         double Tn = Tc - (h - ht) / cp;
         Tn = fmin(fmax(Tn, 200.0), 6000.0);
         const bool done = fabs(Tn - Tc) < 1e-9;
@@ -58,25 +107,23 @@ __global__ void __launch_bounds__(128) thermo_kernel(DevMech m, int64_t n, int64
       }
       T_out[i] = Tc;
     }
-    cp_h(m, Tc, Y, ld, i, cp, h);
+    mix_cp_h<KC>(S.c, K, Tc, m.Tmid, yw, cp, h);
     if (cp_out) cp_out[i] = cp;
     if (h_out) h_out[i] = h;
-    if (!mu_out && !kappa_out) continue;
+    if (!transport) continue;
     // mole fractions and species properties (ln mu, ln lambda cubic in ln T)
-    real X[CHEM_MAX_SPECIES], smu[CHEM_MAX_SPECIES], ismu[CHEM_MAX_SPECIES];
-    double sYW = 0.0;
-    for (int k = 0; k < K; ++k) sYW += Y[(size_t)k * ld + i] * __ldg(m.invW + k);
-    const double isYW = 1.0 / sYW;
+    real X[KC ? KC : CHEM_MAX_SPECIES], smu[KC ? KC : CHEM_MAX_SPECIES], ismu[KC ? KC : CHEM_MAX_SPECIES];
+    const real isYW = (real)(1.0 / sYW);
     const real L = (real)log(Tc);
     real l1 = 0, l2 = 0;
-    for (int k = 0; k < K; ++k) {
-      X[k] = (real)(Y[(size_t)k * ld + i] * __ldg(m.invW + k) * isYW);
-      const double* b = m.tr + (size_t)k * 8;
-      const real lnmu = (real)__ldg(b + 0) + L * ((real)__ldg(b + 1) + L * ((real)__ldg(b + 2) + L * (real)__ldg(b + 3)));
-      const real lnlam = (real)__ldg(b + 4) + L * ((real)__ldg(b + 5) + L * ((real)__ldg(b + 6) + L * (real)__ldg(b + 7)));
+#pragma unroll
+    for (int k = 0; k < (KC ? KC : K); ++k) {
+      X[k] = (real)yw[k] * isYW;
+      const real lnmu = S.tr[k] + L * (S.tr[K + k] + L * (S.tr[2 * K + k] + L * S.tr[3 * K + k]));
+      const real lnlam = S.tr[4 * K + k] + L * (S.tr[5 * K + k] + L * (S.tr[6 * K + k] + L * S.tr[7 * K + k]));
       // sqrt(mu_k) = exp(ln mu_k / 2); lambda_k = exp(ln lambda_k)
       smu[k] = exp(lnmu * (real)0.5);
-      ismu[k] = exp(-lnmu * (real)0.5);
+      ismu[k] = (real)1 / smu[k];
       const real lam = exp(lnlam);
       l1 += X[k] * lam;
       l2 += X[k] / lam;
@@ -86,14 +133,16 @@ __global__ void __launch_bounds__(128) thermo_kernel(DevMech m, int64_t n, int64
       // Wilke: mu = sum_k X_k mu_k / sum_j X_j Phi_kj,
       // Phi_kj = (1 + sqrt(mu_k/mu_j) (W_j/W_k)^(1/4))^2 / sqrt(8 (1 + W_k/W_j))
       real mu = 0;
-      for (int k = 0; k < K; ++k) {
+#pragma unroll 2
+      for (int k = 0; k < (KC ? KC : K); ++k) {
         real den = 0;
-        const double* A = m.wA + (size_t)k * K;
-        const double* B = m.wB + (size_t)k * K;
         const real sk = smu[k];
-        for (int j = 0; j < K; ++j) {
-          const real t = (real)1 + sk * ismu[j] * (real)__ldg(B + j);
-          den += X[j] * (real)__ldg(A + j) * t * t;
+        const real* A = S.wA + k * K;
+        const real* B = S.wB + k * K;
+#pragma unroll
+        for (int j = 0; j < (KC ? KC : K); ++j) {
+          const real t = (real)1 + sk * ismu[j] * B[j];
+          den += X[j] * A[j] * t * t;
         }
         mu += X[k] * sk * sk / den;
       }
@@ -102,18 +151,37 @@ __global__ void __launch_bounds__(128) thermo_kernel(DevMech m, int64_t n, int64
   }
 }
 
-int launch_thermo(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* Y,
-                  double* cp, double* h, double* mu, double* kappa, const double* h_in,
-                  double* T_out, int mixed, cudaStream_t s) {
+template <int KC, bool MIXED>
+static int launch_thermo_t(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* Y, double* cp,
+                           double* h, double* mu, double* kappa, const double* h_in, double* T_out, cudaStream_t s) {
+  using real = typename std::conditional<MIXED, float, double>::type;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t blocks = std::min<int64_t>((n + 127) / 128, (int64_t)sms * 16);
-  if (mixed)
-    thermo_kernel<true><<<(int)blocks, 128, 0, s>>>(m, n, ld, T, Y, cp, h, mu, kappa, h_in, T_out);
-  else
-    thermo_kernel<false><<<(int)blocks, 128, 0, s>>>(m, n, ld, T, Y, cp, h, mu, kappa, h_in, T_out);
+  const size_t smem = thermo_smem_bytes<real>(m.K, true);
+  int rc = cuda_check(cudaFuncSetAttribute(thermo_kernel<KC, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem), "thermo smem attribute");
+  if (rc) return rc;
+  const int64_t blocks = std::min<int64_t>((n + 127) / 128, (int64_t)sms * 8);
+  thermo_kernel<KC, MIXED><<<(int)blocks, 128, smem, s>>>(m, n, ld, T, Y, cp, h, mu, kappa, h_in, T_out);
   return cuda_check(cudaGetLastError(), "thermo_kernel launch");
+}
+
+int launch_thermo(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* Y,
+                  double* cp, double* h, double* mu, double* kappa, const double* h_in,
+                  double* T_out, int mixed, cudaStream_t s) {
+  // species counts of the shipped workloads get fully unrolled kernels; others run the
+  // generic loop
+#define CHEM_THERMO_K(KV)                                                                              \
+  if (m.K == KV)                                                                                       \
+    return mixed ? launch_thermo_t<KV, true>(m, n, ld, T, Y, cp, h, mu, kappa, h_in, T_out, s)         \
+                 : launch_thermo_t<KV, false>(m, n, ld, T, Y, cp, h, mu, kappa, h_in, T_out, s);
+  CHEM_THERMO_K(9)
+  CHEM_THERMO_K(30)
+  CHEM_THERMO_K(53)
+#undef CHEM_THERMO_K
+  return mixed ? launch_thermo_t<0, true>(m, n, ld, T, Y, cp, h, mu, kappa, h_in, T_out, s)
+               : launch_thermo_t<0, false>(m, n, ld, T, Y, cp, h, mu, kappa, h_in, T_out, s);
 }
 
 // ------------------------------------------------------------------------------------------
