@@ -75,10 +75,18 @@ __host__ __device__ inline int pad_ld(int n) { return n | 1; }
 constexpr int kTroeSlots = 14;
 
 // doubles per warp: matrices (optional) + species + reactions + Troe scratch + small vectors
+// The per-reaction Jacobian terms (kfe, kre, aux, qT) are live only between rhs_eval<true> and
+// jac_assemble, when the LU factors are stale (they are refactored right after), so with the
+// matrices present they share the LU region whenever it is large enough.
+__host__ __device__ inline bool jac_terms_in_lu(int I, int n) {
+  return 4 * (size_t)(I > 0 ? I : 1) <= (size_t)n * pad_ld(n);
+}
+
 __host__ __device__ inline size_t warp_doubles(int K, int I, int n, int nT, bool mats, bool jac) {
   size_t ld = pad_ld(n);
   size_t d = (mats ? 2 * (size_t)n * ld : (jac ? (size_t)n * ld : 0));
-  d += 5 * (size_t)K + (jac ? 5 : 1) * (size_t)(I > 0 ? I : 1) + (size_t)kTroeSlots * nT;
+  const bool alias = mats && jac && jac_terms_in_lu(I, n);
+  d += 5 * (size_t)K + (jac && !alias ? 5 : 1) * (size_t)(I > 0 ? I : 1) + (size_t)kTroeSlots * nT;
   d += (size_t)n + 32 + (size_t)(n + 1) / 2 + 2;
   return (d + 1) & ~size_t(1);   // keep 16-byte alignment per warp
 }
@@ -98,7 +106,12 @@ __device__ __forceinline__ WarpMem carve(double* base, int K, int I, int n, int 
   w.ieg = p; p += K;
   const int Ir = I > 0 ? I : 1;
   w.q = p; p += Ir;
-  if (jac) {
+  if (jac && mats && jac_terms_in_lu(I, n)) {
+    w.kfe = w.LU;
+    w.kre = w.LU + Ir;
+    w.aux = w.LU + 2 * Ir;
+    w.qT = w.LU + 3 * Ir;
+  } else if (jac) {
     w.kfe = p; p += Ir;
     w.kre = p; p += Ir;
     w.aux = p; p += Ir;
@@ -1093,16 +1106,26 @@ int launch_di(const DevMech& m, int64_t n, int64_t ld, double dt, double* T, con
   int dev = 0, per_sm = 0, max_threads_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  // persistent grid: the block shape (1..4 warps) that keeps the most warps resident per SM
+  auto best_shape = [&](auto kern) -> int {
+    int best_w = 0;
+    const int optin = smem_optin();
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    for (int cand = 4; cand >= 1; --cand) {
+      if ((size_t)cand * wb > (size_t)optin) continue;
+      int blocks = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * cand, (size_t)cand * wb);
+      if (blocks * cand > best_w) { best_w = blocks * cand; wpb = cand; per_sm = blocks; }
+    }
+    smem = (size_t)wpb * wb;
+    return best_w > 0 ? CHEM_OK : set_error(CHEM_E_UNSUPPORTED, "mechanism needs more shared memory per warp than the device has");
+  };
   if (m.n <= 32) {
-    if ((rc = configure(di_kernel<1>, wb, wpb, smem))) return rc;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, di_kernel<1>, 32 * wpb, smem);
-    if (per_sm < 1) per_sm = 1;
+    if ((rc = best_shape(di_kernel<1>))) return rc;
     const int64_t grid = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)sm_count() * per_sm);
     di_kernel<1><<<(int)grid, 32 * wpb, smem, s>>>(m, n, ld, dt, T, p, Y, idx, o, status, stats, queue, wb, n_dev);
   } else {
-    if ((rc = configure(di_kernel<2>, wb, wpb, smem))) return rc;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, di_kernel<2>, 32 * wpb, smem);
-    if (per_sm < 1) per_sm = 1;
+    if ((rc = best_shape(di_kernel<2>))) return rc;
     const int64_t grid = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)sm_count() * per_sm);
     di_kernel<2><<<(int)grid, 32 * wpb, smem, s>>>(m, n, ld, dt, T, p, Y, idx, o, status, stats, queue, wb, n_dev);
   }

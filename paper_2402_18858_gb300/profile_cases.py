@@ -1,0 +1,75 @@
+"""One kernel case per invocation, for profilers (ncu) and quick timing.
+
+    python -m paper_2402_18858_gb300.profile_cases di --cells 8192
+    python -m paper_2402_18858_gb300.profile_cases thermo --cells 1048576
+    python -m paper_2402_18858_gb300.profile_cases mlp --cells 65536
+
+Each case loads the 30-species workload mechanism, builds seeded inputs, runs the operation
+`--repeats` times (the first is the warm-up) and prints the CUDA-event time of the last one.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import tempfile
+
+import torch
+
+from . import build, chem, workload as wl
+
+MECH = ("c_30", 1)
+CKPT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models", "ann_c30_seed1.ckpt")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["di", "thermo", "mlp"])
+    ap.add_argument("--cells", type=int, default=8192)
+    ap.add_argument("--repeats", type=int, default=2)
+    a = ap.parse_args()
+    build.build()
+    m = wl.make_mechanism(*MECH)
+    gm = chem.chem_load_mech(wl.mechanism_file(*MECH, os.path.join(tempfile.gettempdir(), "chem_mech")))
+    st = wl.make_states(m, a.cells, 101)
+    dev = torch.device("cuda")
+    T0 = torch.as_tensor(st.T, device=dev)
+    p = torch.as_tensor(st.p, device=dev)
+    Y0 = torch.as_tensor(st.Y, device=dev)
+    n = a.cells
+    if a.case == "di":
+        status = torch.empty(n, dtype=torch.int32, device=dev)
+        ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+        T, Y = T0.clone(), Y0.clone()
+
+        def run():
+            T.copy_(T0)
+            Y.copy_(Y0)
+            chem.chem_step_di(gm, 5e-6, T, p, Y, status, workspace=ws)
+    elif a.case == "thermo":
+        outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
+
+        def run():
+            chem.thermo_props(gm, T0, Y0, *outs, mixed_precision=True)
+    else:
+        ann = chem.chem_ann_load(gm, CKPT)
+        X = torch.empty((n, 64), dtype=torch.bfloat16, device=dev)
+        chem.chem_ann_features(ann, T0, p, Y0, X)
+        U = torch.empty((n, ann.n_out_pad), dtype=torch.float32, device=dev)
+        ws = torch.empty(chem.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device=dev)
+
+        def run():
+            chem.chem_ann_forward(ann, X, U, ws)
+    ms = 0.0
+    for _ in range(a.repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    print(json.dumps({"case": a.case, "cells": n, "ms": ms}))
+
+
+if __name__ == "__main__":
+    main()
