@@ -28,9 +28,16 @@ __device__ __forceinline__ float dgelu_f(float x) {
 // ------------------------------------------------------------------------------------------
 // GEMM kernel
 // ------------------------------------------------------------------------------------------
+#ifndef CHEM_GEMM_STAGES_256
+#define CHEM_GEMM_STAGES_256 2   // 2 stages of 48 KB: two CTAs per SM, one's epilogue overlaps the other's MMAs
+#endif
+#ifndef CHEM_GEMM_STAGES
+#define CHEM_GEMM_STAGES 3
+#endif
+
 template <int BN>
 struct TileCfg {
-  static constexpr int STAGES = BN >= 256 ? 4 : 6;
+  static constexpr int STAGES = BN >= 256 ? CHEM_GEMM_STAGES_256 : CHEM_GEMM_STAGES;
   static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   static constexpr size_t A_BYTES = (size_t)tc::BM * tc::BK * 2;
   static constexpr size_t B_BYTES = (size_t)BN * tc::BK * 2;
@@ -38,7 +45,7 @@ struct TileCfg {
 };
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
                                                            const __grid_constant__ CUtensorMap tb,
                                                            GemmEpi e, int M, int N, int K, int* err) {
   using C = TileCfg<BN>;
@@ -53,7 +60,8 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __grid_constant
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * tc::BM, n0 = blockIdx.y * BN;
+  // N tiles fastest: the CTAs of one row block run together and share its A rows in L2
+  const int m0 = blockIdx.y * tc::BM, n0 = blockIdx.x * BN;
   const int nkb = (K + tc::BK - 1) / tc::BK;
 
   if (threadIdx.x == 0) {
@@ -224,7 +232,8 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
       return rc;
     configured = true;
   }
-  dim3 grid((unsigned)((M + tc::BM - 1) / tc::BM), (unsigned)((N + BN - 1) / BN));
+  if ((M + tc::BM - 1) / tc::BM > 65535) return set_error(CHEM_E_ARG, "gemm: more than 65535 row blocks in one call");
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + tc::BM - 1) / tc::BM));
   gemm_bf16_kernel<BN, EPI><<<grid, 128, smem, s>>>(ta, tb, e, M, N, K, err);
   return cuda_check(cudaGetLastError(), "gemm_bf16_kernel launch");
 }
