@@ -279,6 +279,11 @@ int thermo_props(chem_mech mech, int64_t n, int64_t ld, const double* T, const d
  * method the kernels use), for comparison with CUDA's exp.  Device pointers, n >= 0. */
 int chem_selftest_exp(chem_mech mech, int64_t n, const double* x, double* y, chem_stream stream);
 
+/* Testing hook: y[i] = log(x[i]) by the library's own FP64 logarithm (the table-driven method
+ * the kernels use for ln T and the falloff logarithms), for comparison with CUDA's log.  Device
+ * pointers, n >= 0. */
+int chem_selftest_log(chem_mech mech, int64_t n, const double* x, double* y, chem_stream stream);
+
 /* Testing hook: one tensor-core GEMM of the MLP, out = epi(A B^T) with A [M, K] and B [N, K]
  * BF16 row-major (K a multiple of 8, 16-byte aligned), FP32 accumulation.  epi 0: GELU(acc +
  * bias) -> BF16; 1: acc + bias -> FP32; 2: acc * GELU'(z) -> BF16 with z [M, N] BF16;

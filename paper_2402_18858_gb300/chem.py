@@ -59,6 +59,7 @@ def lib(auto_build: bool = False):
         L.chem_last_error.restype = C.c_char_p
         L.chem_fp64_peak_gflops.argtypes = [C.POINTER(dbl), vp]
         L.chem_selftest_exp.argtypes = [vp, i64, vp, vp, vp]
+        L.chem_selftest_log.argtypes = [vp, i64, vp, vp, vp]
         L.chem_selftest_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
         _lib = L
         return L
@@ -189,6 +190,11 @@ def chem_fp64_peak_gflops(stream=None) -> float:
 
 def chem_selftest_exp(m: Mech, x, y, stream=None) -> None:
     _check(lib().chem_selftest_exp(m.handle, x.numel(), _ptr(x, torch.float64),
+                                   _ptr(y, torch.float64), _stream(stream)))
+
+
+def chem_selftest_log(m: Mech, x, y, stream=None) -> None:
+    _check(lib().chem_selftest_log(m.handle, x.numel(), _ptr(x, torch.float64),
                                    _ptr(y, torch.float64), _stream(stream)))
 
 

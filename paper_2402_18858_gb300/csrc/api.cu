@@ -324,9 +324,34 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
     }
   std::vector<double> exptab(128);
   for (int j = 0; j < 128; ++j) exptab[j] = (double)std::exp2((long double)j / 128.0L);
+  std::vector<double> logtab(3 * 97);
+  for (int j = 96; j <= 192; ++j) {
+    const long double F = (long double)j / 128.0L;
+    logtab[3 * (j - 96)] = (double)F;
+    logtab[3 * (j - 96) + 1] = (double)(1.0L / F);
+    logtab[3 * (j - 96) + 2] = (double)std::log(F);
+  }
   std::vector<double> compW((size_t)K * E);
   for (int k = 0; k < K; ++k)
     for (int e = 0; e < E; ++e) compW[(size_t)k * E + e] = hm.comp[(size_t)k * E + e] / hm.W[k];
+  // exponential items of the right-hand side (see DevMech::xarg)
+  const int nT = I - n_tb_end;
+  const int n_x = n_tb_end + 5 * nT;
+  std::vector<double> xarg((size_t)std::max(n_x, 1) * 4, 0.0);
+  for (int jj = 0; jj < n_tb_end; ++jj)
+    for (int c = 0; c < 3; ++c) xarg[(size_t)jj * 4 + c] = arr[(size_t)jj * 4 + c];
+  for (int jt = 0; jt < nT; ++jt) {
+    const int jj = n_tb_end + jt;
+    const double* a = &arr[(size_t)jj * 4];
+    const double* tp = &troe[(size_t)jj * 8];
+    double* x = &xarg[(size_t)(n_tb_end + 5 * jt) * 4];
+    x[0] = a[0]; x[1] = a[1]; x[2] = a[2];                            // k_inf
+    x[4] = tp[0] - a[0]; x[5] = tp[1] - a[1]; x[6] = tp[2] - a[2];    // k_0 / k_inf
+    x[11] = -tp[4];                                                   // exp(-T / T***)
+    x[15] = -tp[5];                                                   // exp(-T / T*)
+    if (tp[7] != 0.0) x[18] = tp[6];                                  // exp(-T** / T)
+    else x[16] = -1e300;                                              // absent term: 0
+  }
   std::vector<int> refs_pad(refs);
   if (refs_pad.empty()) refs_pad.push_back(0);
 
@@ -340,6 +365,43 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
     }
   }
   sp_ptr[K] = (int)sp_rxn.size();
+  // Lane-balanced schedule of the species production rates (see DevMech::bal): the incidence
+  // entries in species order, cut into 32 equal segments, one per lane; a segment's
+  // consecutive entries of one species form a run whose partial sum goes to its own slot.
+  const int E_inc = (int)sp_rxn.size();
+  int bal_P = (E_inc + 31) / 32;
+  std::vector<unsigned int> bal((size_t)std::max(bal_P, 1) * 32, 0u);
+  std::vector<int> run_ptr(K + 1, 0);
+  {
+    int runs = 0;
+    bool ok = bal_P > 0 && I < (1 << 20);
+    std::vector<int> run_of_entry(E_inc, -1), sp_of(E_inc);
+    for (int k = 0; k < K; ++k)
+      for (int e = sp_ptr[k]; e < sp_ptr[k + 1]; ++e) sp_of[e] = k;
+    for (int e = 0; e < E_inc && ok; ++e) {
+      const bool first = e == 0 || sp_of[e] != sp_of[e - 1] || e % bal_P == 0;
+      if (first) ++runs;
+      run_of_entry[e] = runs - 1;
+      const double nu = sp_nu[e];
+      const int a = (int)std::fabs(nu);
+      if ((double)a != std::fabs(nu) || a < 1 || a > 3) ok = false;
+    }
+    if (runs > 3 * K || runs > 255) ok = false;   // the runs' slots reuse 3K dead doubles
+    if (ok) {
+      for (int k = 0; k < K; ++k) run_ptr[k] = sp_ptr[k] < sp_ptr[k + 1] ? run_of_entry[sp_ptr[k]] : -1;
+      run_ptr[K] = runs;
+      for (int k = K - 1; k >= 0; --k) if (run_ptr[k] < 0) run_ptr[k] = run_ptr[k + 1];
+      for (int e = 0; e < E_inc; ++e) {
+        const int lane = e / bal_P, i = e % bal_P;
+        const bool last = e + 1 == E_inc || run_of_entry[e + 1] != run_of_entry[e];
+        const double nu = sp_nu[e];
+        bal[(size_t)i * 32 + lane] = (unsigned int)std::fabs(nu) | (nu < 0 ? 4u : 0u) | (last ? 8u : 0u) |
+                                     ((unsigned int)run_of_entry[e] << 4) | ((unsigned int)sp_rxn[e] << 12);
+      }
+    } else {
+      bal_P = 0;
+    }
+  }
   const int nnz = std::max((int)sp_rxn.size(), 1);
   sp_rxn.resize(nnz, 0);
   sp_nu.resize(nnz, 0.0);
@@ -363,6 +425,8 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   size_t orxn = add(sp_rxn.data(), sp_rxn.size() * 4), onu = add(sp_nu.data(), sp_nu.size() * 8);
   size_t oref = add(refs_pad.data(), refs_pad.size() * 4), oP = add(Pm.data(), Pm.size() * 8);
   size_t oexp = add(exptab.data(), exptab.size() * 8), ocw = add(compW.data(), compW.size() * 8);
+  size_t oxa = add(xarg.data(), xarg.size() * 8), olog = add(logtab.data(), logtab.size() * 8);
+  size_t obal = add(bal.data(), bal.size() * 4), orun = add(run_ptr.data(), run_ptr.size() * 4);
   std::vector<char> blob(total, 0);
   for (auto& p : pieces) std::memcpy(blob.data() + p.off, p.src, p.bytes);
   void* d = nullptr;
@@ -386,7 +450,13 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   m.sp_rxn = (const int*)(b + orxn); m.sp_nu = (const double*)(b + onu);
   m.n_ref = R; m.ref_sp = (const int*)(b + oref); m.P = (const double*)(b + oP);
   m.exptab = (const double*)(b + oexp);
+  m.logtab = (const double*)(b + olog);
   m.compW = (const double*)(b + ocw);
+  m.n_x = n_x;
+  m.xarg = (const double*)(b + oxa);
+  m.bal_P = bal_P;
+  m.bal = (const unsigned int*)(b + obal);
+  m.run_ptr = (const int*)(b + orun);
   cm->dmem = d;
   cm->K = K; cm->I = I; cm->E = m.E;
   return CHEM_OK;
@@ -514,6 +584,14 @@ int chem_selftest_exp(chem_mech m, int64_t n, const double* x, double* y, chem_s
   if (n < 0 || (n > 0 && (!x || !y))) return set_error(CHEM_E_ARG, "chem_selftest_exp: bad arguments");
   if (n == 0) return CHEM_OK;
   return launch_exp_selftest(m->dev, n, x, y, (cudaStream_t)stream);
+}
+
+int chem_selftest_log(chem_mech m, int64_t n, const double* x, double* y, chem_stream stream) {
+  int rc = check_mech(m);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!x || !y))) return set_error(CHEM_E_ARG, "chem_selftest_log: bad arguments");
+  if (n == 0) return CHEM_OK;
+  return launch_log_selftest(m->dev, n, x, y, (cudaStream_t)stream);
 }
 
 int chem_fp64_peak_gflops(double* gflops, chem_stream stream) {

@@ -39,6 +39,19 @@ __device__ __forceinline__ float wsumf(float v) {
   return __shfl_sync(FULLMASK, v, 0);
 }
 
+// 1/x from the hardware reciprocal estimate and two Newton-Raphson steps y += y (1 - x y), each
+// of which squares the relative error, so the result is within about an ulp of 1/x for finite
+// normal x; 4 FP64 instructions against about twice that for a correctly rounded division.
+// Zero, subnormal or infinite x give NaN (every caller treats that as a failed evaluation).
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 template <int NPL>
 __device__ __forceinline__ double comp_get(const double (&x)[NPL], int i) {
   // value of component i (owned by lane i & 31, slot i >> 5), on every lane
@@ -56,8 +69,8 @@ struct WarpMem {
   double* C;      // K concentrations
   double* hRT;    // K
   double* g;      // K   g/RT = h/RT - s/R
-  double* eg;     // K   exp(-(g/RT - shift)), shift = element-potential term
-  double* ieg;    // K   exp(+(g/RT - shift))
+  double* eg;     // K   exp(-(g/RT - shift)) p0/RT, shift = element-potential term
+  double* ieg;    // K   exp(+(g/RT - shift)) RT/p0
   double* q;      // I   net rates of progress
   double* kfe;    // I   effective forward coefficient (third-body factor included)
   double* kre;    // I   effective reverse coefficient
@@ -137,36 +150,17 @@ struct CellSc {
 };
 
 // ------------------------------------------------------------------------------------------
-// Troe falloff (Lindemann form with the Troe broadening factor, Gilbert, Luther & Troe 1983),
-// evaluated for all falloff reactions of a cell at once with the transcendental functions
-// spread over the lanes: five exponentials per reaction (k_inf, k_0 and the three F_cent
-// terms), then P_r and F_cent, then the two base-10 logarithms, then F and k.  Results in
-// w.tr: [10] k, [11] dk/d[M], [12] d ln k/dT at fixed [M].
+// Troe falloff (Lindemann form with the Troe broadening factor, Gilbert, Luther & Troe 1983)
+// for all falloff reactions of a cell.  The exponential rounds of rhs_eval have already put
+// [0] k_inf, [1] k_0/k_inf, [2] exp(-T/T***), [3] exp(-T/T*), [4] exp(-T**/T) into w.tr; here
+// P_r = (k_0/k_inf)[M] and F_cent (no division), their base-10 logarithms (one lane each), and
+// F and k with two divisions per reaction.  Results: [10] k, [11] dk/d[M], [12] d ln k/dT at
+// fixed [M].
 // ------------------------------------------------------------------------------------------
 template <bool JAC>
-__device__ __forceinline__ void troe_phase(const DevMech& m, const WarpMem& w, double T, double invT, double lnT,
-                                           double ctot, int lane) {
+__device__ __forceinline__ void troe_phase(const DevMech& m, const WarpMem& w, double invT, double ctot, int lane) {
   const int nT = m.I - m.n_tb_end;
   const double* __restrict__ et = m.exptab;
-  for (int t = lane; t < 5 * nT; t += 32) {
-    const int jt = t / 5, q = t - 5 * jt, j = m.n_tb_end + jt;
-    const double* tp = m.troe + 8 * (size_t)j;
-    double arg;
-    if (q == 0) {
-      const double* a = m.arr + 4 * (size_t)j;
-      arg = __ldg(a) + __ldg(a + 1) * lnT - __ldg(a + 2) * invT;
-    } else if (q == 1) {
-      arg = __ldg(tp) + __ldg(tp + 1) * lnT - __ldg(tp + 2) * invT;
-    } else if (q == 2) {
-      arg = -T * __ldg(tp + 4);
-    } else if (q == 3) {
-      arg = -T * __ldg(tp + 5);
-    } else {
-      arg = __ldg(tp + 7) != 0.0 ? -__ldg(tp + 6) * invT : -1e300;   // absent T** term -> 0
-    }
-    w.tr[kTroeSlots * jt + q] = exp_t(arg, et);
-  }
-  __syncwarp();
   for (int jt = lane; jt < nT; jt += 32) {
     const int j = m.n_tb_end + jt;
     const double* tp = m.troe + 8 * (size_t)j;
@@ -179,36 +173,39 @@ __device__ __forceinline__ void troe_phase(const DevMech& m, const WarpMem& w, d
     }
     const double a = __ldg(tp + 3);
     r[5] = (1.0 - a) * r[2] + a * r[3] + r[4];
-    r[6] = fmax(r[1] * M / r[0], 1e-300);
+    r[6] = fmax(r[1] * M, 1e-300);
   }
   __syncwarp();
   for (int t = lane; t < 2 * nT; t += 32) {
     const int jt = t >> 1, q = t & 1;
-    w.tr[kTroeSlots * jt + 8 + q] = log10(w.tr[kTroeSlots * jt + 5 + q]);
+    w.tr[kTroeSlots * jt + 8 + q] = log_t(w.tr[kTroeSlots * jt + 5 + q], m.logtab) * 0.4342944819032518;   // log10
   }
   __syncwarp();
   for (int jt = lane; jt < nT; jt += 32) {
     const int j = m.n_tb_end + jt;
     double* r = w.tr + kTroeSlots * jt;
-    const double kinf = r[0], k0 = r[1], Fc = r[5], Pr = r[6], L = r[8];
+    const double kinf = r[0], Fc = r[5], Pr = r[6], L = r[8];
     const double c = -0.4 - 0.67 * L;
     const double nn = 0.75 - 1.27 * L;
     const double x = r[9] + c;
     const double den = nn - 0.14 * x;
-    const double f1 = x / den;
-    const double opf = 1.0 + f1 * f1;
-    const double F = exp_t(2.302585092994046 * (L / opf), et);   // 10^(L/opf)
-    const double ipr = 1.0 / (1.0 + Pr);
+    const double d2 = den * den;
+    // log10 F = log10 F_cent / (1 + (x / den)^2) = log10 F_cent den^2 / (den^2 + x^2)
+    const double F = exp_t(2.302585092994046 * (L * d2 * rcp_nr(d2 + x * x)), et);
+    const double ipr = rcp_nr(1.0 + Pr);
     r[10] = kinf * Pr * ipr * F;
     if (JAC) {
       const double* tp = m.troe + 8 * (size_t)j;
       const double* ar = m.arr + 4 * (size_t)j;
+      const double k0 = kinf * r[1];
+      const double f1 = x / den;
+      const double opf = 1.0 + f1 * f1;
       const double aa = __ldg(tp + 3), iT3 = __ldg(tp + 4), iT1 = __ldg(tp + 5);
       const double dFc = -(1.0 - aa) * iT3 * r[2] - aa * iT1 * r[3] + __ldg(tp + 6) * invT * invT * r[4];
-      const double df1dx = nn / (den * den);
+      const double df1dx = nn / d2;
       const double gg = -L * 2.0 * f1 / (opf * opf) * df1dx;          // d log F / d log Pr
       r[11] = k0 * F * (ipr * ipr + gg * ipr);
-      const double df1dL = df1dx * (-0.67) + (-x / (den * den)) * (-1.27);
+      const double df1dL = df1dx * (-0.67) + (-x / d2) * (-1.27);
       const double dlogFdL = 1.0 / opf - L * 2.0 * f1 / (opf * opf) * df1dL;
       const double dlnkinf = __ldg(ar + 1) * invT + __ldg(ar + 2) * invT * invT;
       const double dlnk0 = __ldg(tp + 1) * invT + __ldg(tp + 2) * invT * invT;
@@ -226,20 +223,11 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
                          double (&f)[NPL], LaneSp<NPL>& sp, CellSc& cs, int lane) {
   const int K = m.K, I = m.I;
   const double T = comp_get<NPL>(y, K);
-  const double lnT = log(T), invT = 1.0 / T, RT = kR * T;
+  const double lnT = log_t(T, m.logtab), RT = kR * T;
   const double* __restrict__ et = m.exptab;
-  double sYW = 0.0;
-#pragma unroll
-  for (int s = 0; s < NPL; ++s) {
-    const int k = lane + 32 * s;
-    if (k < K) sYW += y[s] * __ldg(m.invW + k);
-  }
-  sYW = wsum(sYW);
-  const double Wbar = 1.0 / sYW;
-  const double rho = p * Wbar * invT * (1.0 / kR);
-  const double irho = sYW * RT * ip;        // 1/rho without a division (ip = 1/p)
-  double ctot = 0.0, cpp = 0.0;
   const int hi = T >= m.Tmid ? 1 : 0;
+  // pass 1: c_p/R per species and the two mixture sums sum Y/W and sum Y c_p/(R W)
+  double sYW = 0.0, cpp = 0.0;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
     const int k = lane + 32 * s;
@@ -248,27 +236,48 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
       const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
       const double a0 = __ldg(a + 0), a1 = __ldg(a + 1), a2 = __ldg(a + 2), a3 = __ldg(a + 3), a4 = __ldg(a + 4);
       const double cpR = a0 + T * (a1 + T * (a2 + T * (a3 + T * a4)));
+      if (JAC) sp.dcpR[s] = a1 + T * (2.0 * a2 + T * (3.0 * a3 + T * 4.0 * a4));
+      const double yw = y[s] * __ldg(m.invW + k);
+      sYW += yw;
+      cpp += yw * cpR;
+      sp.cpR[s] = cpR;
+    }
+  }
+  sYW = wsum(sYW);
+  cpp = wsum(cpp);
+  // one division gives 1/T, the mean molar mass and 1/c_p
+  const double TsY = T * sYW;
+  const double inv = rcp_nr(TsY * cpp);
+  const double invT = inv * (sYW * cpp);
+  const double Wbar = inv * (T * cpp);
+  const double icp = inv * TsY * (1.0 / kR);
+  const double rho = p * (inv * cpp) * (1.0 / kR);   // p Wbar / (R T)
+  const double irho = sYW * RT * ip;                 // 1 / rho
+  const double ctot = rho * sYW;                     // sum of the concentrations
+  const double cp = cpp * kR;
+  // pass 2: h/RT, g/RT and the concentrations
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int k = lane + 32 * s;
+    if (k < K) {
+      const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
       const double hRT = __ldg(a + 5) + T * (__ldg(a + 6) + T * (__ldg(a + 7) + T * (__ldg(a + 8) + T * __ldg(a + 9))))
                          + __ldg(a + 10) * invT;
       const double sR = __ldg(a + 11) * lnT + T * (__ldg(a + 12) + T * (__ldg(a + 13) + T * (__ldg(a + 14) + T * __ldg(a + 15))))
                         + __ldg(a + 16);
-      if (JAC) sp.dcpR[s] = a1 + T * (2.0 * a2 + T * (3.0 * a3 + T * 4.0 * a4));
-      const double iW = __ldg(m.invW + k);
-      const double Ck = rho * y[s] * iW;
+      const double Ck = rho * y[s] * __ldg(m.invW + k);
       w.C[k] = Ck;
       w.hRT[k] = hRT;
       w.g[k] = hRT - sR;
-      sp.cpR[s] = cpR;
       sp.hRT[s] = hRT;
-      ctot += Ck;
-      cpp += y[s] * cpR * iW;
     }
   }
-  ctot = wsum(ctot);
-  const double cp = wsum(cpp) * kR;
   __syncwarp();
   // exp(-g'/RT) per species, g' = g - sum_r P_kr g_ref_r (one exp per species instead of
   // one per reaction; the element-potential shift cancels in every balanced reaction)
+  // kr / kf = 1/K_c = prod_r e_r prod_p (1/e_p) (RT/p0)^(sum nu): the pressure factor goes
+  // into the per-species values, p0/RT with every reactant and RT/p0 with every product
+  const double P0RT = (kP0 / kR) * invT, RTP0 = RT * (1.0 / kP0);
   const int R = m.n_ref;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
@@ -277,29 +286,40 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
       double gs = w.g[k];
       for (int r = 0; r < R; ++r) gs -= __ldg(m.P + (size_t)k * R + r) * w.g[__ldg(m.ref_sp + r)];
       const double e = exp_t(-gs, et);
-      w.eg[k] = e;
-      w.ieg[k] = 1.0 / e;
+      w.eg[k] = e * P0RT;
+      w.ieg[k] = rcp_nr(e) * RTP0;
+    }
+  }
+  // exponential rounds: k_f of every non-falloff reaction (into w.q, read back by the same
+  // lane below) and the five exponentials of each falloff reaction (into w.tr), all items
+  // packed over the lanes
+  const int nb = m.n_tb_end;
+  for (int t = lane; t < m.n_x; t += 32) {
+    const double2 x01 = __ldg((const double2*)(m.xarg + 4 * (size_t)t));
+    const double2 x23 = __ldg((const double2*)(m.xarg + 4 * (size_t)t + 2));
+    const double e = exp_t(fma(x23.y, T, fma(-x23.x, invT, fma(x01.y, lnT, x01.x))), et);
+    if (t < nb) {
+      w.q[t] = e;
+    } else {
+      const int u = t - nb, jt = u / 5;
+      w.tr[kTroeSlots * jt + (u - 5 * jt)] = e;
     }
   }
   __syncwarp();
-  if (I > m.n_tb_end) troe_phase<JAC>(m, w, T, invT, lnT, ctot, lane);
-  const double P0RT = (kP0 / kR) * invT, RTP0 = RT * (1.0 / kP0);
+  if (I > nb) troe_phase<JAC>(m, w, invT, ctot, lane);
   for (int j = lane; j < I; j += 32) {
     const int4 ra = __ldg((const int4*)(m.rsp + 8 * (size_t)j));
     const int4 rb = __ldg((const int4*)(m.rsp + 8 * (size_t)j + 4));
-    const double2 a01 = __ldg((const double2*)(m.arr + 4 * (size_t)j));
-    const double2 a23 = __ldg((const double2*)(m.arr + 4 * (size_t)j + 2));
-    const bool falloff = j >= m.n_tb_end;
+    const bool falloff = j >= nb;
     double kf, dlnkf = 0.0, dkdM = 0.0;
     if (!falloff) {
-      kf = exp_t(a01.x + a01.y * lnT - a23.x * invT, et);
-      if (JAC) dlnkf = a01.y * invT + a23.x * invT * invT;
+      kf = w.q[j];
+      if (JAC) dlnkf = __ldg(m.arr + 4 * (size_t)j + 1) * invT + __ldg(m.arr + 4 * (size_t)j + 2) * invT * invT;
     } else {
-      const double* r = w.tr + kTroeSlots * (j - m.n_tb_end);
+      const double* r = w.tr + kTroeSlots * (j - nb);
       kf = r[10];
       if (JAC) { dkdM = r[11]; dlnkf = r[12]; }
     }
-    // kr / kf = 1/K_c = exp(sum nu g/RT) (p0/RT)^(-sum nu) = prod_r e_r prod_p (1/e_p) ...
     double fwd = w.C[ra.x], ratio = w.eg[ra.x], sh = 0.0;
     if (JAC) sh = -w.hRT[ra.x];
     if (ra.w > 1) { fwd *= w.C[ra.y]; ratio *= w.eg[ra.y]; if (JAC) sh -= w.hRT[ra.y]; }
@@ -309,11 +329,6 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
     if (JAC) sh += w.hRT[rb.x];
     if (rb.w > 1) { rev *= w.C[rb.y]; ratio *= w.ieg[rb.y]; if (JAC) sh += w.hRT[rb.y]; }
     if (rb.w > 2) { rev *= w.C[rb.z]; ratio *= w.ieg[rb.z]; if (JAC) sh += w.hRT[rb.z]; }
-    const int dnu = (int)a23.y;
-    if (dnu == -1) ratio *= P0RT;
-    else if (dnu == 1) ratio *= RTP0;
-    else if (dnu == -2) ratio *= P0RT * P0RT;
-    else if (dnu == 2) ratio *= RTP0 * RTP0;
     double Mfac = 1.0;
     if (j >= m.n_elem && !falloff) {
       double M = ctot;
@@ -330,12 +345,32 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
     if (JAC) {
       w.kfe[j] = Mfac * kf;
       w.kre[j] = Mfac * kr;
-      w.aux[j] = (j < m.n_elem) ? 0.0 : (j < m.n_tb_end ? q0 : dkdM * (fwd - ratio * rev));
-      const double dlnKc = (sh - a23.y) * invT;
+      w.aux[j] = (j < m.n_elem) ? 0.0 : (j < nb ? q0 : dkdM * (fwd - ratio * rev));
+      const double dlnKc = (sh - __ldg(m.arr + 4 * (size_t)j + 3)) * invT;
       w.qT[j] = Mfac * (kf * dlnkf * fwd - kr * (dlnkf - dlnKc) * rev);
     }
   }
   __syncwarp();
+  // production rates wdot_k = sum_j nu_kj q_j
+  const int P = m.bal_P;
+  double* part = w.g;   // g, eg and ieg are dead from here on: 3K slots for the runs
+  if (P > 0) {
+    double acc = 0.0;
+    for (int i = 0; i < P; ++i) {
+      const unsigned int e = __ldg(m.bal + (size_t)i * 32 + lane);
+      if (e & 3u) {
+        // nu = +-1, +-2, +-3 built from its bits (no FP64 conversion)
+        const unsigned int a = e & 3u;
+        const unsigned int hw = (a == 1u ? 0x3ff00000u : a == 2u ? 0x40000000u : 0x40080000u) | ((e & 4u) << 29);
+        acc = fma(__hiloint2double((int)hw, 0), w.q[e >> 12], acc);
+        if (e & 8u) {
+          part[(e >> 4) & 255u] = acc;
+          acc = 0.0;
+        }
+      }
+    }
+    __syncwarp();
+  }
   double Qp = 0.0;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
@@ -343,16 +378,21 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
     f[s] = 0.0;
     sp.wdot[s] = 0.0;
     if (k < K) {
-      const int e0 = __ldg(m.sp_ptr + k), e1 = __ldg(m.sp_ptr + k + 1);
       double wd = 0.0;
-      for (int e = e0; e < e1; ++e) wd += __ldg(m.sp_nu + e) * w.q[__ldg(m.sp_rxn + e)];
+      if (P > 0) {
+        const int r0 = __ldg(m.run_ptr + k), r1 = __ldg(m.run_ptr + k + 1);
+        for (int r = r0; r < r1; ++r) wd += part[r];
+      } else {
+        const int e0 = __ldg(m.sp_ptr + k), e1 = __ldg(m.sp_ptr + k + 1);
+        for (int e = e0; e < e1; ++e) wd += __ldg(m.sp_nu + e) * w.q[__ldg(m.sp_rxn + e)];
+      }
       sp.wdot[s] = wd;
       f[s] = __ldg(m.W + k) * wd * irho;
       Qp += sp.hRT[s] * wd;
     }
   }
   const double Q = wsum(Qp) * RT;
-  const double fT = -Q * irho * (1.0 / cp);
+  const double fT = -Q * irho * icp;
 #pragma unroll
   for (int s = 0; s < NPL; ++s)
     if (lane + 32 * s == K) f[s] = fT;
@@ -467,7 +507,11 @@ __device__ void jac_assemble(const DevMech& m, const WarpMem& w, const double (&
 }
 
 // ------------------------------------------------------------------------------------------
-// dense LU of M = I - c J with partial pivoting (ties: lowest row), lane = row
+// dense LU of M = I - c J with partial pivoting (ties: lowest row), lane = row.  The pivot
+// search runs on the warp's integer reductions (the bit pattern of a non-negative double
+// orders like its value), the row permutation lives in shared memory, and each row of U is
+// left scaled by its reciprocal pivot (unit upper factor) so that a solve multiplies by the
+// pivots once instead of once per column.
 // ------------------------------------------------------------------------------------------
 template <int NPL>
 __device__ bool lu_factor(const WarpMem& w, int n, double c, int lane) {
@@ -479,57 +523,43 @@ __device__ bool lu_factor(const WarpMem& w, int n, double c, int lane) {
       const double* jr = w.J + (size_t)r * ld;
       double* lr = w.LU + (size_t)r * ld;
       for (int cc = 0; cc < n; ++cc) lr[cc] = (r == cc ? 1.0 : 0.0) - c * jr[cc];
+      w.perm[r] = r;
     }
   }
-  int myperm[NPL];
-#pragma unroll
-  for (int s = 0; s < NPL; ++s) myperm[s] = lane + 32 * s;
   __syncwarp();
   bool ok = true;
   for (int col = 0; col < n; ++col) {
-    double bv = -1.0;
-    int bi = n;
+    // this lane's best candidate (largest |v|, lower row on ties), then the warp's
+    unsigned long long key = 0ull;
+    unsigned int row = 0xffffffffu;
 #pragma unroll
     for (int s = 0; s < NPL; ++s) {
       const int r = lane + 32 * s;
       if (r >= col && r < n) {
-        const double v = fabs(w.LU[(size_t)r * ld + col]);
-        if (v > bv) { bv = v; bi = r; }
+        const unsigned long long kv = (unsigned long long)__double_as_longlong(fabs(w.LU[(size_t)r * ld + col]));
+        if (row == 0xffffffffu || kv > key) { key = kv; row = (unsigned int)r; }
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(FULLMASK, bv, o);
-      const int oi = __shfl_xor_sync(FULLMASK, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-    }
-    if (!(bv > 0.0) || !isfinite(bv)) { ok = false; break; }
-    if (bi != col) {
+    const unsigned int hi = (unsigned int)(key >> 32), lo = (unsigned int)key;
+    const unsigned int mhi = __reduce_max_sync(FULLMASK, hi);
+    const unsigned int mlo = __reduce_max_sync(FULLMASK, hi == mhi ? lo : 0u);
+    const unsigned int bi = __reduce_min_sync(FULLMASK, (hi == mhi && lo == mlo) ? row : 0xffffffffu);
+    const double bv = __longlong_as_double((long long)(((unsigned long long)mhi << 32) | mlo));
+    if (!(bv > 0.0) || !isfinite(bv) || bi >= (unsigned int)n) { ok = false; break; }
+    if ((int)bi != col) {
       for (int cc = lane; cc < n; cc += 32) {
         const double t = w.LU[(size_t)col * ld + cc];
         w.LU[(size_t)col * ld + cc] = w.LU[(size_t)bi * ld + cc];
         w.LU[(size_t)bi * ld + cc] = t;
       }
-      // track the permutation: position col <-> bi
-      int pc = 0, pb = 0;
-#pragma unroll
-      for (int s = 0; s < NPL; ++s) {
-        if (lane + 32 * s == col) pc = myperm[s];
-        if (lane + 32 * s == bi) pb = myperm[s];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        pc |= __shfl_xor_sync(FULLMASK, pc, o);
-        pb |= __shfl_xor_sync(FULLMASK, pb, o);
-      }
-#pragma unroll
-      for (int s = 0; s < NPL; ++s) {
-        if (lane + 32 * s == col) myperm[s] = pb;
-        if (lane + 32 * s == bi) myperm[s] = pc;
+      if (lane == 0) {
+        const int t = w.perm[col];
+        w.perm[col] = w.perm[bi];
+        w.perm[bi] = t;
       }
     }
     __syncwarp();
-    const double inv = 1.0 / w.LU[(size_t)col * ld + col];
+    const double inv = rcp_nr(w.LU[(size_t)col * ld + col]);
     if (lane == 0) w.invd[col] = inv;
     const double* pr = w.LU + (size_t)col * ld;
 #pragma unroll
@@ -544,14 +574,22 @@ __device__ bool lu_factor(const WarpMem& w, int n, double c, int lane) {
     }
     __syncwarp();
   }
+  if (ok) {
 #pragma unroll
-  for (int s = 0; s < NPL; ++s)
-    if (lane + 32 * s < n) w.perm[lane + 32 * s] = myperm[s];
-  __syncwarp();
+    for (int s = 0; s < NPL; ++s) {
+      const int r = lane + 32 * s;
+      if (r < n) {
+        const double d = w.invd[r];
+        double* lr = w.LU + (size_t)r * ld;
+        for (int cc = r + 1; cc < n; ++cc) lr[cc] *= d;
+      }
+    }
+    __syncwarp();
+  }
   return ok;
 }
 
-// x <- M^{-1} x with the factors in w.LU (x distributed: lane = row)
+// x <- M^{-1} x with the factors of lu_factor (x distributed: lane = row)
 template <int NPL>
 __device__ void lu_solve(const WarpMem& w, int n, double (&x)[NPL], int lane) {
   const int ld = w.ld;
@@ -568,6 +606,7 @@ __device__ void lu_solve(const WarpMem& w, int n, double (&x)[NPL], int lane) {
     }
     b[s] = r < n ? v : 0.0;
   }
+  // L (unit lower) forward substitution
   for (int col = 0; col < n - 1; ++col) {
     const double xc = comp_get<NPL>(b, col);
 #pragma unroll
@@ -576,13 +615,18 @@ __device__ void lu_solve(const WarpMem& w, int n, double (&x)[NPL], int lane) {
       if (r > col && r < n) b[s] -= w.LU[(size_t)r * ld + col] * xc;
     }
   }
-  for (int col = n - 1; col >= 0; --col) {
-    const double xc = comp_get<NPL>(b, col) * w.invd[col];
+  // diag(1/u_kk), then the unit upper factor backward
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    const int r = lane + 32 * s;
+    if (r < n) b[s] *= w.invd[r];
+  }
+  for (int col = n - 1; col > 0; --col) {
+    const double xc = comp_get<NPL>(b, col);
 #pragma unroll
     for (int s = 0; s < NPL; ++s) {
       const int r = lane + 32 * s;
-      if (r == col) b[s] = xc;
-      else if (r < col) b[s] -= w.LU[(size_t)r * ld + col] * xc;
+      if (r < col) b[s] -= w.LU[(size_t)r * ld + col] * xc;
     }
   }
 #pragma unroll
@@ -605,6 +649,17 @@ __device__ __forceinline__ double bdf_gamma(int k) {
     case 4: return 2.0833333333333333;
     case 5: return 2.2833333333333333;
     default: return 2.45;
+  }
+}
+
+__device__ __forceinline__ double bdf_inv_gamma(int k) {
+  switch (k) {
+    case 1: return 1.0;
+    case 2: return 1.0 / 1.5;
+    case 3: return 6.0 / 11.0;
+    case 4: return 12.0 / 25.0;
+    case 5: return 60.0 / 137.0;
+    default: return 1.0 / 2.45;
   }
 }
 
@@ -727,7 +782,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
   int order = 1, n_equal = 0, newton_iters = 0, fails = 0;
   bool need_jac = true, have_lu = false;
   int jac_age = 0;
-  double c_lu = 0.0;
+  double c_lu = 0.0, ic_lu = 0.0;
   float crate = 0.5f;
   double t = 0.0;
   int status = CHEM_CELL_OK;
@@ -745,7 +800,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     double t_new = t + h;
     if (t_new > dt || dt - t_new < hmin) t_new = dt;
     // predictor and the history term psi
-    const double ig = 1.0 / bdf_gamma(order);
+    const double ig = bdf_inv_gamma(order);
 #pragma unroll
     for (int s = 0; s < NPL; ++s) {
       double yp = D[0][s], ps = 0.0;
@@ -769,7 +824,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
       have_lu = false;
       f_at_pred = true;   // f(ypred) doubles as the first Newton residual
     }
-    if (!have_lu || fabs(c / c_lu - 1.0) > 0.3) {
+    if (!have_lu || fabsf((float)(c * ic_lu) - 1.0f) > 0.3f) {
       if (!lu_factor<NPL>(w, n, c, lane)) {
         // singular Newton matrix: shrink the step
         fails++;
@@ -781,10 +836,13 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
       }
       cnt[3]++;
       c_lu = c;
+      ic_lu = 1.0 / c;
       have_lu = true;
       crate = 0.5f;
     }
-    const double lscale = 2.0 / (1.0 + c / c_lu);
+    // modified Newton with a stale h/gamma: scale the correction by 2 / (1 + c / c_lu)
+    const bool rescale = c != c_lu;
+    const double lscale = rescale ? (double)(2.0f / (1.0f + (float)(c * ic_lu))) : 1.0;
     bool converged = false;
     float dn_old = 0.0f;
     newton_iters = 0;
@@ -801,8 +859,10 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
       }
       if (__any_sync(FULLMASK, !ok)) break;
       lu_solve<NPL>(w, n, dy, lane);
+      if (rescale) {
 #pragma unroll
-      for (int s = 0; s < NPL; ++s) dy[s] *= lscale;
+        for (int s = 0; s < NPL; ++s) dy[s] *= lscale;
+      }
       const float dn = wrms<NPL>(dy, isc, n, lane);
       ++newton_iters;
       if (it > 0) crate = fmaxf(0.3f * crate, dn / fmaxf(dn_old, 1e-30f));
@@ -1015,6 +1075,11 @@ __global__ void exp_selftest_kernel(const double* __restrict__ tab, int64_t n, c
     y[i] = exp_t(x[i], tab);
 }
 
+__global__ void log_selftest_kernel(const double* __restrict__ tab, int64_t n, const double* x, double* y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = log_t(x[i], tab);
+}
+
 // ------------------------------------------------------------------------------------------
 // launches
 // ------------------------------------------------------------------------------------------
@@ -1022,6 +1087,12 @@ int launch_exp_selftest(const DevMech& m, int64_t n, const double* x, double* y,
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
   exp_selftest_kernel<<<(int)blocks, 256, 0, s>>>(m.exptab, n, x, y);
   return cuda_check(cudaGetLastError(), "exp_selftest_kernel launch");
+}
+
+int launch_log_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  log_selftest_kernel<<<(int)blocks, 256, 0, s>>>(m.logtab, n, x, y);
+  return cuda_check(cudaGetLastError(), "log_selftest_kernel launch");
 }
 
 static int sm_count() {

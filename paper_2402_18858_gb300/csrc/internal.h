@@ -45,14 +45,28 @@ struct DevMech {
   const int* ref_sp;       // [n_ref]
   const double* P;         // [K][n_ref]
   const double* exptab;    // [128] 2^(j/128), the table of the FP64 exponential below
+  const double* logtab;    // [97][3] F = j/128, 1/F, log F (j = 96..192): the table of log_t below
   const double* compW;     // [K][E] element counts divided by the molar mass (mol/kg)
+  // Exponentials of one right-hand side, in lane rounds: item t < n_tb_end is k_f of reaction
+  // t, then 5 per falloff reaction (k_inf, k_0/k_inf, the three F_cent terms).  Item t is
+  // exp(xarg[4t] + xarg[4t+1] ln T - xarg[4t+2] / T + xarg[4t+3] T).
+  int n_x;
+  const double* xarg;      // [n_x][4]
+  // Lane-balanced species production rates: lane L walks entries bal[i*32 + L], i < bal_P,
+  // each |nu| (bits 0-1), nu < 0 (bit 2), last entry of its run (bit 3), run slot (bits 4-11),
+  // reaction (bits 12-31); 0 = padding.  wdot_k = sum of the run slots run_ptr[k] ..
+  // run_ptr[k+1] - 1 in order.  bal_P = 0: walk the incidence lists instead.
+  int bal_P;
+  const unsigned int* bal;   // [bal_P][32]
+  const int* run_ptr;        // [K+1]
 };
 
 // FP64 exponential by the table-driven method (P. T. P. Tang, "Table-driven implementation of
 // the exponential function in IEEE floating-point arithmetic", ACM TOMS 15, 1989):
 // x = (128 k + j) ln2/128 + r with |r| <= ln2/256, exp(x) = 2^k 2^(j/128) e^r, e^r from its
-// degree-6 Taylor polynomial (truncation < 1e-19 relative).  About 11 FP64 instructions
-// against ~22 FP64-pipe slots for the library exp on GB300; within 2 ulp of it (tested).
+// degree-5 Taylor polynomial (truncation |r|^6/720 < 6e-19 relative, far below half an ulp).
+// About 10 FP64 instructions against ~22 FP64-pipe slots for the library exp on GB300; within
+// 2 ulp of a correctly rounded exp (tested).
 // Arguments below -708 return 0, above 709.78 return +inf, NaN propagates.
 __device__ __forceinline__ double exp_t(double x, const double* __restrict__ tab) {
   const double kInvL = 184.6649652337873;            // 128 / ln 2
@@ -63,8 +77,7 @@ __device__ __forceinline__ double exp_t(double x, const double* __restrict__ tab
   const double nd = t - kMagic;
   const int nn = (int)(unsigned int)(unsigned long long)__double_as_longlong(t);
   const double r = fma(-nd, kL2, fma(-nd, kL1, x));
-  double pr = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-  pr = fma(pr, r, 1.0 / 24.0);
+  double pr = fma(r, 1.0 / 120.0, 1.0 / 24.0);
   pr = fma(pr, r, 1.0 / 6.0);
   pr = fma(pr, r, 0.5);
   pr = fma(pr, r, 1.0);
@@ -79,6 +92,37 @@ __device__ __forceinline__ double exp_t(double x, const double* __restrict__ tab
     else if (x > 709.78) res = __longlong_as_double(0x7ff0000000000000LL);
   }
   return res;
+}
+// FP64 natural logarithm by the table-driven method (P. T. P. Tang, "Table-driven
+// implementation of the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16,
+// 1990): x = 2^k m with m in [0.75, 1.5), F = j/128 the grid point nearest m (j = 96..192),
+// log x = k ln2 + log F + log1p(u), u = (m - F)/F (m - F exact), |u| <= 1/192, log1p(u) from
+// its degree-7 Taylor polynomial (truncation < |u|^8/8: < 1.7e-18 |u| at F = 1, where u is
+// exact, and < 3e-17 of the result elsewhere).  Centring m on 1 keeps log x accurate near
+// x = 1; k ln2 is split (32-bit high part, exact product).
+// tab[3(j-96) + {0, 1, 2}] = F_j, 1/F_j, log F_j.  Positive normal x only: zero, negative,
+// subnormal, inf and NaN take the library log.
+__device__ __forceinline__ double log_t(double x, const double* __restrict__ tab) {
+  const long long b = __double_as_longlong(x);
+  const unsigned int hw = (unsigned int)((unsigned long long)b >> 32);
+  if (hw - 0x00100000u >= 0x7fe00000u) return log(x);
+  const long long frac = b & 0x000fffffffffffffLL;
+  const int up = (int)(frac >> 51);                 // m >= 1.5: use m/2 and k + 1
+  const int j = (int)((frac + (1LL << 52) + (1LL << (44 + up))) >> (45 + up));     // round(128 m)
+  const double* t = tab + 3 * (j - 96);
+  const double m = __longlong_as_double(frac | ((long long)(1023 - up) << 52));
+  const double u = (m - __ldg(t)) * __ldg(t + 1);
+  double pl = fma(u, 1.0 / 7.0, -1.0 / 6.0);
+  pl = fma(pl, u, 0.2);
+  pl = fma(pl, u, -0.25);
+  pl = fma(pl, u, 1.0 / 3.0);
+  pl = fma(pl, u, -0.5);
+  // k as a double without a conversion instruction: 1.5 * 2^52 + k (any sign) has k in its
+  // low bits and the same exponent
+  const int k = (int)(hw >> 20) - 1023 + up;
+  const double kd = __longlong_as_double(0x4338000000000000LL + (long long)k) - 6755399441055744.0;
+  const double kLn2Hi = 0x1.62e42fee00000p-1, kLn2Lo = 1.9082149292705877e-10;
+  return fma(kd, kLn2Hi, __ldg(t + 2)) + fma(kd, kLn2Lo, fma(pl, u * u, u));
 }
 constexpr int kMaxElem = 8;
 
@@ -113,6 +157,7 @@ int gemm_bf16(int epi, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16*
 size_t di_smem_per_warp(const DevMech& m);
 
 int launch_exp_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s);
+int launch_log_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s);
 
 // thermo.cu
 int launch_thermo(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* Y,

@@ -253,3 +253,29 @@ def test_table_exp_against_cuda_exp(lc, gmech):
     torch.cuda.synchronize()
     v = ys.cpu().numpy()
     assert np.isnan(v[0]) and v[1] == np.inf and v[2] == 0.0 and v[3] == 0.0 and v[4] == np.inf
+
+
+def test_table_log_against_cuda_log(lc, gmech):
+    """The kernels' table-driven FP64 log stays within 3 ulp of CUDA's log, including near 1
+    (its own error is about 2 ulp at most, CUDA's under 1)."""
+    rng = np.random.default_rng(4)
+    x = np.concatenate([np.exp(rng.uniform(-700, 700, 200000)), rng.uniform(200, 4000, 100000),
+                        1.0 + rng.uniform(-0.05, 0.05, 100000), 1.0 + rng.uniform(-1e-6, 1e-6, 50000),
+                        rng.uniform(0.5, 2.0, 100000),
+                        [1.0, 2.0, 0.5, 0.75, 1.5, 1.4999999999999998, 2.2250738585072014e-308, 1.7976931348623157e308]])
+    xd = _dev(x)
+    y = torch.empty_like(xd)
+    lc.chem_selftest_log(gmech["h2_9"], xd, y)
+    ref = torch.log(xd)
+    torch.cuda.synchronize()
+    yy, rr = y.cpu().numpy(), ref.cpu().numpy()
+    ulp = np.abs(yy - rr) / np.spacing(np.maximum(np.abs(rr), np.finfo(np.float64).tiny))
+    assert ulp.max() <= 3.0, (ulp.max(), x[np.argmax(ulp)])
+    assert yy[x == 1.0][0] == 0.0
+    spec = _dev(np.array([0.0, -1.0, np.inf, np.nan, 5e-324]))
+    ys = torch.empty_like(spec)
+    lc.chem_selftest_log(gmech["h2_9"], spec, ys)
+    torch.cuda.synchronize()
+    v = ys.cpu().numpy()
+    assert v[0] == -np.inf and np.isnan(v[1]) and v[2] == np.inf and np.isnan(v[3])
+    assert abs(v[4] - np.log(5e-324)) < 1e-12 * abs(np.log(5e-324))
