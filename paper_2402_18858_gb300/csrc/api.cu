@@ -322,8 +322,8 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
       for (int e = 0; e < E; ++e) acc += (double)hm.comp[(size_t)k * E + e] * Linv[(size_t)e * R + r];
       Pm[(size_t)k * R + r] = acc;
     }
-  std::vector<double> exptab(128);
-  for (int j = 0; j < 128; ++j) exptab[j] = (double)std::exp2((long double)j / 128.0L);
+  std::vector<double> exptab(256);
+  for (int j = 0; j < 256; ++j) exptab[j] = (double)std::exp2((long double)j / 256.0L);
   std::vector<double> logtab(3 * 97);
   for (int j = 96; j <= 192; ++j) {
     const long double F = (long double)j / 128.0L;
@@ -402,6 +402,17 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
       bal_P = 0;
     }
   }
+  // two-partner reaction table (see DevMech::rsp2)
+  std::vector<int> rsp2((size_t)std::max(I, 1) * 4, K);
+  int arity2 = 1;
+  for (int jj = 0; jj < I; ++jj) {
+    const int* s = &rsp[(size_t)jj * 8];
+    if (s[3] > 2 || s[7] > 2) arity2 = 0;
+    rsp2[(size_t)jj * 4 + 0] = s[0];
+    rsp2[(size_t)jj * 4 + 1] = s[3] > 1 ? s[1] : K;
+    rsp2[(size_t)jj * 4 + 2] = s[4];
+    rsp2[(size_t)jj * 4 + 3] = s[7] > 1 ? s[5] : K;
+  }
   const int nnz = std::max((int)sp_rxn.size(), 1);
   sp_rxn.resize(nnz, 0);
   sp_nu.resize(nnz, 0.0);
@@ -427,6 +438,7 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   size_t oexp = add(exptab.data(), exptab.size() * 8), ocw = add(compW.data(), compW.size() * 8);
   size_t oxa = add(xarg.data(), xarg.size() * 8), olog = add(logtab.data(), logtab.size() * 8);
   size_t obal = add(bal.data(), bal.size() * 4), orun = add(run_ptr.data(), run_ptr.size() * 4);
+  size_t orsp2 = add(rsp2.data(), rsp2.size() * 4);
   std::vector<char> blob(total, 0);
   for (auto& p : pieces) std::memcpy(blob.data() + p.off, p.src, p.bytes);
   void* d = nullptr;
@@ -457,6 +469,8 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   m.bal_P = bal_P;
   m.bal = (const unsigned int*)(b + obal);
   m.run_ptr = (const int*)(b + orun);
+  m.arity2 = arity2;
+  m.rsp2 = (const int4*)(b + orsp2);
   cm->dmem = d;
   cm->K = K; cm->I = I; cm->E = m.E;
   return CHEM_OK;

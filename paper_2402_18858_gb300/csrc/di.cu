@@ -99,7 +99,7 @@ __host__ __device__ inline size_t warp_doubles(int K, int I, int n, int nT, bool
   size_t ld = pad_ld(n);
   size_t d = (mats ? 2 * (size_t)n * ld : (jac ? (size_t)n * ld : 0));
   const bool alias = mats && jac && jac_terms_in_lu(I, n);
-  d += 5 * (size_t)K + (jac && !alias ? 5 : 1) * (size_t)(I > 0 ? I : 1) + (size_t)kTroeSlots * nT;
+  d += 5 * (size_t)K + 3 + (jac && !alias ? 5 : 1) * (size_t)(I > 0 ? I : 1) + (size_t)kTroeSlots * nT;
   d += (size_t)n + 32 + (size_t)(n + 1) / 2 + 2;
   return (d + 1) & ~size_t(1);   // keep 16-byte alignment per warp
 }
@@ -112,11 +112,11 @@ __device__ __forceinline__ WarpMem carve(double* base, int K, int I, int n, int 
   w.LU = nullptr;
   if (mats || jac) { w.J = p; p += (size_t)n * w.ld; }
   if (mats) { w.LU = p; p += (size_t)n * w.ld; }
-  w.C = p; p += K;
+  w.C = p; p += K + 1;
   w.hRT = p; p += K;
   w.g = p; p += K;
-  w.eg = p; p += K;
-  w.ieg = p; p += K;
+  w.eg = p; p += K + 1;
+  w.ieg = p; p += K + 1;
   const int Ir = I > 0 ? I : 1;
   w.q = p; p += Ir;
   if (jac && mats && jac_terms_in_lu(I, n)) {
@@ -255,10 +255,18 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
   const double irho = sYW * RT * ip;                 // 1 / rho
   const double ctot = rho * sYW;                     // sum of the concentrations
   const double cp = cpp * kR;
-  // pass 2: h/RT, g/RT and the concentrations
+  // pass 2: h/RT, g/RT and the concentrations (and the sentinel slots of the two-partner
+  // reactions, which the production-rate runs of the previous call may have overwritten)
+  double Cs[NPL];
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
     const int k = lane + 32 * s;
+    Cs[s] = 0.0;
+    if (k == K) {
+      w.C[K] = 1.0;
+      w.eg[K] = 1.0;
+      w.ieg[K] = 1.0;
+    }
     if (k < K) {
       const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
       const double hRT = __ldg(a + 5) + T * (__ldg(a + 6) + T * (__ldg(a + 7) + T * (__ldg(a + 8) + T * __ldg(a + 9))))
@@ -267,6 +275,7 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
                         + __ldg(a + 16);
       const double Ck = rho * y[s] * __ldg(m.invW + k);
       w.C[k] = Ck;
+      Cs[s] = Ck;
       w.hRT[k] = hRT;
       w.g[k] = hRT - sR;
       sp.hRT[s] = hRT;
@@ -279,6 +288,7 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
   // into the per-species values, p0/RT with every reactant and RT/p0 with every product
   const double P0RT = (kP0 / kR) * invT, RTP0 = RT * (1.0 / kP0);
   const int R = m.n_ref;
+  const bool two = !JAC && m.arity2;   // warp-uniform
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
     const int k = lane + 32 * s;
@@ -287,7 +297,7 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
       for (int r = 0; r < R; ++r) gs -= __ldg(m.P + (size_t)k * R + r) * w.g[__ldg(m.ref_sp + r)];
       const double e = exp_t(-gs, et);
       w.eg[k] = e * P0RT;
-      w.ieg[k] = rcp_nr(e) * RTP0;
+      w.ieg[k] = rcp_nr(e) * (two ? RTP0 * Cs[s] : RTP0);
     }
   }
   // exponential rounds: k_f of every non-falloff reaction (into w.q, read back by the same
@@ -307,6 +317,27 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
   }
   __syncwarp();
   if (I > nb) troe_phase<JAC>(m, w, invT, ctot, lane);
+  if (two) {
+    // q_j = k_f (C_a C_b - K_c^-1 C_c C_d) = k_f (C_a C_b - (e_a e_b)(u_c u_d)) with
+    // e = exp(-g'/RT) p0/RT and u = exp(g'/RT) (RT/p0) C; a missing partner is the sentinel 1.
+    // No predication on the reaction's arity, one rounding in the difference.
+    for (int j = lane; j < I; j += 32) {
+      const int4 rs = __ldg(m.rsp2 + j);
+      double kf;
+      if (j < nb) kf = w.q[j];
+      else kf = w.tr[kTroeSlots * (j - nb) + 10];
+      if (j >= m.n_elem && j < nb) {
+        double M = ctot;
+#pragma unroll
+        for (int e = 0; e < kMaxEx; ++e) {
+          const int se = __ldg(m.ex_sp + (size_t)j * kMaxEx + e);
+          if (se >= 0) M += __ldg(m.ex_a + (size_t)j * kMaxEx + e) * w.C[se];
+        }
+        kf *= M;
+      }
+      w.q[j] = kf * fma(-(w.eg[rs.x] * w.eg[rs.y]), w.ieg[rs.z] * w.ieg[rs.w], w.C[rs.x] * w.C[rs.y]);
+    }
+  } else
   for (int j = lane; j < I; j += 32) {
     const int4 ra = __ldg((const int4*)(m.rsp + 8 * (size_t)j));
     const int4 rb = __ldg((const int4*)(m.rsp + 8 * (size_t)j + 4));
@@ -686,14 +717,18 @@ __device__ void rescale_D(double (&D)[kMaxOrd + 3][NPL], int order, double fct, 
     const int i = 1 + lane / 5, j = 1 + lane % 5;
     double acc = 0.0;
     if (i <= order && j <= order) {
-      // sum_{l=1..j} R_il (-1)^l C(j, l)
-      double binom = 1.0;
+      // sum_{l=1..j} (-1)^l C(j, l) R_il with R_il = (1/i!) prod_{mm=1..i} (mm - 1 - f l):
+      // integer binomials and one 1/i! per entry, no divisions
+      int binom = 1;
       for (int l = 1; l <= j; ++l) {
-        binom = binom * (double)(j - l + 1) / (double)l;
-        double r = 1.0;
-        for (int mm = 1; mm <= i; ++mm) r *= ((double)(mm - 1) - fct * (double)l) / (double)mm;
-        acc += ((l & 1) ? -binom : binom) * r;
+        binom = binom * (j - l + 1) / l;   // C(j, l), exact in integers
+        const double fl = fct * (double)l;
+        double r = -fl;                    // mm = 1
+        for (int mm = 2; mm <= i; ++mm) r *= (double)(mm - 1) - fl;
+        acc = fma((l & 1) ? -(double)binom : (double)binom, r, acc);
       }
+      const double inv_fact = i == 1 ? 1.0 : i == 2 ? 0.5 : i == 3 ? 1.0 / 6.0 : i == 4 ? 1.0 / 24.0 : 1.0 / 120.0;
+      acc *= inv_fact;
     }
     w.ru[lane] = acc;
   }
@@ -978,7 +1013,7 @@ __device__ __forceinline__ void load_cell(const DevMech& m, int64_t col, int64_t
 }
 
 template <int NPL>
-__global__ void __launch_bounds__(128) di_kernel(DevMech m, int64_t n, int64_t ld, double dt, double* T,
+__global__ void __launch_bounds__(128, 2) di_kernel(DevMech m, int64_t n, int64_t ld, double dt, double* T,
                                                  const double* p, double* Y, const int32_t* idx, DiOpts o,
                                                  int32_t* status, int32_t* stats, unsigned int* queue,
                                                  size_t warp_bytes, const int32_t* n_dev) {

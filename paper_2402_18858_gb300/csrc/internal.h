@@ -44,7 +44,7 @@ struct DevMech {
   int n_ref;               // number of reference species (rank of the composition matrix)
   const int* ref_sp;       // [n_ref]
   const double* P;         // [K][n_ref]
-  const double* exptab;    // [128] 2^(j/128), the table of the FP64 exponential below
+  const double* exptab;    // [256] 2^(j/256), the table of the FP64 exponential below
   const double* logtab;    // [97][3] F = j/128, 1/F, log F (j = 96..192): the table of log_t below
   const double* compW;     // [K][E] element counts divided by the molar mass (mol/kg)
   // Exponentials of one right-hand side, in lane rounds: item t < n_tb_end is k_f of reaction
@@ -59,32 +59,35 @@ struct DevMech {
   int bal_P;
   const unsigned int* bal;   // [bal_P][32]
   const int* run_ptr;        // [K+1]
+  // Two-partner form of the reactions, used when every reaction has at most two reactants and
+  // two products (arity2 = 1): (r0, r1, p0, p1), a missing partner pointing at the sentinel
+  // slot K of the per-species shared-memory vectors, which holds 1.
+  int arity2;
+  const int4* rsp2;          // [I]
 };
 
 // FP64 exponential by the table-driven method (P. T. P. Tang, "Table-driven implementation of
-// the exponential function in IEEE floating-point arithmetic", ACM TOMS 15, 1989):
-// x = (128 k + j) ln2/128 + r with |r| <= ln2/256, exp(x) = 2^k 2^(j/128) e^r, e^r from its
-// degree-5 Taylor polynomial (truncation |r|^6/720 < 6e-19 relative, far below half an ulp).
-// About 10 FP64 instructions against ~22 FP64-pipe slots for the library exp on GB300; within
-// 2 ulp of a correctly rounded exp (tested).
+// the exponential function in IEEE floating-point arithmetic", ACM TOMS 15, 1989), here with a
+// 256-entry table: x = (256 k + j) ln2/256 + r with |r| <= ln2/512, exp(x) = 2^k 2^(j/256) e^r,
+// e^r - 1 from its degree-4 Taylor polynomial (truncation |r|^5/120 < 4e-17 relative, a third
+// of an ulp).  9 FP64 instructions against ~22 FP64-pipe slots for the library exp on GB300;
+// within 2 ulp of a correctly rounded exp (tested).
 // Arguments below -708 return 0, above 709.78 return +inf, NaN propagates.
 __device__ __forceinline__ double exp_t(double x, const double* __restrict__ tab) {
-  const double kInvL = 184.6649652337873;            // 128 / ln 2
-  const double kL1 = 0x1.62e42ff000000p-8;           // ln 2 / 128, high part (32 bits)
-  const double kL2 = -3.2819649005320973e-13;        // ln 2 / 128 - kL1
+  const double kInvL = 369.3299304675746;            // 256 / ln 2
+  const double kL1 = 0x1.62e42ff000000p-9;           // ln 2 / 256, high part (29 bits: nd kL1 exact)
+  const double kL2 = -1.6409824502660487e-13;        // ln 2 / 256 - kL1
   const double kMagic = 6755399441055744.0;          // 1.5 * 2^52: rounds to an integer
   const double t = fma(x, kInvL, kMagic);
   const double nd = t - kMagic;
   const int nn = (int)(unsigned int)(unsigned long long)__double_as_longlong(t);
   const double r = fma(-nd, kL2, fma(-nd, kL1, x));
-  double pr = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  pr = fma(pr, r, 1.0 / 6.0);
-  pr = fma(pr, r, 0.5);
-  pr = fma(pr, r, 1.0);
-  pr *= r;
-  const double tj = __ldg(tab + (nn & 127));
-  double res = fma(tj, pr, tj);
-  res = __longlong_as_double(__double_as_longlong(res) + ((long long)(nn >> 7) << 52));
+  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  q = fma(q, r, 1.0);
+  const double tj = __ldg(tab + (nn & 255));
+  double res = fma(tj * r, q, tj);                   // 2^(j/256) (1 + r q)
+  res = __longlong_as_double(__double_as_longlong(res) + ((long long)(nn >> 8) << 52));
   // |x| >= 708, inf and NaN, detected on the exponent bits (integer pipe, rare branch)
   if (((unsigned int)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu) >= 0x40862000u) {
     if (x != x) res = x;

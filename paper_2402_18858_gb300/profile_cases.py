@@ -3,6 +3,8 @@
     python -m paper_2402_18858_gb300.profile_cases di --cells 8192
     python -m paper_2402_18858_gb300.profile_cases thermo --cells 1048576
     python -m paper_2402_18858_gb300.profile_cases mlp --cells 65536
+    python -m paper_2402_18858_gb300.profile_cases rates --cells 65536
+    python -m paper_2402_18858_gb300.profile_cases jacobian --cells 8192
 
 Each case loads the 30-species workload mechanism, builds seeded inputs, runs the operation
 `--repeats` times (the first is the warm-up) and prints the CUDA-event time of the last one.
@@ -24,7 +26,7 @@ CKPT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models", "ann_c
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["di", "thermo", "mlp"])
+    ap.add_argument("case", choices=["di", "thermo", "mlp", "rates", "jacobian"])
     ap.add_argument("--cells", type=int, default=8192)
     ap.add_argument("--repeats", type=int, default=2)
     a = ap.parse_args()
@@ -41,11 +43,24 @@ def main():
         status = torch.empty(n, dtype=torch.int32, device=dev)
         ws = torch.zeros(256, dtype=torch.uint8, device=dev)
         T, Y = T0.clone(), Y0.clone()
+        stats = torch.zeros(4 * n, dtype=torch.int32, device=dev)
 
         def run():
             T.copy_(T0)
             Y.copy_(Y0)
-            chem.chem_step_di(gm, 5e-6, T, p, Y, status, workspace=ws)
+            chem.chem_step_di(gm, 5e-6, T, p, Y, status, workspace=ws, stats=stats)
+    elif a.case == "rates":
+        wdot = torch.empty_like(Y0)
+        hrr = torch.empty_like(T0)
+
+        def run():
+            chem.chem_rates(gm, T0, p, Y0, wdot, hrr)
+    elif a.case == "jacobian":
+        nn = m.n_species + 1
+        jac = torch.empty(n * nn * nn, dtype=torch.float64, device=dev)
+
+        def run():
+            chem.chem_jacobian(gm, T0, p, Y0, jac)
     elif a.case == "thermo":
         outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
 
@@ -68,7 +83,12 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-    print(json.dumps({"case": a.case, "cells": n, "ms": ms}))
+    out = {"case": a.case, "cells": n, "ms": ms}
+    if a.case == "di":
+        # per-cell means of the kernel's counters: BDF steps, RHS, Jacobians, LU factorisations
+        c = stats.view(4, n).double().mean(dim=1).tolist()
+        out.update(steps=c[0], rhs=c[1], jac=c[2], lu=c[3], failed=int((status != 0).sum().item()))
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
