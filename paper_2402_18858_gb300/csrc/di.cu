@@ -78,7 +78,7 @@ struct WarpMem {
   double* qT;     // I   d q / d T at fixed C
   double* tr;     // 14 per Troe reaction: exponentials, F_cent, P_r, logs, k, dk/d[M], dln k/dT
   double* invd;   // n   reciprocal pivots
-  double* ru;     // 25  step-size change matrix
+  double* ru;     // 64  step-size change matrix (0..24) and R(f) (32..56)
   int* perm;      // n   row permutation of the LU
   int ld;
 };
@@ -100,7 +100,7 @@ __host__ __device__ inline size_t warp_doubles(int K, int I, int n, int nT, bool
   size_t d = (mats ? 2 * (size_t)n * ld : (jac ? (size_t)n * ld : 0));
   const bool alias = mats && jac && jac_terms_in_lu(I, n);
   d += 5 * (size_t)K + 3 + (jac && !alias ? 5 : 1) * (size_t)(I > 0 ? I : 1) + (size_t)kTroeSlots * nT;
-  d += (size_t)n + 32 + (size_t)(n + 1) / 2 + 2;
+  d += (size_t)n + 64 + (size_t)(n + 1) / 2 + 2;
   return (d + 1) & ~size_t(1);   // keep 16-byte alignment per warp
 }
 
@@ -134,7 +134,7 @@ __device__ __forceinline__ WarpMem carve(double* base, int K, int I, int n, int 
   }
   w.tr = p; p += (size_t)kTroeSlots * nT;
   w.invd = p; p += n;
-  w.ru = p; p += 32;
+  w.ru = p; p += 64;
   w.perm = (int*)p;
   return w;
 }
@@ -592,15 +592,26 @@ __device__ bool lu_factor(const WarpMem& w, int n, double c, int lane) {
     __syncwarp();
     const double inv = rcp_nr(w.LU[(size_t)col * ld + col]);
     if (lane == 0) w.invd[col] = inv;
-    const double* pr = w.LU + (size_t)col * ld;
+    // multipliers (lane = row), then the trailing (n-col-1)^2 update spread over all lanes
+    // (element e of the block at row e / m, column e % m, stepped incrementally)
 #pragma unroll
     for (int s = 0; s < NPL; ++s) {
       const int r = lane + 32 * s;
-      if (r > col && r < n) {
-        double* lr = w.LU + (size_t)r * ld;
-        const double l = lr[col] * inv;
-        lr[col] = l;
-        for (int cc = col + 1; cc < n; ++cc) lr[cc] -= l * pr[cc];
+      if (r > col && r < n) w.LU[(size_t)r * ld + col] *= inv;
+    }
+    __syncwarp();
+    const int md = n - col - 1;
+    if (md > 0) {
+      const int q = 32 / md, rm = 32 - q * md;
+      int rr = lane / md, cc = lane - rr * md;
+      double* base = w.LU + (size_t)(col + 1) * ld + (col + 1);
+      const double* pr = w.LU + (size_t)col * ld + (col + 1);
+      for (int e = lane; e < md * md; e += 32) {
+        double* a = base + (size_t)rr * ld + cc;
+        *a = fma(-base[(size_t)rr * ld - 1], pr[cc], *a);
+        rr += q;
+        cc += rm;
+        if (cc >= md) { cc -= md; ++rr; }
       }
     }
     __syncwarp();
@@ -701,57 +712,115 @@ __device__ __forceinline__ float wrms(const double (&x)[NPL], const float (&isc)
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
     if (lane + 32 * s < n) {
-      float v = fminf(fabsf((float)x[s]) * isc[s], 1e15f);
+      float v = fminf(fabsf(narrow_f32(x[s])) * isc[s], 1e15f);
       a += v * v;
     }
   }
   return sqrtf(wsumf(a) / (float)n);
 }
 
-// D[0..order] <- (R(f) U)^T D; R(f)_ij = prod_{l=1..i} (l-1-f j)/l, U_ij = (-1)^i C(j, i).
-// Row 0 and column 0 of R U are (1, 0, ...), so D[0] is untouched and only the 5 x 5 block
-// (i, j >= 1) is formed, one entry per lane.
-template <int NPL>
-__device__ void rescale_D(double (&D)[kMaxOrd + 3][NPL], int order, double fct, const WarpMem& w, int lane) {
-  if (lane < 25) {
-    const int i = 1 + lane / 5, j = 1 + lane % 5;
-    double acc = 0.0;
-    if (i <= order && j <= order) {
-      // sum_{l=1..j} (-1)^l C(j, l) R_il with R_il = (1/i!) prod_{mm=1..i} (mm - 1 - f l):
-      // integer binomials and one 1/i! per entry, no divisions
-      int binom = 1;
-      for (int l = 1; l <= j; ++l) {
-        binom = binom * (j - l + 1) / l;   // C(j, l), exact in integers
-        const double fl = fct * (double)l;
-        double r = -fl;                    // mm = 1
-        for (int mm = 2; mm <= i; ++mm) r *= (double)(mm - 1) - fl;
-        acc = fma((l & 1) ? -(double)binom : (double)binom, r, acc);
-      }
-      const double inv_fact = i == 1 ? 1.0 : i == 2 ? 0.5 : i == 3 ? 1.0 / 6.0 : i == 4 ? 1.0 / 24.0 : 1.0 / 120.0;
-      acc *= inv_fact;
-    }
-    w.ru[lane] = acc;
-  }
-  __syncwarp();
-  double Dn[kMaxOrd + 1][NPL];
+// Step-size change of the backward differences (Shampine & Reichelt): D[1..order] <-
+// (R(f) U)^T D[1..order] with R(f)_il = prod_{m=1..i} (m - 1 - f l) / m and U = R(1), i.e.
+// U_lj = (-1)^l C(j, l); row and column 0 of R U are (1, 0, ...), so D[0] is untouched.
+// Lanes 0..24 hold entry (i, l) = (1 + lane / 5, 1 + lane % 5): first R(f) (one product chain
+// per lane), then (R U)_ij = sum_l R_il U_lj with U from a constant table.
+// The update of D is specialised per order so that only order^2 FMAs are issued.
+struct RescaleLane {
+  int i;             // 1 + lane / 5
+  int j;             // 1 + lane % 5
+  double l;          // 1 + lane % 5 as a double (l in phase 1)
+  double inv_fact;   // 1 / i!
+};
+
+// U_lj = (-1)^l C(j, l), l, j = 1..5 (row l - 1, column j - 1)
+__device__ const double kRescaleU[25] = {-1, -2, -3, -4, -5,  0, 1, 3, 6, 10,  0, 0, -1, -4, -10,
+                                         0, 0, 0, 1, 5,  0, 0, 0, 0, -1};
+
+__device__ __forceinline__ RescaleLane rescale_lane(int lane) {
+  RescaleLane rc;
+  rc.i = 1 + lane / 5;
+  rc.j = 1 + lane % 5;
+  rc.l = (double)rc.j;
+  rc.inv_fact = rc.i == 1 ? 1.0 : rc.i == 2 ? 0.5 : rc.i == 3 ? 1.0 / 6.0 : rc.i == 4 ? 1.0 / 24.0 : 1.0 / 120.0;
+  return rc;
+}
+
+template <int ORD, int NPL>
+__device__ __forceinline__ void rescale_apply(double (&D)[kMaxOrd + 3][NPL], const double* __restrict__ ru) {
+  double Dn[ORD][NPL];
 #pragma unroll
-  for (int j = 1; j <= kMaxOrd; ++j)
+  for (int j = 1; j <= ORD; ++j)
 #pragma unroll
     for (int s = 0; s < NPL; ++s) {
-      double a = 0.0;
-      if (j <= order) {
+      double a = ru[j - 1] * D[1][s];
 #pragma unroll
-        for (int i = 1; i <= kMaxOrd; ++i)
-          if (i <= order) a += w.ru[(i - 1) * 5 + (j - 1)] * D[i][s];
-      }
-      Dn[j][s] = a;
+      for (int i = 2; i <= ORD; ++i) a = fma(ru[(i - 1) * 5 + (j - 1)], D[i][s], a);
+      Dn[j - 1][s] = a;
     }
 #pragma unroll
-  for (int j = 1; j <= kMaxOrd; ++j)
+  for (int j = 1; j <= ORD; ++j)
 #pragma unroll
-    for (int s = 0; s < NPL; ++s)
-      if (j <= order) D[j][s] = Dn[j][s];
+    for (int s = 0; s < NPL; ++s) D[j][s] = Dn[j - 1][s];
+}
+
+template <int NPL>
+__device__ void rescale_D(double (&D)[kMaxOrd + 3][NPL], int order, double fct, const WarpMem& w,
+                          const RescaleLane& rc, int lane) {
+  if (lane < 25) {
+    const double fl = fct * rc.l;
+    double r = -fl;                                   // m = 1
+#pragma unroll
+    for (int mm = 2; mm <= kMaxOrd; ++mm)
+      if (mm <= rc.i) r *= (double)(mm - 1) - fl;
+    w.ru[32 + lane] = r * rc.inv_fact;
+  }
   __syncwarp();
+  if (lane < 25) {
+    const double* Ri = w.ru + 32 + (rc.i - 1) * 5;
+    const double* Uj = kRescaleU + (rc.j - 1);
+    double a = Ri[0] * __ldg(Uj);
+#pragma unroll
+    for (int l = 2; l <= kMaxOrd; ++l) a = fma(Ri[l - 1], __ldg(Uj + 5 * (l - 1)), a);
+    w.ru[lane] = a;
+  }
+  __syncwarp();
+  switch (order) {
+    case 1: rescale_apply<1, NPL>(D, w.ru); break;
+    case 2: rescale_apply<2, NPL>(D, w.ru); break;
+    case 3: rescale_apply<3, NPL>(D, w.ru); break;
+    case 4: rescale_apply<4, NPL>(D, w.ru); break;
+    default: rescale_apply<5, NPL>(D, w.ru); break;
+  }
+  __syncwarp();
+}
+
+// predictor y = sum_{j<=order} D[j] and history term psi = sum_j gamma_j D[j] / gamma_order
+template <int ORD, int NPL>
+__device__ __forceinline__ void bdf_predict(const double (&D)[kMaxOrd + 3][NPL], double (&y)[NPL],
+                                            double (&psi)[NPL], double ig) {
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    double yp = D[0][s] + D[1][s], ps = D[1][s];
+#pragma unroll
+    for (int j = 2; j <= ORD; ++j) {
+      yp += D[j][s];
+      ps = fma(bdf_gamma(j), D[j][s], ps);
+    }
+    y[s] = yp;
+    psi[s] = ps * ig;
+  }
+}
+
+// accepted step: D[order+2] = d - D[order+1], D[order+1] = d, D[j] += D[j+1] (j = order..0)
+template <int ORD, int NPL>
+__device__ __forceinline__ void bdf_accept(double (&D)[kMaxOrd + 3][NPL], const double (&d)[NPL]) {
+#pragma unroll
+  for (int s = 0; s < NPL; ++s) {
+    D[ORD + 2][s] = d[s] - D[ORD + 1][s];
+    D[ORD + 1][s] = d[s];
+#pragma unroll
+    for (int j = ORD; j >= 0; --j) D[j][s] += D[j + 1][s];
+  }
 }
 
 struct DiOpts {
@@ -766,13 +835,15 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
   cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
   LaneSp<NPL> sp;
   CellSc cs;
-  double atol[NPL];
+  // error weights 1 / (atol + rtol |y|) in FP32 (they only steer step control)
+  float atolf[NPL];
   float isc[NPL];
+  const float rtolf = (float)o.rtol;
   bool fin = true;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
     const int i = lane + 32 * s;
-    atol[s] = (i == K) ? o.atol_T : o.atol_Y;
+    atolf[s] = (float)((i == K) ? o.atol_T : o.atol_Y);
     if (i < n && !isfinite(z[s])) fin = false;
   }
   if (__any_sync(FULLMASK, !fin)) return CHEM_CELL_NONFINITE;
@@ -783,6 +854,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
   }
   const double EPS = 2.220446049250313e-16;
   const float ntol = (float)o.newton_tol;
+  const RescaleLane rc = rescale_lane(lane);
   const double ip = 1.0 / pc;
 
   double D[kMaxOrd + 3][NPL];
@@ -791,7 +863,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
   rhs_eval<NPL, false>(m, w, pc, ip, z, f, sp, cs, lane);
   cnt[1]++;
 #pragma unroll
-  for (int s = 0; s < NPL; ++s) isc[s] = 1.0f / (float)(atol[s] + o.rtol * fabs(z[s]));
+  for (int s = 0; s < NPL; ++s) isc[s] = __frcp_rn(fmaf(rtolf, fabsf(narrow_f32(z[s])), atolf[s]));
   const float d0 = wrms<NPL>(z, isc, n, lane), d1 = wrms<NPL>(f, isc, n, lane);
   double h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6 : 0.01 * (double)d0 / (double)d1;
   h0 = fmin(h0, dt);
@@ -827,7 +899,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     const double hmin = 10.0 * EPS * fabs(t) + 1e-300;
     if (t + h > dt) {
       const double hn = dt - t;
-      rescale_D<NPL>(D, order, hn / h, w, lane);
+      rescale_D<NPL>(D, order, hn / h, w, rc, lane);
       h = hn;
       n_equal = 0;
     }
@@ -836,16 +908,17 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     if (t_new > dt || dt - t_new < hmin) t_new = dt;
     // predictor and the history term psi
     const double ig = bdf_inv_gamma(order);
+    switch (order) {
+      case 1: bdf_predict<1, NPL>(D, y, psi, ig); break;
+      case 2: bdf_predict<2, NPL>(D, y, psi, ig); break;
+      case 3: bdf_predict<3, NPL>(D, y, psi, ig); break;
+      case 4: bdf_predict<4, NPL>(D, y, psi, ig); break;
+      default: bdf_predict<5, NPL>(D, y, psi, ig); break;
+    }
 #pragma unroll
     for (int s = 0; s < NPL; ++s) {
-      double yp = D[0][s], ps = 0.0;
-#pragma unroll
-      for (int j = 1; j <= kMaxOrd; ++j)
-        if (j <= order) { yp += D[j][s]; ps += bdf_gamma(j) * D[j][s]; }
-      y[s] = yp;
-      psi[s] = ps * ig;
       d[s] = 0.0;
-      isc[s] = 1.0f / (float)(atol[s] + o.rtol * fabs(yp));
+      isc[s] = __frcp_rn(fmaf(rtolf, fabsf(narrow_f32(y[s])), atolf[s]));
     }
     const double c = h * ig;
     bool f_at_pred = false;
@@ -863,7 +936,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
       if (!lu_factor<NPL>(w, n, c, lane)) {
         // singular Newton matrix: shrink the step
         fails++;
-        rescale_D<NPL>(D, order, 0.25, w, lane);
+        rescale_D<NPL>(D, order, 0.25, w, rc, lane);
         h *= 0.25;
         n_equal = 0;
         have_lu = false;
@@ -912,7 +985,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
       if (jac_age > 0) {
         need_jac = true;       // retry this step with a fresh Jacobian
       } else {
-        rescale_D<NPL>(D, order, 0.25, w, lane);
+        rescale_D<NPL>(D, order, 0.25, w, rc, lane);
         h *= 0.25;
         n_equal = 0;
       }
@@ -921,12 +994,12 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     // local error test
     const float safety = 0.9f * (2 * kNewtonMax + 1) / (float)(2 * kNewtonMax + newton_iters);
 #pragma unroll
-    for (int s = 0; s < NPL; ++s) isc[s] = 1.0f / (float)(atol[s] + o.rtol * fabs(y[s]));
+    for (int s = 0; s < NPL; ++s) isc[s] = __frcp_rn(fmaf(rtolf, fabsf(narrow_f32(y[s])), atolf[s]));
     const float en = wrms<NPL>(d, isc, n, lane) / (float)(order + 1);
     if (!(en <= 1.0f)) {
       fails++;
       const float fac = fmaxf(0.2f, safety * exp2f(-log2f(fmaxf(en, 1e-30f)) / (float)(order + 1)));
-      rescale_D<NPL>(D, order, (double)fac, w, lane);
+      rescale_D<NPL>(D, order, (double)fac, w, rc, lane);
       h *= (double)fac;
       n_equal = 0;
       continue;
@@ -937,18 +1010,12 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     cnt[0]++;
     n_equal++;
     jac_age++;
-#pragma unroll
-    for (int s = 0; s < NPL; ++s) {
-#pragma unroll
-      for (int j = 0; j <= kMaxOrd; ++j) {
-        if (j == order) {
-          D[j + 2][s] = d[s] - D[j + 1][s];
-          D[j + 1][s] = d[s];
-        }
-      }
-#pragma unroll
-      for (int j = kMaxOrd; j >= 0; --j)
-        if (j <= order) D[j][s] += D[j + 1][s];
+    switch (order) {
+      case 1: bdf_accept<1, NPL>(D, d); break;
+      case 2: bdf_accept<2, NPL>(D, d); break;
+      case 3: bdf_accept<3, NPL>(D, d); break;
+      case 4: bdf_accept<4, NPL>(D, d); break;
+      default: bdf_accept<5, NPL>(D, d); break;
     }
     if (jac_age >= kJacMaxAge) need_jac = true;
     if (n_equal < order + 1) continue;
@@ -979,7 +1046,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     // keep h unless the gain is worth a new factorisation (CVODE's threshold of 1.5)
     if (delta == 0 && facf >= 1.0f && facf < 1.5f) continue;
     const double fac = (double)facf;
-    rescale_D<NPL>(D, order, fac, w, lane);
+    rescale_D<NPL>(D, order, fac, w, rc, lane);
     h *= fac;
   }
   if (status == CHEM_CELL_OK) {
@@ -1013,7 +1080,7 @@ __device__ __forceinline__ void load_cell(const DevMech& m, int64_t col, int64_t
 }
 
 template <int NPL>
-__global__ void __launch_bounds__(128, 2) di_kernel(DevMech m, int64_t n, int64_t ld, double dt, double* T,
+__global__ void __launch_bounds__(NPL == 1 ? 160 : 128, 2) di_kernel(DevMech m, int64_t n, int64_t ld, double dt, double* T,
                                                  const double* p, double* Y, const int32_t* idx, DiOpts o,
                                                  int32_t* status, int32_t* stats, unsigned int* queue,
                                                  size_t warp_bytes, const int32_t* n_dev) {
@@ -1212,13 +1279,15 @@ int launch_di(const DevMech& m, int64_t n, int64_t ld, double dt, double* T, con
   int dev = 0, per_sm = 0, max_threads_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
-  // persistent grid: the block shape (1..4 warps) that keeps the most warps resident per SM
+  // persistent grid: the block shape (1..5 warps) that keeps the most warps resident per SM
   auto best_shape = [&](auto kern) -> int {
     int best_w = 0;
     const int optin = smem_optin();
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    for (int cand = 4; cand >= 1; --cand) {
-      if ((size_t)cand * wb > (size_t)optin) continue;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return cuda_check(cudaGetLastError(), "di_kernel attributes");
+    for (int cand = 5; cand >= 1; --cand) {
+      if ((size_t)cand * wb > (size_t)optin || 32 * cand > fa.maxThreadsPerBlock) continue;
       int blocks = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * cand, (size_t)cand * wb);
       if (blocks * cand > best_w) { best_w = blocks * cand; wpb = cand; per_sm = blocks; }

@@ -129,6 +129,17 @@ __device__ __forceinline__ double log_t(double x, const double* __restrict__ tab
 }
 constexpr int kMaxElem = 8;
 
+// FP64 -> FP32 on the integer pipe for values that only steer heuristics or feed FP32 sums
+// (exponent rebias, mantissa truncated: relative error below 2^-23).  |x| < 2^-126 gives a
+// signed zero, |x| >= 2^128, inf and NaN give a signed inf.
+__device__ __forceinline__ float narrow_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
+  const unsigned int e = (hi >> 20) & 0x7ffu, sgn = hi & 0x80000000u;
+  const unsigned int f = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(e > 896u ? (e < 1151u ? (sgn | f) : (sgn | 0x7f800000u)) : sgn);
+}
+
 struct HostMech;   // parsed mechanism (host)
 const DevMech& mech_dev(chem_mech m);
 

@@ -5,8 +5,8 @@
 // c_p, h and the Newton solve are FP64.  The Wilke viscosity and the conductivity
 // combining rule cost O(K^2) per cell; on GB300 FP64 issue (2 lanes/clock/SM) would make
 // them compute-bound far above the HBM time, so the mixed-precision mode evaluates those
-// sums in FP32 (the fits themselves are accurate to percent level) while the FP64 mode is
-// kept for reference and parity.
+// sums in FP32 (the fits themselves are accurate to percent level) and keeps the FP64 pipe
+// for the c_p and h sums alone, while the FP64 mode is kept for reference and parity.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,35 +18,41 @@
 
 namespace chem {
 
-// Shared-memory copy of the tables one block needs: NASA-7 coefficients transposed to
-// [range][coefficient][species] (cp/R: a1..a5, h/RT: a6 is the only extra term), the
-// transport fits and the Wilke constants.
+// Shared-memory copy of the tables one block needs: NASA-7 coefficients divided by the molar
+// mass and transposed to [range][coefficient][species] (cp/R: a1..a5, h/RT: a6 is the only
+// extra term), the transport fits, and the Wilke constants: in FP64 mode A_kj and B_kj, in the
+// mixed mode the three coefficients of the expanded form (see thermo_kernel).
 template <typename real>
 struct ThermoSmem {
-  double* c;     // [2][6][K]  a1..a5 and a6 per range
+  double* c;     // [2][6][K]  a_qk / W_k
   real* tr;      // [8][K]     ln mu (4), ln lambda (4)
-  real* wA;      // [K][K]
-  real* wB;      // [K][K]
+  real* wA;      // FP64 mode: [K][K] A_kj
+  real* wB;      // FP64 mode: [K][K] B_kj
+  float4* w3;    // mixed mode: [K][K] (A, A B, A B^2, 0)
+  float* invW;   // mixed mode: [K]
 };
 
 template <typename real>
 __host__ __device__ inline size_t thermo_smem_bytes(int K, bool transport) {
   size_t b = (size_t)12 * K * sizeof(double);
-  if (transport) b += ((size_t)8 * K + 2 * (size_t)K * K) * sizeof(real);
+  if (transport) {
+    if (sizeof(real) == sizeof(double)) b += ((size_t)8 * K + 2 * (size_t)K * K) * sizeof(real);
+    else b += (size_t)8 * K * sizeof(float) + (size_t)K * K * sizeof(float4) + (size_t)K * sizeof(float) + 16;
+  }
   return b;
 }
 
 // mixture c_p (J/kg/K) and h (J/kg): the species sums are folded into mixture polynomial
-// coefficients A_i = sum_k (Y_k / W_k) a_ik (one FMA per coefficient and species), then
+// coefficients A_i = sum_k Y_k (a_ik / W_k) (one FMA per coefficient and species), then
 // c_p = R sum_i A_i T^i and h = R T (sum_i A_i T^i / (i+1) + A_5 / T)
 template <int KC>
 __device__ __forceinline__ void mix_cp_h(const double* __restrict__ c, int K, double T, double Tmid,
-                                         const double* yw, double& cp, double& h) {
+                                         const double* yv, double& cp, double& h) {
   const double* cr = c + (T >= Tmid ? 6 * K : 0);
   double A0 = 0, A1 = 0, A2 = 0, A3 = 0, A4 = 0, A5 = 0;
 #pragma unroll
   for (int k = 0; k < (KC ? KC : K); ++k) {
-    const double y = yw[k];
+    const double y = yv[k];
     A0 = fma(y, cr[k], A0);
     A1 = fma(y, cr[K + k], A1);
     A2 = fma(y, cr[2 * K + k], A2);
@@ -70,35 +76,51 @@ __global__ void __launch_bounds__(128) thermo_kernel(DevMech m, int64_t n, int64
   ThermoSmem<real> S;
   S.c = tsm;
   S.tr = (real*)(tsm + 12 * K);
-  S.wA = S.tr + 8 * K;
-  S.wB = S.wA + K * K;
+  S.wA = S.wB = nullptr;
+  S.w3 = nullptr;
+  S.invW = nullptr;
+  if (MIXED) {
+    // float4 table 16-byte aligned after the FP32 fits
+    S.w3 = (float4*)(((uintptr_t)(S.tr + 8 * K) + 15) & ~(uintptr_t)15);
+    S.invW = (float*)(S.w3 + K * K);
+  } else {
+    S.wA = S.tr + 8 * K;
+    S.wB = S.wA + K * K;
+  }
   for (int i = threadIdx.x; i < 12 * K; i += blockDim.x) {
     const int rg = i / (6 * K), q = (i / K) % 6, k = i % K;
     const double* a = m.th + ((size_t)k * 2 + rg) * kThermoStride;
-    S.c[i] = __ldg(a + (q < 5 ? q : 10));     // cp/R coefficients a1..a5, then a6
+    S.c[i] = __ldg(a + (q < 5 ? q : 10)) * __ldg(m.invW + k);   // cp/R coefficients a1..a5, then a6
   }
   if (transport) {
     for (int i = threadIdx.x; i < 8 * K; i += blockDim.x) S.tr[i] = (real)__ldg(m.tr + (size_t)(i % K) * 8 + i / K);
     for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
-      S.wA[i] = (real)__ldg(m.wA + i);
-      S.wB[i] = (real)__ldg(m.wB + i);
+      if (MIXED) {
+        const double A = __ldg(m.wA + i), B = __ldg(m.wB + i);
+        S.w3[i] = make_float4((float)A, (float)(A * B), (float)(A * B * B), 0.0f);
+      } else {
+        S.wA[i] = (real)__ldg(m.wA + i);
+        S.wB[i] = (real)__ldg(m.wB + i);
+      }
     }
+    if (MIXED)
+      for (int i = threadIdx.x; i < K; i += blockDim.x) S.invW[i] = (float)__ldg(m.invW + i);
   }
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    double yw[KC ? KC : CHEM_MAX_SPECIES];
+    double yv[KC ? KC : CHEM_MAX_SPECIES];
     double sYW = 0.0;
 #pragma unroll
     for (int k = 0; k < (KC ? KC : K); ++k) {
-      yw[k] = Y[(size_t)k * ld + i] * __ldg(m.invW + k);
-      sYW += yw[k];
+      yv[k] = Y[(size_t)k * ld + i];
+      sYW = fma(yv[k], __ldg(m.invW + k), sYW);
     }
     double Tc = T[i], cp, h;
     if (h_in) {
       const double ht = h_in[i];
       for (int it = 0; it < 50; ++it) {
-        mix_cp_h<KC>(S.c, K, Tc, m.Tmid, yw, cp, h);
+        mix_cp_h<KC>(S.c, K, Tc, m.Tmid, yv, cp, h);
         double Tn = Tc - (h - ht) / cp;
         Tn = fmin(fmax(Tn, 200.0), 6000.0);
         const bool done = fabs(Tn - Tc) < 1e-9;
@@ -107,46 +129,89 @@ __global__ void __launch_bounds__(128) thermo_kernel(DevMech m, int64_t n, int64
       }
       T_out[i] = Tc;
     }
-    mix_cp_h<KC>(S.c, K, Tc, m.Tmid, yw, cp, h);
+    mix_cp_h<KC>(S.c, K, Tc, m.Tmid, yv, cp, h);
     if (cp_out) cp_out[i] = cp;
     if (h_out) h_out[i] = h;
     if (!transport) continue;
-    // mole fractions and species properties (ln mu, ln lambda cubic in ln T)
-    real X[KC ? KC : CHEM_MAX_SPECIES], smu[KC ? KC : CHEM_MAX_SPECIES], ismu[KC ? KC : CHEM_MAX_SPECIES];
-    const real isYW = (real)(1.0 / sYW);
-    const real L = (real)log(Tc);
-    real l1 = 0, l2 = 0;
+    if (MIXED) {
+      // FP32 transport.  Wilke's denominator D_k = sum_j X_j A_kj (1 + s_k B_kj / s_j)^2 with
+      // s = sqrt(mu) expands into three sums over j with per-cell vectors X_j, X_j / s_j and
+      // X_j / s_j^2: D_k = sum A X + 2 s_k sum (A B) (X / s) + s_k^2 sum (A B^2)(X / s^2),
+      // all terms positive (no cancellation), 3 FMAs per species pair.
+      float X[KC ? KC : CHEM_MAX_SPECIES], sm[KC ? KC : CHEM_MAX_SPECIES];
+      float vx[KC ? KC : CHEM_MAX_SPECIES], wx[KC ? KC : CHEM_MAX_SPECIES];
+      const float isYW = __frcp_rn(narrow_f32(sYW));
+      const float L = logf(narrow_f32(Tc));
+      float l1 = 0.0f, l2 = 0.0f;
 #pragma unroll
-    for (int k = 0; k < (KC ? KC : K); ++k) {
-      X[k] = (real)yw[k] * isYW;
-      const real lnmu = S.tr[k] + L * (S.tr[K + k] + L * (S.tr[2 * K + k] + L * S.tr[3 * K + k]));
-      const real lnlam = S.tr[4 * K + k] + L * (S.tr[5 * K + k] + L * (S.tr[6 * K + k] + L * S.tr[7 * K + k]));
-      // sqrt(mu_k) = exp(ln mu_k / 2); lambda_k = exp(ln lambda_k)
-      smu[k] = exp(lnmu * (real)0.5);
-      ismu[k] = (real)1 / smu[k];
-      const real lam = exp(lnlam);
-      l1 += X[k] * lam;
-      l2 += X[k] / lam;
-    }
-    if (kappa_out) kappa_out[i] = 0.5 * ((double)l1 + 1.0 / (double)l2);
-    if (mu_out) {
-      // Wilke: mu = sum_k X_k mu_k / sum_j X_j Phi_kj,
-      // Phi_kj = (1 + sqrt(mu_k/mu_j) (W_j/W_k)^(1/4))^2 / sqrt(8 (1 + W_k/W_j))
-      real mu = 0;
-#pragma unroll 2
       for (int k = 0; k < (KC ? KC : K); ++k) {
-        real den = 0;
-        const real sk = smu[k];
-        const real* A = S.wA + k * K;
-        const real* B = S.wB + k * K;
-#pragma unroll
-        for (int j = 0; j < (KC ? KC : K); ++j) {
-          const real t = (real)1 + sk * ismu[j] * B[j];
-          den += X[j] * A[j] * t * t;
-        }
-        mu += X[k] * sk * sk / den;
+        X[k] = narrow_f32(yv[k]) * S.invW[k] * isYW;
+        const float lnmu = S.tr[k] + L * (S.tr[K + k] + L * (S.tr[2 * K + k] + L * S.tr[3 * K + k]));
+        const float lnlam = S.tr[4 * K + k] + L * (S.tr[5 * K + k] + L * (S.tr[6 * K + k] + L * S.tr[7 * K + k]));
+        sm[k] = expf(0.5f * lnmu);
+        const float ism = expf(-0.5f * lnmu);
+        l1 = fmaf(X[k], expf(lnlam), l1);
+        l2 = fmaf(X[k], expf(-lnlam), l2);
+        vx[k] = X[k] * ism;
+        wx[k] = vx[k] * ism;
       }
-      mu_out[i] = (double)mu;
+      if (kappa_out) kappa_out[i] = 0.5 * ((double)l1 + (double)__frcp_rn(l2));
+      if (mu_out) {
+        float mu = 0.0f;
+#pragma unroll 2
+        for (int k = 0; k < (KC ? KC : K); ++k) {
+          const float4* W3 = S.w3 + k * K;
+          float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
+#pragma unroll
+          for (int j = 0; j < (KC ? KC : K); ++j) {
+            const float4 c = W3[j];
+            d0 = fmaf(c.x, X[j], d0);
+            d1 = fmaf(c.y, vx[j], d1);
+            d2 = fmaf(c.z, wx[j], d2);
+          }
+          const float sk = sm[k];
+          const float den = fmaf(sk, fmaf(sk, d2, 2.0f * d1), d0);
+          mu = fmaf(X[k] * sk * sk, __frcp_rn(den), mu);
+        }
+        mu_out[i] = (double)mu;
+      }
+    } else {
+      // FP64 reference form: Wilke mu = sum_k X_k mu_k / sum_j X_j Phi_kj,
+      // Phi_kj = (1 + sqrt(mu_k/mu_j) (W_j/W_k)^(1/4))^2 / sqrt(8 (1 + W_k/W_j)),
+      // mixture-averaged conductivity 0.5 (sum X lambda + 1 / sum X / lambda)
+      real X[KC ? KC : CHEM_MAX_SPECIES], smu[KC ? KC : CHEM_MAX_SPECIES], ismu[KC ? KC : CHEM_MAX_SPECIES];
+      const real isYW = (real)(1.0 / sYW);
+      const real L = (real)log(Tc);
+      real l1 = 0, l2 = 0;
+#pragma unroll
+      for (int k = 0; k < (KC ? KC : K); ++k) {
+        X[k] = (real)(yv[k] * __ldg(m.invW + k)) * isYW;
+        const real lnmu = S.tr[k] + L * (S.tr[K + k] + L * (S.tr[2 * K + k] + L * S.tr[3 * K + k]));
+        const real lnlam = S.tr[4 * K + k] + L * (S.tr[5 * K + k] + L * (S.tr[6 * K + k] + L * S.tr[7 * K + k]));
+        smu[k] = exp(lnmu * (real)0.5);
+        ismu[k] = (real)1 / smu[k];
+        const real lam = exp(lnlam);
+        l1 += X[k] * lam;
+        l2 += X[k] / lam;
+      }
+      if (kappa_out) kappa_out[i] = 0.5 * ((double)l1 + 1.0 / (double)l2);
+      if (mu_out) {
+        real mu = 0;
+#pragma unroll 2
+        for (int k = 0; k < (KC ? KC : K); ++k) {
+          real den = 0;
+          const real sk = smu[k];
+          const real* A = S.wA + k * K;
+          const real* B = S.wB + k * K;
+#pragma unroll
+          for (int j = 0; j < (KC ? KC : K); ++j) {
+            const real t = (real)1 + sk * ismu[j] * B[j];
+            den += X[j] * A[j] * t * t;
+          }
+          mu += X[k] * sk * sk / den;
+        }
+        mu_out[i] = (double)mu;
+      }
     }
   }
 }
