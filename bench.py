@@ -172,6 +172,38 @@ def run_reference(args, cfg, m, m_path):
 
 
 # ------------------------------------------------------------------------------------------
+# PaSR source assembly (the step after the chemistry step): HBM-bound, thread per cell
+# ------------------------------------------------------------------------------------------
+def run_pasr(gm, m, N, dt, Y0, Y1, seed, dev):
+    import torch
+    from paper_2402_18858_gb300 import chem
+    tf = wl.make_turbulence(N, seed)
+    rho, k, eps, nu = (torch.as_tensor(a, device=dev) for a in (tf.rho, tf.k, tf.eps, tf.nu))
+    omega = torch.empty_like(Y0)
+    kap = torch.empty_like(rho)
+    s = torch.cuda.current_stream()
+    times = []
+    for r in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        chem.chem_pasr_source(gm, dt, rho, Y0, Y1, k, eps, nu, omega, kap)
+        e1.record(s)
+        torch.cuda.synchronize()
+        if r:
+            times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    K = m.n_species
+    bytes_cell = (3 * K + 5) * 8          # Y0, Y1, rho, k, eps, nu read; omega, kappa written
+    gbs = N * bytes_cell / (ms * 1e-3) / 1e9
+    kap_np = kap.cpu().numpy()
+    return {"workload": f"{N} cells, {K} species, seeded sub-grid fields (5 % laminar)",
+            "ms": ms, "cells_per_s": N / (ms * 1e-3), "bytes_per_cell": bytes_cell,
+            "kappa_mean": float(kap_np.mean()), "kappa_laminar_or_1": float((kap_np == 1.0).mean()),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": 6780.0, "unit": "GB/s", "frac": gbs / 6780.0,
+                         "kernel": "pasr_kernel", "peak_source": "MEASURED_PEAKS hbm_gbs"}}
+
+
+# ------------------------------------------------------------------------------------------
 # learned step (ANN + DI fallback): train on DI-generated states, then time inference
 # ------------------------------------------------------------------------------------------
 ANN_WORKLOAD = "ann_c_30sp_2m"
@@ -206,9 +238,14 @@ def run_ann(args, m, gm, di_rate):
         provenance = {"source": "trained in this run", "train_cells": args.ann_train_cells,
                       "train_epochs": args.ann_epochs, "data_generation_s": gen_s, "train_s": trn["seconds"],
                       "train_samples_per_s": trn["samples_per_s"]}
+    # two operating points of the learned step, both with a fallback DI at rtol 1e-5 (the
+    # fallback's own error stays far below the network's): "fast" falls back on range and
+    # element-residual checks only, "accurate" also on a predicted |dT| above 30 K
+    points = {"fast": dict(elem_tol=ANN_ELEM_TOL, dT_max=0.0, di_rtol=1e-5, di_atol_Y=1e-10),
+              "accurate": dict(elem_tol=ANN_ELEM_TOL, dT_max=30.0, di_rtol=1e-5, di_atol_Y=1e-10)}
     # accuracy against DI on held-out cells (DI is within 1e-6 of the FP64 oracle)
     ev_data = tr.di_states(gm, m, 100_000, 3, dt)
-    ev = tr.evaluate(gm, ann, ev_data, dt, repeats=1, elem_tol=ANN_ELEM_TOL)
+    errs = {k: tr.evaluate(gm, ann, ev_data, dt, repeats=1, **o) for k, o in points.items()}
     del ev_data
     # throughput of ANN + fallback on the full inference batch (2 M cells), and the MLP alone
     n = args.ann_cells
@@ -221,31 +258,39 @@ def run_ann(args, m, gm, di_rate):
     status = torch.empty(n, dtype=torch.int32, device=dev)
     ws = torch.empty(chem.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device=dev)
     s = torch.cuda.current_stream()
-    best, best_mlp = 1e30, 1e30
     X = torch.empty((n, 64), dtype=torch.bfloat16, device=dev)
     Uo = torch.empty((n, ann.n_out_pad), dtype=torch.float32, device=dev)
     chem.chem_ann_features(ann, T0, p, Y0, X)
-    for _ in range(3):
-        T.copy_(T0)
-        Y.copy_(Y0)
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(s)
-        chem.chem_step_ann(gm, ann, dt, T, p, Y, status, ws, elem_tol=ANN_ELEM_TOL)
-        e1.record(s)
-        chem.chem_ann_forward(ann, X, Uo, ws)
-        e2.record(s)
-        torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1))
-        best_mlp = min(best_mlp, e1.elapsed_time(e2))
-    fb = float((status != 0).float().mean().item())
-    mlp_tf = mlp_flops_per_cell(ann.dims) * n / (best_mlp * 1e-3) / 1e12
-    rate = n / (best * 1e-3)
+    best_mlp = 1e30
     report = {"workload": f"{ANN_WORKLOAD}: MLP {ann.dims}, BF16 tcgen05, {n} cells, dt {dt}",
-              "network": provenance,
-              "cells_per_s": rate, "ms": best, "fallback_fraction": fb, "speedup_vs_di": rate / di_rate,
-              "elem_tol": ANN_ELEM_TOL,
-              "error_vs_di_100k_heldout": {"fallback_fraction": ev["fallback_fraction"], **ev["all_cells"]},
-              "mlp_ms": best_mlp, "mlp_tflops": mlp_tf, "mlp_cells_per_s": n / (best_mlp * 1e-3)}
+              "network": provenance, "points": {}}
+    for name, o in points.items():
+        best = 1e30
+        for _ in range(3):
+            T.copy_(T0)
+            Y.copy_(Y0)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(s)
+            chem.chem_step_ann(gm, ann, dt, T, p, Y, status, ws, **o)
+            e1.record(s)
+            chem.chem_ann_forward(ann, X, Uo, ws)
+            e2.record(s)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+            best_mlp = min(best_mlp, e1.elapsed_time(e2))
+        fb = float((status != 0).float().mean().item())
+        rate = n / (best * 1e-3)
+        ev = errs[name]
+        report["points"][name] = {"options": o, "cells_per_s": rate, "ms": best, "fallback_fraction": fb,
+                                  "speedup_vs_di": rate / di_rate,
+                                  "error_vs_di_100k_heldout": {"fallback_fraction": ev["fallback_fraction"],
+                                                               **ev["all_cells"]}}
+    mlp_tf = mlp_flops_per_cell(ann.dims) * n / (best_mlp * 1e-3) / 1e12
+    acc = report["points"]["accurate"]
+    report.update({"cells_per_s": acc["cells_per_s"], "speedup_vs_di": acc["speedup_vs_di"],
+                   "fallback_fraction": acc["fallback_fraction"],
+                   "error_vs_di_100k_heldout": acc["error_vs_di_100k_heldout"],
+                   "mlp_ms": best_mlp, "mlp_tflops": mlp_tf, "mlp_cells_per_s": n / (best_mlp * 1e-3)})
     roof = {"bound": "tensor", "achieved": mlp_tf, "peak": 1937.2, "unit": "TFLOP/s", "frac": mlp_tf / 1937.2,
             "traffic": None, "kernel": "gemm_bf16_kernel (MLP forward, 2 M cells)",
             "peak_source": "MEASURED_PEAKS bf16_tflops (burst)"}
@@ -412,6 +457,9 @@ def main():
     th_flops_cell = thermo_fp64_flops(m.n_species)
     th_tf = th_flops_cell * N / (th_ms * 1e-3) / 1e12
 
+    # PaSR filtered source from this step (Y0 -> Y after DI) with seeded sub-grid fields
+    pasr = run_pasr(gm, m, N, cfg["dt"], Y0, Y, cfg["state_seed"] + 3, dev)
+
     # end to end through the public API from pinned host buffers (copies inside the timed region)
     hT = torch.as_tensor(st.T).pin_memory()
     hY = torch.as_tensor(st.Y).pin_memory()
@@ -486,6 +534,7 @@ def main():
             "ann": ann["report"] if ann else None,
             "tensor_roofline": ann["roofline"] if ann else None,
             "serve": serve,
+            "pasr": pasr,
         }
         print(json.dumps(line), flush=True)
     if dist:

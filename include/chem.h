@@ -148,7 +148,10 @@ typedef struct chem_ann_s* chem_ann;
  * stored BF16 [n, 64] (zero padded).  Outputs u_k = (F(Y_k(t+dt)) - F(Y_k(t)) - mu_k)/sigma_k,
  * FP32 [n, n_out_pad] with n_out_pad = 32 (K <= 32) or 64.  Normalisation block (floats):
  * in_mean[n_in], in_std[n_in], in_min[n_in], in_max[n_in], out_mean[K], out_std[K],
- * n_in = K + 2. */
+ * n_in = K + 2.
+ * chem_ann_create: n_hidden GELU layers of hidden[l] units (1..8192 each; widths that are not
+ * multiples of 8 are stored rounded up with zero-weight units that stay zero, so chem_ann_info
+ * reports the stored widths), weights N(0, 2/fan_in), zero biases, seeded. */
 int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t seed, chem_ann* out);
 void chem_ann_free(chem_ann ann);
 int chem_ann_info(chem_ann ann, int* n_in, int* n_out, int* n_layers, int* dims /* [n_layers+1] */,
@@ -274,6 +277,28 @@ void chem_server_free(chem_server server);
 int thermo_props(chem_mech mech, int64_t n, int64_t ld, const double* T, const double* Y,
                  double* cp, double* h, double* mu, double* kappa, const double* h_in,
                  double* T_out, int mixed_precision, chem_stream stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* PaSR filtered reaction source (the paper's swirl-flame LES closes turbulence-chemistry    */
+/* interaction with the partially stirred reactor model and feeds it the chemistry step:    */
+/* Sec. 3, "the ANN model only substitutes the direct integration of source terms within    */
+/* the PaSR model"; chemical time from the slowest species formation rate, mixing time from  */
+/* the Taylor and Kolmogorov scales)                                                         */
+/* ---------------------------------------------------------------------------------------- */
+/* From the states before (Y0) and after (Y1) one chemistry step of length dt, per cell:
+ *   kappa[i]  = tau_c / (tau_c + tau_mix) (1 when both are 0),
+ *   tau_mix   = sqrt(sqrt(nu / eps) * k_sgs / eps), or 0 when k_sgs <= 0 or eps <= 0,
+ *   tau_c     = max over species with Y1 >= y_min and Y1 - Y0 > r_min Y1 of
+ *               dt Y1 / (Y1 - Y0), or 0 when there is none,
+ *   omega[k * ld + i] = kappa rho (Y1 - Y0) / dt   (kg/m^3/s).
+ * rho (kg/m^3), k_sgs (m^2/s^2), eps (m^2/s^3) and nu (m^2/s) are per-cell arrays [n]; Y0, Y1
+ * and omega are species-major [K][ld]; kappa [n] may be NULL.  y_min < 0 and r_min < 0 select
+ * the defaults 1e-10 and 1e-9.  tau_mix is formed in FP32 (relative error below 1e-6), the
+ * source differences and products in FP64.  Returns CHEM_E_ARG for dt <= 0 or null arrays. */
+int chem_pasr_source(chem_mech mech, int64_t n, int64_t ld, double dt, const double* rho,
+                     const double* Y0, const double* Y1, const double* k_sgs, const double* eps,
+                     const double* nu, double y_min, double r_min, double* omega, double* kappa,
+                     chem_stream stream);
 
 /* Testing hook: y[i] = exp(x[i]) by the library's own FP64 exponential (the table-driven
  * method the kernels use), for comparison with CUDA's exp.  Device pointers, n >= 0. */

@@ -56,6 +56,7 @@ def lib(auto_build: bool = False):
         L.chem_workspace_bytes.argtypes = [vp, i64]
         L.chem_workspace_bytes.restype = C.c_size_t
         L.thermo_props.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
+        L.chem_pasr_source.argtypes = [vp, i64, i64, dbl, vp, vp, vp, vp, vp, vp, dbl, dbl, vp, vp, vp]
         L.chem_last_error.restype = C.c_char_p
         L.chem_fp64_peak_gflops.argtypes = [C.POINTER(dbl), vp]
         L.chem_selftest_exp.argtypes = [vp, i64, vp, vp, vp]
@@ -180,6 +181,18 @@ def thermo_props(m: Mech, T, Y, cp=None, h=None, mu=None, kappa=None, h_in=None,
     _check(lib().thermo_props(m.handle, n, ld, _ptr(T, f64), _ptr(Y, f64), _ptr(cp, f64),
                               _ptr(h, f64), _ptr(mu, f64), _ptr(kappa, f64), _ptr(h_in, f64),
                               _ptr(T_out, f64), int(bool(mixed_precision)), _stream(stream)))
+
+
+def chem_pasr_source(m: Mech, dt: float, rho, Y0, Y1, k_sgs, eps, nu, omega, kappa=None,
+                     y_min: float = -1.0, r_min: float = -1.0, n: Optional[int] = None, stream=None) -> None:
+    ld = _ld(Y0, m)
+    if _ld(Y1, m) != ld or _ld(omega, m) != ld:
+        raise ValueError("Y0, Y1 and omega must share the species-major layout")
+    n = ld if n is None else n
+    f64 = torch.float64
+    _check(lib().chem_pasr_source(m.handle, n, ld, float(dt), _ptr(rho, f64), _ptr(Y0, f64), _ptr(Y1, f64),
+                                  _ptr(k_sgs, f64), _ptr(eps, f64), _ptr(nu, f64), float(y_min), float(r_min),
+                                  _ptr(omega, f64), _ptr(kappa, f64), _stream(stream)))
 
 
 def chem_fp64_peak_gflops(stream=None) -> float:

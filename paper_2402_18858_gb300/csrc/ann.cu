@@ -523,13 +523,20 @@ int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t se
   a->n_out_pad = a->K <= 32 ? 32 : 64;
   a->L = n_hidden + 1;
   a->dims[0] = kInPad;
+  // hidden widths are stored rounded up to a multiple of 8 (16-byte rows for the TMA loads);
+  // the extra units start with zero weights and biases, so their activations, gradients and
+  // Adam updates stay exactly zero and the network is the one with the requested widths
+  int real[kMaxLayers + 1] = {0};
+  real[0] = a->n_in;
   for (int l = 0; l < n_hidden; ++l) {
-    if (hidden[l] < 8 || hidden[l] % 8 != 0 || hidden[l] > 8192) {
+    if (hidden[l] < 1 || hidden[l] > 8192) {
       delete a;
-      return set_error(CHEM_E_ARG, "chem_ann_create: hidden widths must be multiples of 8 in [8, 8192]");
+      return set_error(CHEM_E_ARG, "chem_ann_create: hidden widths must be in [1, 8192]");
     }
-    a->dims[l + 1] = hidden[l];
+    a->dims[l + 1] = (hidden[l] + 7) & ~7;
+    real[l + 1] = hidden[l];
   }
+  real[a->L] = a->n_out;
   a->dims[a->L] = a->n_out_pad;
   int rc = cuda_check(cudaGetDevice(&a->device), "cudaGetDevice");
   if (rc) { delete a; return rc; }
@@ -565,11 +572,12 @@ int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t se
   a->norm = (float*)(b + off[q++]);
   a->err = (int*)(b + off[q++]);
   a->loss_part = (float*)(b + off[q++]);
-  // initial weights: N(0, 2/fan_in) on the real (unpadded) inputs and outputs, zero biases
+  // initial weights: N(0, 2/fan_in) on the real (unpadded) inputs, units and outputs, zero
+  // biases and zero padding
   uint64_t st = seed * 0x9E3779B97F4A7C15ull + 12345;
   for (int l = 0; l < a->L; ++l) {
     const int rows = a->dims[l + 1], cols = a->dims[l];
-    const int real_cols = l == 0 ? a->n_in : cols, real_rows = l == a->L - 1 ? a->n_out : rows;
+    const int real_cols = real[l], real_rows = real[l + 1];
     std::vector<float> w((size_t)rows * cols, 0.0f);
     const double sd = std::sqrt(2.0 / real_cols) * (l == a->L - 1 ? 0.5 : 1.0);
     for (int r = 0; r < real_rows; ++r)

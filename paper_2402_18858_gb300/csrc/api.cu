@@ -592,6 +592,24 @@ int thermo_props(chem_mech m, int64_t n, int64_t ld, const double* T, const doub
                        (cudaStream_t)stream);
 }
 
+int chem_pasr_source(chem_mech m, int64_t n, int64_t ld, double dt, const double* rho, const double* Y0,
+                     const double* Y1, const double* k_sgs, const double* eps, const double* nu, double y_min,
+                     double r_min, double* omega, double* kappa, chem_stream stream) {
+  int rc = check_mech(m);
+  if (rc) return rc;
+  if (n < 0 || ld < n) return set_error(CHEM_E_ARG, "chem_pasr_source: need 0 <= n <= ld");
+  if (!(dt > 0.0) || !(dt < 1e300)) return set_error(CHEM_E_ARG, "chem_pasr_source: dt must be positive and finite");
+  if (n == 0) return CHEM_OK;
+  if (!rho || !Y0 || !Y1 || !k_sgs || !eps || !nu || !omega)
+    return set_error(CHEM_E_ARG, "chem_pasr_source: null array argument");
+  if (!(y_min == y_min)) return set_error(CHEM_E_ARG, "chem_pasr_source: y_min is NaN");
+  if (!(r_min == r_min)) return set_error(CHEM_E_ARG, "chem_pasr_source: r_min is NaN");
+  if (y_min < 0.0) y_min = 1e-10;
+  if (r_min < 0.0) r_min = 1e-9;
+  return launch_pasr(m->dev, n, ld, dt, rho, Y0, Y1, k_sgs, eps, nu, y_min, r_min, omega, kappa,
+                     (cudaStream_t)stream);
+}
+
 int chem_selftest_exp(chem_mech m, int64_t n, const double* x, double* y, chem_stream stream) {
   int rc = check_mech(m);
   if (rc) return rc;

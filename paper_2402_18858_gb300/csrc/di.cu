@@ -39,19 +39,6 @@ __device__ __forceinline__ float wsumf(float v) {
   return __shfl_sync(FULLMASK, v, 0);
 }
 
-// 1/x from the hardware reciprocal estimate and two Newton-Raphson steps y += y (1 - x y), each
-// of which squares the relative error, so the result is within about an ulp of 1/x for finite
-// normal x; 4 FP64 instructions against about twice that for a correctly rounded division.
-// Zero, subnormal or infinite x give NaN (every caller treats that as a failed evaluation).
-__device__ __forceinline__ double rcp_nr(double x) {
-  double y;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
-}
-
 template <int NPL>
 __device__ __forceinline__ double comp_get(const double (&x)[NPL], int i) {
   // value of component i (owned by lane i & 31, slot i >> 5), on every lane

@@ -129,6 +129,19 @@ __device__ __forceinline__ double log_t(double x, const double* __restrict__ tab
 }
 constexpr int kMaxElem = 8;
 
+// 1/x from the hardware reciprocal estimate and two Newton-Raphson steps y += y (1 - x y), each
+// of which squares the relative error, so the result is within about an ulp of 1/x for finite
+// normal x; 4 FP64 instructions against about twice that for a correctly rounded division.
+// Zero, subnormal or infinite x give NaN (every caller treats that as a failed evaluation).
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // FP64 -> FP32 on the integer pipe for values that only steer heuristics or feed FP32 sums
 // (exponent rebias, mantissa truncated: relative error below 2^-23).  |x| < 2^-126 gives a
 // signed zero, |x| >= 2^128, inf and NaN give a signed inf.
@@ -177,6 +190,11 @@ int launch_log_selftest(const DevMech& m, int64_t n, const double* x, double* y,
 int launch_thermo(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* Y,
                   double* cp, double* h, double* mu, double* kappa, const double* h_in,
                   double* T_out, int mixed, cudaStream_t s);
+
+// pasr.cu
+int launch_pasr(const DevMech& m, int64_t n, int64_t ld, double dt, const double* rho, const double* Y0,
+                const double* Y1, const double* ksgs, const double* eps, const double* nu, double y_min,
+                double r_min, double* omega, double* kappa, cudaStream_t s);
 
 // probe.cu
 int launch_fp64_probe(double* gflops, cudaStream_t s);

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -37,7 +38,7 @@ __device__ __forceinline__ float dgelu_f(float x) {
 
 template <int BN>
 struct TileCfg {
-  static constexpr int STAGES = BN >= 256 ? CHEM_GEMM_STAGES_256 : CHEM_GEMM_STAGES;
+  static constexpr int STAGES = BN >= 224 ? CHEM_GEMM_STAGES_256 : CHEM_GEMM_STAGES;
   static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   static constexpr size_t A_BYTES = (size_t)tc::BM * tc::BK * 2;
   static constexpr size_t B_BYTES = (size_t)BN * tc::BK * 2;
@@ -239,11 +240,20 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
 }
 
 // C = A B^T with the epilogue `epi` (0: bias+GELU -> BF16 [+ pre-activation copy],
-// 1: bias -> FP32, 2: * GELU'(z) -> BF16, 3: FP32).  BN is chosen from N.
+// 1: bias -> FP32, 2: * GELU'(z) -> BF16, 3: FP32).  BN (a multiple of 32, at most 256) is
+// chosen from N.
 int gemm_bf16(int epi, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int M, int N, int K,
               const GemmEpi& e, int* err, cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return CHEM_OK;
-  const int bn = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+  // tile width: the least padded width ceil(N / BN) BN, ties to the wider tile (N = 1600 and
+  // 800 take 160, N = 400 and 2000 take 224, N = 1000 and 500 take 256)
+  static const int kBN[] = {256, 224, 160, 128, 64, 32};
+  int bn = 256;
+  int64_t best = INT64_MAX;
+  for (int c : kBN) {
+    const int64_t padded = (int64_t)((N + c - 1) / c) * c;
+    if (padded < best) { best = padded; bn = c; }
+  }
 #define CHEM_GEMM_CASE(BNV)                                                                    \
   if (bn == BNV) {                                                                             \
     switch (epi) {                                                                             \
@@ -256,6 +266,8 @@ int gemm_bf16(int epi, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, i
   CHEM_GEMM_CASE(32)
   CHEM_GEMM_CASE(64)
   CHEM_GEMM_CASE(128)
+  CHEM_GEMM_CASE(160)
+  CHEM_GEMM_CASE(224)
   CHEM_GEMM_CASE(256)
 #undef CHEM_GEMM_CASE
   return set_error(CHEM_E_ARG, "gemm: unsupported tile");

@@ -161,6 +161,10 @@ def main():
     ap.add_argument("--eval-seed", type=int, default=3)
     ap.add_argument("--out", default="")
     ap.add_argument("--with-moments", action="store_true", help="keep the Adam moments (resumable)")
+    ap.add_argument("--repeats", type=int, default=3, help="timing repeats of the evaluation")
+    ap.add_argument("--infer-cells", type=int, default=0,
+                    help="> 0: also time the learned step with fallback on this many fresh cells")
+    ap.add_argument("--elem-tol", type=float, default=1e-2)
     args = ap.parse_args()
     build.build()
     m = wl.make_mechanism(args.kind, args.mech_seed)
@@ -176,9 +180,44 @@ def main():
     if args.out:
         chem.chem_ann_save(ann, args.out, with_moments=args.with_moments)
     del X, bcty, U
-    ev = evaluate(gm, ann, di_states(gm, m, args.eval_cells, args.eval_seed, args.dt), args.dt)
+    ev = evaluate(gm, ann, di_states(gm, m, args.eval_cells, args.eval_seed, args.dt), args.dt,
+                  repeats=args.repeats, elem_tol=args.elem_tol)
+    out = dict(kind=args.kind, hidden=ann.dims, data_generation_s=gen_s,
+               di_generation_cells_per_s=args.train_cells / gen_s, train=tr, eval=ev)
+    if args.infer_cells > 0:
+        out["inference"] = time_inference(gm, m, ann, args.infer_cells, args.eval_seed + 1, args.dt,
+                                          ev["di_cells_per_s"], elem_tol=args.elem_tol)
     hist = tr.pop("loss_history", None)
-    print(json.dumps(dict(data_generation_s=gen_s, train=tr, eval=ev, loss_history=hist[-20:] if hist else None)))
+    out["loss_history"] = hist[-20:] if hist else None
+    print(json.dumps(out))
+
+
+def time_inference(gm, m: wl.Mechanism, ann, n: int, seed: int, dt: float, di_rate: float, repeats: int = 2,
+                   **ann_opts) -> Dict:
+    """Learned step with DI fallback on n fresh cells (best of `repeats`, CUDA events)."""
+    st = wl.make_states(m, n, seed)
+    dev = torch.device("cuda")
+    T0 = torch.as_tensor(st.T, device=dev)
+    p = torch.as_tensor(st.p, device=dev)
+    Y0 = torch.as_tensor(st.Y, device=dev)
+    del st
+    T, Y = T0.clone(), Y0.clone()
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = torch.empty(chem.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+    best = 1e30
+    for _ in range(repeats):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        chem.chem_step_ann(gm, ann, dt, T, p, Y, status, ws, **ann_opts)
+        e1.record(s)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    fb = float((status != 0).float().mean().item())
+    return dict(cells=n, ms=best, cells_per_s=n / (best * 1e-3), fallback_fraction=fb,
+                speedup_vs_di=n / (best * 1e-3) / di_rate)
 
 
 if __name__ == "__main__":

@@ -545,6 +545,28 @@ WORKLOADS = {
 }
 
 
+@dataclasses.dataclass
+class TurbulenceFields:
+    """Per-cell LES sub-grid quantities for the PaSR source: density (kg/m^3), sub-grid kinetic
+    energy k (m^2/s^2), its dissipation rate eps (m^2/s^3) and kinematic viscosity nu (m^2/s)."""
+    rho: np.ndarray
+    k: np.ndarray
+    eps: np.ndarray
+    nu: np.ndarray
+
+
+def make_turbulence(n: int, seed: int, laminar_fraction: float = 0.05) -> TurbulenceFields:
+    """Seeded synthetic sub-grid fields with swirl-flame LES magnitudes: rho log-uniform in
+    [0.12, 1.2] (2500 K to 300 K at 1 atm), k log-uniform in [1e-3, 10], eps log-uniform in
+    [1, 1e6], nu log-uniform in [1.5e-5, 4e-4]; a fraction of cells has k = 0 (no sub-grid
+    turbulence, e.g. near walls or in the fresh gas core)."""
+    rng = np.random.default_rng(seed)
+    lu = lambda lo, hi: np.exp(rng.uniform(np.log(lo), np.log(hi), n))  # noqa: E731
+    rho, k, eps, nu = lu(0.12, 1.2), lu(1e-3, 10.0), lu(1.0, 1e6), lu(1.5e-5, 4e-4)
+    k[rng.random(n) < laminar_fraction] = 0.0
+    return TurbulenceFields(rho=rho, k=k, eps=eps, nu=nu)
+
+
 def mechanism_file(kind: str, seed: int, directory: str) -> str:
     """Generate (once) and return the path of a mechanism file in `directory`."""
     import os

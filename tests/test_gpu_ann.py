@@ -132,3 +132,33 @@ def test_training_is_deterministic_and_resumable(lc, setup, tmp_path, mechs):
                                lr=1e-3, loss_out=loss)
         lb.append(float(loss[0].item()))
     assert la == lb
+
+
+def test_widths_that_are_not_multiples_of_8(lc, setup):
+    """Hidden widths 20 and 12 are stored as 24 and 16; the padding units start at zero and stay
+    exactly zero through training, so the network equals the 20-12 network of the oracle."""
+    gm, ann0, st, X, bcty, U = setup
+    ann = lc.chem_ann_create(gm, [20, 12], seed=5)
+    assert list(ann.dims[1:3]) == [24, 16]
+    lc.chem_ann_set_norm(ann, lc.chem_ann_get_norm(ann0))
+    B = 1024
+    for it in range(10):
+        s = (it * B) % 2048
+        lc.chem_ann_train_step(ann, X[s:s + B].contiguous(), U[s:s + B].contiguous(), bcty[s:s + B].contiguous(),
+                               lr=1e-3)
+    torch.cuda.synchronize()
+    assert lc.chem_ann_error(ann) == 0
+    (W1, b1), (W2, b2), (W3, b3) = mlp.unflatten(lc.chem_ann_get_params(ann), ann.dims)
+    assert (W1[20:] == 0).all() and (b1[20:] == 0).all()
+    assert (W2[12:] == 0).all() and (W2[:, 20:] == 0).all() and (b2[12:] == 0).all()
+    assert (W3[:, 12:] == 0).all()
+    assert np.abs(W1[:20]).max() > 0 and np.abs(W2[:12, :20]).max() > 0
+    n = X.shape[0]
+    Ug = torch.empty((n, ann.n_out_pad), dtype=torch.float32, device="cuda")
+    ws = torch.empty(lc.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device="cuda")
+    lc.chem_ann_forward(ann, X, Ug, ws)
+    torch.cuda.synchronize()
+    real = [(W1[:20], b1[:20]), (W2[:12, :20], b2[:12]), (W3[:, :12], b3)]
+    Uo, _ = mlp.forward(real, X.float().cpu().numpy().astype(np.float64), bf16=True)
+    d = Ug.cpu().numpy() - Uo
+    assert np.abs(d).max() <= 2e-3 * np.abs(Uo).max() + 1e-3
