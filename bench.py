@@ -34,6 +34,10 @@ WORKLOAD = "di_c_30sp_1m"
 DI_RTOL = 1e-9           # library defaults (rtol 1e-9, atol_Y 1e-18, Newton 0.1): what the parity tests validate
 MECH_DIR = os.path.join(tempfile.gettempdir(), "chem_bench_mech")
 EXP_FLOPS = 20           # flop convention for exp/log/log10/pow in the algorithmic count
+# DRAM bytes of one di_kernel launch per cell, from the 8,192-cell ncu capture of the current
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum = 2,909,696 + 0 B; the written state
+# stayed in L2 there), scaled to a launch by the cells processed
+DI_DRAM_BYTES_PER_CELL = 2909696 / 8192
 
 
 # ------------------------------------------------------------------------------------------
@@ -518,7 +522,7 @@ def main():
             "di_flops_per_cell": flops / N,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_gf / 1e3,
                          "unit": "TFLOP/s", "frac": achieved_tf / (peak_gf / 1e3),
-                         "traffic": None, "kernel": "di_kernel (FP64 DFMA pipe)",
+                         "traffic": DI_DRAM_BYTES_PER_CELL * N, "kernel": "di_kernel (FP64 DFMA pipe)",
                          "peak_source": "measured live: chem_fp64_peak_gflops DFMA probe"},
             "thermo_roofline": {"bound": "alu", "achieved": th_tf, "peak": peak_gf / 1e3, "unit": "TFLOP/s",
                                 "frac": th_tf / (peak_gf / 1e3), "kernel": "thermo_kernel (mixed precision)",

@@ -177,13 +177,26 @@ typedef struct {
   float lr, beta1, beta2, eps;   /* Adam */
   float w_data, w_mass;          /* Eq. 11 weights of L_data (Eq. 8) and L_mass (Eq. 9) */
   int apply;                     /* 0: gradients only (chem_ann_get_params(which = 1)) */
-  int reserved;
+  float w_hrr;                   /* Eq. 11 weight of L_HRR (Eq. 10); 0 leaves the term out */
 } chem_train_opts;
 
+/* Per-sample coefficients of L_HRR (Eq. 10), read as the step-mean heat release
+ * HRR = -(rho / dt) sum_k h_k(T0) (Y_k(t+dt) - Y_k(t)) with mass enthalpies at the initial
+ * temperature and rho = p / (R T0 sum_k Y0_k / W_k):  hrr_c [n, K] = -rho h_k / (dt scale) and
+ * the DI target hrr_r [n] = sum_k hrr_c (Y1 - Y0), both FP32 in units of `scale` (W/m^3, e.g.
+ * the RMS heat release of the training set; pass 1 to obtain raw values). */
+int chem_ann_hrr_coeffs(chem_ann ann, int64_t n, int64_t ld, const double* T0, const double* p,
+                        const double* Y0, const double* Y1, double dt, double scale, float* hrr_c,
+                        float* hrr_r, chem_stream stream);
+
 /* One optimisation step on a minibatch: X [B, 64] BF16, targets Ut [B, n_out_pad] FP32,
- * bcty [B, K] FP32 raw F(Y) (NULL unless w_mass != 0), B a multiple of 8.  loss_out (device,
- * nullable) receives {L_tot, L_data, L_mass}.  The library keeps its training buffers. */
-int chem_ann_train_step(chem_ann ann, const void* X, const float* Ut, const float* bcty, int64_t B,
+ * bcty [B, K] FP32 raw F(Y) (NULL unless w_mass or w_hrr != 0), hrr_c [B, K] and hrr_r [B]
+ * from chem_ann_hrr_coeffs (NULL unless w_hrr != 0), B a multiple of 8.  The loss is
+ * L = w_data L_data + w_mass L_mass + w_hrr L_HRR with L_HRR = mean_b e_b^2,
+ * e_b = sum_k hrr_c (Y*_k - Y_k(t)) - hrr_r.  loss_out (device, nullable) receives
+ * {L_tot, L_data, L_mass, L_HRR}.  The library keeps its training buffers. */
+int chem_ann_train_step(chem_ann ann, const void* X, const float* Ut, const float* bcty,
+                        const float* hrr_c, const float* hrr_r, int64_t B,
                         const chem_train_opts* opts, float* loss_out, chem_stream stream);
 /* Flat FP32 parameters (which = 0) or last gradients (which = 1), per layer W [out, in] then b. */
 int chem_ann_get_params(chem_ann ann, int which, float* host, int64_t count);
@@ -277,6 +290,33 @@ void chem_server_free(chem_server server);
 int thermo_props(chem_mech mech, int64_t n, int64_t ld, const double* T, const double* Y,
                  double* cp, double* h, double* mu, double* kappa, const double* h_in,
                  double* T_out, int mixed_precision, chem_stream stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Random augmentation of training states (the hybrid flamelet/random data method, Sec. 2.2,*/
+/* Eqs. 3-6, with the constraints of the same passage)                                       */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+  double alpha, beta, theta;   /* Eqs. 3-6 (0.125, 10, 0.1) */
+  double hc[2];                /* accepted molar H/C ([2.65, 4.67]; skipped without carbon) */
+  double on[2];                /* accepted molar O/N ([0.254, 0.320]) */
+  double phi[2];               /* accepted (2 n_C + n_H / 2) / n_O ([0.20, 1.15]) */
+} chem_hfrd_opts;
+
+/* For n base states (T, p, Y; SoA, ld) and uniform draws gamma in [-1, 1] (species-major
+ * [3 + K][ld]: rows 0, 1, 2 for T, p and Y_N2, then one row per species, the N2 row unused):
+ *   T' = T + alpha gamma_T (T_max - T_min), p' = p + beta gamma_p (p_max - p_min),
+ *   Y'_N2 = Y_N2 + alpha gamma_N2 (Y_N2,max - Y_N2,min), Y'_j = Y_j^(1 + theta gamma_j),
+ * the ranges taken over the n base states, then Y' divided by its sum.  keep[i] = 1 when
+ * T' > 0, p' > 0, Y'_N2 >= 0 and the molar element ratios H/C and O/N and the element-based
+ * equivalence ratio lie in the accepted ranges, else 0.  Outputs T_out, p_out [ld], Y_out
+ * [K][ld] (written for every state), keep [ld].  opts NULL selects the paper's values.  The
+ * mechanism needs a species named N2 and elements H, O and N (CHEM_E_UNSUPPORTED otherwise).
+ * workspace: device scratch of chem_hfrd_workspace_bytes() bytes (the ranges). */
+int chem_hfrd_augment(chem_mech mech, int64_t n, int64_t ld, const double* T, const double* p,
+                      const double* Y, const double* gamma, const chem_hfrd_opts* opts, double* T_out,
+                      double* p_out, double* Y_out, int32_t* keep, void* workspace, size_t ws_bytes,
+                      chem_stream stream);
+size_t chem_hfrd_workspace_bytes(void);
 
 /* ---------------------------------------------------------------------------------------- */
 /* PaSR filtered reaction source (the paper's swirl-flame LES closes turbulence-chemistry    */

@@ -4,15 +4,17 @@
   [-1/lambda, 0] fixes it as F(x) = (x^lambda - 1)/lambda), lambda = 0.1, and its inverse.
 * MLP with GELU hidden layers (exact erf form, Hendrycks & Gimpel 2016) and a linear output,
   weights W_l [out, in], biases b_l; forward and a hand-written backward pass.
-* Loss of Eq. 11 with L_data (Eq. 8, mean squared error in the normalised output space) and
-  L_mass (Eq. 9, mean over samples of |sum_k Y*_k - 1|); the HRR term (Eq. 10) has weight 0.
+* Loss of Eq. 11 with L_data (Eq. 8, mean squared error in the normalised output space),
+  L_mass (Eq. 9, mean over samples of |sum_k Y*_k - 1|) and L_HRR (Eq. 10, squared error of the
+  step-mean heat release, in units of a scale; weight W3, 0 unless requested).
 * Adam (Kingma & Ba 2015).
 * Optional emulation of BF16 storage (round to nearest even) of inputs, weights and hidden
   activations, so that the GPU's BF16 tensor-core forward can be compared element by element.
 
-Parity status: forward, backward, loss gradient and Adam are pinned by the tests in
-tests/test_oracle_mlp.py (finite differences, closed forms, special values).  The loss
-weights W1, W2, W3 of Eq. 11 are unstated in the paper: W1 = 1, W2 = 0.1, W3 = 0 here.
+Parity status: forward, backward, loss gradient (all three terms), the heat-release
+coefficients and Adam are pinned by the tests in tests/test_oracle_mlp.py (finite differences,
+closed forms, special values).  The loss weights W1, W2, W3 of Eq. 11 are unstated in the
+paper: W1 = 1, W2 = 0.1 and W3 = 0 by default.
 """
 from __future__ import annotations
 
@@ -107,8 +109,14 @@ def backward(params: Params, cache, dU: np.ndarray) -> Params:
     return grads
 
 
-def loss_and_grad(U, Ut, K, bcty=None, out_mean=None, out_std=None, w_data=1.0, w_mass=0.1):
-    """Eq. 11 with W3 = 0 over the first K output columns; returns (L, L_data, L_mass, dU)."""
+def loss_and_grad(U, Ut, K, bcty=None, out_mean=None, out_std=None, w_data=1.0, w_mass=0.1,
+                  w_hrr=0.0, hrr_c=None, hrr_r=None, with_hrr=False):
+    """Eq. 11 over the first K output columns; returns (L, L_data, L_mass, dU), or with
+    with_hrr=True (L, L_data, L_mass, L_hrr, dU).
+
+    L_hrr (Eq. 10): mean over samples of e_b^2, e_b = sum_k c_bk (Y*_bk - Y_bk(t)) - r_b, with
+    Y* the predicted state, Y(t) = F^-1(bcty), c_bk the per-sample heat-release coefficients
+    and r_b the DI target, both in units of a heat-release scale (see hrr_coefficients)."""
     U = np.asarray(U, dtype=np.float64)
     B = U.shape[0]
     d = U[:, :K] - Ut[:, :K]
@@ -116,15 +124,37 @@ def loss_and_grad(U, Ut, K, bcty=None, out_mean=None, out_std=None, w_data=1.0, 
     dU = np.zeros_like(U)
     dU[:, :K] = w_data * 2.0 * d / (B * K)
     L_mass = 0.0
-    if bcty is not None and w_mass != 0.0:
+    L_hrr = 0.0
+    need_y = bcty is not None and (w_mass != 0.0 or (w_hrr != 0.0 and hrr_c is not None))
+    if need_y:
         Ys = ibct(bcty + U[:, :K] * out_std[None, :] + out_mean[None, :])
+        dYs = np.power(np.maximum(Ys, 0.0), 1.0 - LAMBDA) * out_std[None, :]
+    if bcty is not None and w_mass != 0.0:
         s = Ys.sum(axis=1)
         L_mass = float(np.abs(s - 1.0).mean())
-        dYs = np.power(np.maximum(Ys, 0.0), 1.0 - LAMBDA) * out_std[None, :]
         dU[:, :K] += w_mass / B * np.sign(s - 1.0)[:, None] * dYs
-    return w_data * L_data + w_mass * L_mass, L_data, L_mass, dU
+    if bcty is not None and w_hrr != 0.0 and hrr_c is not None:
+        e = (hrr_c * (Ys - ibct(bcty))).sum(axis=1) - hrr_r
+        L_hrr = float((e * e).mean())
+        dU[:, :K] += w_hrr * 2.0 / B * e[:, None] * hrr_c * dYs
+    L = w_data * L_data + w_mass * L_mass + w_hrr * L_hrr
+    if with_hrr:
+        return L, L_data, L_mass, L_hrr, dU
+    return L, L_data, L_mass, dU
 
 
+def hrr_coefficients(T0, p, Y0, Y1, dt, W, h_molar, scale):
+    """Per-sample coefficients of the heat-release loss term (Eq. 10), read as the step-mean
+    heat release HRR = -(rho / dt) sum_k h_k(T0) (Y_k(t + dt) - Y_k(t)) (W/m^3) with the mass
+    enthalpies h_k = h_k,molar / W_k at the initial temperature and the initial density
+    rho = p / (R T0 sum_k Y_k / W_k):  c_bk = -rho h_k / (dt scale) and the DI target
+    r_b = sum_k c_bk (Y1_bk - Y0_bk).  h_molar [K, N] (J/mol) from the oracle's NASA-7;
+    Y0, Y1 [K, N]; returns c [N, K], r [N]."""
+    R = 8.314462618
+    rho = p / (R * T0 * (Y0 / W[:, None]).sum(axis=0))
+    c = -(rho[None, :] * h_molar / W[:, None]) / (dt * scale)
+    r = (c * (Y1 - Y0)).sum(axis=0)
+    return c.T.copy(), r
 def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam update (step number t >= 1); returns (p, m, v)."""
     m = b1 * m + (1 - b1) * g

@@ -25,6 +25,11 @@ class ChemError(RuntimeError):
         self.code = code
 
 
+class HfrdOpts(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("theta", C.c_double), ("hc", C.c_double * 2),
+                ("on", C.c_double * 2), ("phi", C.c_double * 2)]
+
+
 class DiOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol_Y", C.c_double), ("atol_T", C.c_double),
                 ("newton_tol", C.c_double), ("max_steps", C.c_int), ("reserved", C.c_int)]
@@ -57,6 +62,10 @@ def lib(auto_build: bool = False):
         L.chem_workspace_bytes.restype = C.c_size_t
         L.thermo_props.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
         L.chem_pasr_source.argtypes = [vp, i64, i64, dbl, vp, vp, vp, vp, vp, vp, dbl, dbl, vp, vp, vp]
+        L.chem_hfrd_augment.argtypes = [vp, i64, i64, vp, vp, vp, vp, C.POINTER(HfrdOpts), vp, vp, vp, vp, vp,
+                                        C.c_size_t, vp]
+        L.chem_hfrd_workspace_bytes.restype = C.c_size_t
+        L.chem_hfrd_workspace_bytes.argtypes = []
         L.chem_last_error.restype = C.c_char_p
         L.chem_fp64_peak_gflops.argtypes = [C.POINTER(dbl), vp]
         L.chem_selftest_exp.argtypes = [vp, i64, vp, vp, vp]
@@ -195,6 +204,28 @@ def chem_pasr_source(m: Mech, dt: float, rho, Y0, Y1, k_sgs, eps, nu, omega, kap
                                   _ptr(omega, f64), _ptr(kappa, f64), _stream(stream)))
 
 
+def chem_hfrd_workspace_bytes() -> int:
+    return int(lib().chem_hfrd_workspace_bytes())
+
+
+def chem_hfrd_augment(m: Mech, T, p, Y, gamma, T_out, p_out, Y_out, keep, workspace, opts: Optional[dict] = None,
+                      n: Optional[int] = None, stream=None) -> None:
+    """HFRD augmentation (Eqs. 3-6); opts: dict with alpha, beta, theta, hc, on, phi, or None."""
+    ld = _ld(Y, m)
+    if gamma.dim() != 2 or gamma.shape[0] != 3 + m.K or gamma.shape[1] != ld:
+        raise ValueError(f"gamma must be [3 + K = {3 + m.K}, ld = {ld}]")
+    n = ld if n is None else n
+    o = None
+    if opts is not None:
+        o = HfrdOpts(opts["alpha"], opts["beta"], opts["theta"], (C.c_double * 2)(*opts["hc"]),
+                     (C.c_double * 2)(*opts["on"]), (C.c_double * 2)(*opts["phi"]))
+    f64 = torch.float64
+    _check(lib().chem_hfrd_augment(m.handle, n, ld, _ptr(T, f64), _ptr(p, f64), _ptr(Y, f64), _ptr(gamma, f64),
+                                   C.byref(o) if o is not None else None, _ptr(T_out, f64), _ptr(p_out, f64),
+                                   _ptr(Y_out, f64), _ptr(keep, torch.int32), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
 def chem_fp64_peak_gflops(stream=None) -> float:
     v = C.c_double()
     _check(lib().chem_fp64_peak_gflops(C.byref(v), _stream(stream)))
@@ -228,7 +259,7 @@ def chem_selftest_gemm(epi: int, A, B, out, bias=None, z=None, err=None, stream=
 # ------------------------------------------------------------------------------------------
 class TrainOpts(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
-                ("w_data", C.c_float), ("w_mass", C.c_float), ("apply", C.c_int), ("reserved", C.c_int)]
+                ("w_data", C.c_float), ("w_mass", C.c_float), ("apply", C.c_int), ("w_hrr", C.c_float)]
 
 
 class AnnOpts(C.Structure):
@@ -257,7 +288,8 @@ def _ann_sigs():
     L.chem_ann_features.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.chem_ann_targets.argtypes = [vp, i64, i64, vp, vp, vp, vp]
     L.chem_ann_forward.argtypes = [vp, vp, i64, vp, vp, C.c_size_t, vp]
-    L.chem_ann_train_step.argtypes = [vp, vp, vp, vp, i64, C.POINTER(TrainOpts), vp, vp]
+    L.chem_ann_train_step.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(TrainOpts), vp, vp]
+    L.chem_ann_hrr_coeffs.argtypes = [vp, i64, i64, vp, vp, vp, vp, C.c_double, C.c_double, vp, vp, vp]
     L.chem_ann_get_params.argtypes = [vp, i32, fp, i64]
     L.chem_ann_set_params.argtypes = [vp, fp, i64]
     L.chem_ann_save.argtypes = [vp, C.c_char_p, i32]
@@ -368,11 +400,29 @@ def chem_ann_forward(a: Ann, X, U, workspace, stream=None) -> None:
 
 
 def chem_ann_train_step(a: Ann, X, Ut, bcty=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
-                        w_data=1.0, w_mass=0.1, apply=True, loss_out=None, stream=None) -> None:
-    o = TrainOpts(lr, beta1, beta2, eps, w_data, w_mass if bcty is not None else 0.0, int(apply), 0)
+                        w_data=1.0, w_mass=0.1, apply=True, loss_out=None, hrr_c=None, hrr_r=None,
+                        w_hrr=0.0, stream=None) -> None:
+    """One Adam step; loss_out (4 floats, device) receives L_tot, L_data, L_mass, L_HRR."""
+    if loss_out is not None and loss_out.numel() < 4:
+        raise ValueError("loss_out needs 4 floats")
+    if w_hrr != 0.0 and (hrr_c is None or hrr_r is None or bcty is None):
+        raise ValueError("w_hrr != 0 needs bcty, hrr_c and hrr_r")
+    o = TrainOpts(lr, beta1, beta2, eps, w_data, w_mass if bcty is not None else 0.0, int(apply), float(w_hrr))
     _check(lib().chem_ann_train_step(a.handle, _ptr(X, torch.bfloat16), _ptr(Ut, torch.float32),
-                                     _ptr(bcty, torch.float32), X.shape[0], C.byref(o),
+                                     _ptr(bcty, torch.float32), _ptr(hrr_c, torch.float32),
+                                     _ptr(hrr_r, torch.float32), X.shape[0], C.byref(o),
                                      _ptr(loss_out, torch.float32), _stream(stream)))
+
+
+def chem_ann_hrr_coeffs(a: Ann, dt: float, scale: float, T0, p, Y0, Y1, hrr_c, hrr_r, n: Optional[int] = None,
+                        stream=None) -> None:
+    """Per-sample heat-release coefficients [n, K] and DI targets [n] of the L_HRR term."""
+    ld = Y0.shape[1]
+    n = ld if n is None else n
+    f64 = torch.float64
+    _check(lib().chem_ann_hrr_coeffs(a.handle, n, ld, _ptr(T0, f64), _ptr(p, f64), _ptr(Y0, f64), _ptr(Y1, f64),
+                                     float(dt), float(scale), _ptr(hrr_c, torch.float32), _ptr(hrr_r, torch.float32),
+                                     _stream(stream)))
 
 
 def chem_ann_get_params(a: Ann, which: int = 0):

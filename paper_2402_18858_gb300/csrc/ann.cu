@@ -82,6 +82,32 @@ __device__ __forceinline__ float raw_feature(int j, int64_t i, int64_t ld, const
   return bct_f(Y[(size_t)(j - 2) * ld + i]);
 }
 
+// heat-release coefficients of the L_HRR term (Eq. 10) per sample: c_bk = -rho h_k(T0) / (dt s)
+// (h_k the mass enthalpy from NASA-7 at the initial temperature, rho = p / (R T0 sum Y/W)) and
+// the DI target r_b = sum_k c_bk (Y1_bk - Y0_bk); FP64 arithmetic, FP32 results [n, K], [n]
+__global__ void hrr_coeff_kernel(DevMech m, int64_t n, int64_t ld, const double* T0, const double* p,
+                                 const double* Y0, const double* Y1, double dt, double scale, float* c, float* r) {
+  const int K = m.K;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double T = T0[i], invT = 1.0 / T;
+    double sYW = 0.0;
+    for (int k = 0; k < K; ++k) sYW += Y0[(size_t)k * ld + i] * m.invW[k];
+    const double rho = p[i] / (kR * T * sYW);
+    const double f = -rho * kR * T / (dt * scale);
+    const int hi = T >= m.Tmid ? 1 : 0;
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
+      const double hRT = a[5] + T * (a[6] + T * (a[7] + T * (a[8] + T * a[9]))) + a[10] * invT;
+      const double ck = f * hRT * m.invW[k];
+      c[(size_t)i * K + k] = (float)ck;
+      acc += ck * (Y1[(size_t)k * ld + i] - Y0[(size_t)k * ld + i]);
+    }
+    r[i] = (float)acc;
+  }
+}
+
+
 // normalised BF16 features X[i][0..63]; range flag (bit 1) against the training min/max
 __global__ void features_kernel(int64_t n, int64_t ld, const double* T, const double* p, const double* Y, int n_in,
                                 const float* norm, float margin, bf16* X, int32_t* flags, float* bcty, int K,
@@ -338,32 +364,49 @@ __global__ void scatter_status_kernel(int64_t nmax, const int32_t* n_dev, const 
     status[slots[s]] = st_slot[s] == CHEM_CELL_OK ? CHEM_CELL_ANN_FALLBACK : st_slot[s];
 }
 
-// training loss (Eqs. 8-9) and its gradient w.r.t. the network output
-//   L = w_data * mean_{b,k}(u - u_t)^2 + w_mass * mean_b |sum_k Y*_k - 1|,
-//   Y*_k = F^-1(F(Y_k) + u_k sigma_k + mu_k)
+// training loss (Eqs. 8-10) and its gradient w.r.t. the network output
+//   L = w_data * mean_{b,k}(u - u_t)^2 + w_mass * mean_b |sum_k Y*_k - 1| + w_hrr * mean_b e_b^2,
+//   Y*_k = F^-1(F(Y_k) + u_k sigma_k + mu_k),
+//   e_b = sum_k c_bk (Y*_k - Y_k) - r_b   (the step-mean heat-release error, scaled)
 // dU (BF16 [B, n_out_pad]) and its transpose dUT ([n_out_pad, B]); per-block loss partials.
 __global__ void loss_grad_kernel(int64_t B, int K, int n_out_pad, const float* Up, const float* Ut, const float* bcty,
                                  const float* out_mean, const float* out_sd, float w_data, float w_mass,
-                                 bf16* dU, bf16* dUT, float* part) {
-  __shared__ float sh[2][256];
-  float ld = 0.0f, lm = 0.0f;
+                                 const float* hrr_c, const float* hrr_r, float w_hrr, bf16* dU, bf16* dUT,
+                                 float* part) {
+  __shared__ float sh[3][256];
+  float ld = 0.0f, lm = 0.0f, lh = 0.0f;
   const float cdata = 2.0f * w_data / (float)(B * K);
+  const bool mass = bcty && w_mass != 0.0f;
+  const bool hrr = bcty && hrr_c && hrr_r && w_hrr != 0.0f;
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (int64_t)gridDim.x * blockDim.x) {
-    float ysum = 0.0f;
-    if (bcty && w_mass != 0.0f)
-      for (int k = 0; k < K; ++k) ysum += ibct_f(bcty[b * K + k] + Up[b * n_out_pad + k] * out_sd[k] + out_mean[k]);
+    float ysum = 0.0f, eb = 0.0f;
+    if (mass || hrr) {
+      for (int k = 0; k < K; ++k) {
+        const float ys = ibct_f(bcty[b * K + k] + Up[b * n_out_pad + k] * out_sd[k] + out_mean[k]);
+        ysum += ys;
+        if (hrr) eb += hrr_c[b * K + k] * (ys - ibct_f(bcty[b * K + k]));
+      }
+    }
+    if (hrr) {
+      eb -= hrr_r[b];
+      lh += eb * eb;
+    }
     const float sgn = ysum > 1.0f ? 1.0f : (ysum < 1.0f ? -1.0f : 0.0f);
-    if (bcty && w_mass != 0.0f) lm += fabsf(ysum - 1.0f);
+    if (mass) lm += fabsf(ysum - 1.0f);
     for (int k = 0; k < n_out_pad; ++k) {
       float g = 0.0f;
       if (k < K) {
         const float d = Up[b * n_out_pad + k] - Ut[b * n_out_pad + k];
         ld += d * d;
         g = cdata * d;
-        if (bcty && w_mass != 0.0f) {
+        if (mass || hrr) {
           const float ys = ibct_f(bcty[b * K + k] + Up[b * n_out_pad + k] * out_sd[k] + out_mean[k]);
           // dY*/du = Y*^(1 - lambda) sigma_k
-          g += w_mass / (float)B * sgn * (ys > 0.0f ? exp2f(0.9f * log2f(ys)) : 0.0f) * out_sd[k];
+          const float dys = (ys > 0.0f ? exp2f(0.9f * log2f(ys)) : 0.0f) * out_sd[k];
+          float f = 0.0f;
+          if (mass) f += w_mass / (float)B * sgn;
+          if (hrr) f += w_hrr * 2.0f / (float)B * eb * hrr_c[b * K + k];
+          g += f * dys;
         }
       }
       const bf16 gb = __float2bfloat16_rn(g);
@@ -373,30 +416,35 @@ __global__ void loss_grad_kernel(int64_t B, int K, int n_out_pad, const float* U
   }
   sh[0][threadIdx.x] = ld;
   sh[1][threadIdx.x] = lm;
+  sh[2][threadIdx.x] = lh;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
       sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
       sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + o];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = sh[0][0] / (float)(B * K);
-    part[2 * blockIdx.x + 1] = sh[1][0] / (float)B;
+    part[3 * blockIdx.x] = sh[0][0] / (float)(B * K);
+    part[3 * blockIdx.x + 1] = sh[1][0] / (float)B;
+    part[3 * blockIdx.x + 2] = sh[2][0] / (float)B;
   }
 }
 
-__global__ void loss_final_kernel(int nb, const float* part, float w_data, float w_mass, float* out) {
+__global__ void loss_final_kernel(int nb, const float* part, float w_data, float w_mass, float w_hrr, float* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    float a = 0.0f, b = 0.0f;
+    float a = 0.0f, b = 0.0f, c = 0.0f;
     for (int i = 0; i < nb; ++i) {
-      a += part[2 * i];
-      b += part[2 * i + 1];
+      a += part[3 * i];
+      b += part[3 * i + 1];
+      c += part[3 * i + 2];
     }
-    out[0] = w_data * a + w_mass * b;
+    out[0] = w_data * a + w_mass * b + w_hrr * c;
     out[1] = a;
     out[2] = b;
+    out[3] = c;
   }
 }
 
@@ -706,6 +754,19 @@ int chem_ann_targets(chem_ann a, int64_t n, int64_t ld, const double* Y0, const 
   return cuda_check(cudaGetLastError(), "targets_kernel launch");
 }
 
+int chem_ann_hrr_coeffs(chem_ann a, int64_t n, int64_t ld, const double* T0, const double* p, const double* Y0,
+                        const double* Y1, double dt, double scale, float* hrr_c, float* hrr_r, chem_stream stream) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (n < 0 || ld < n) return set_error(CHEM_E_ARG, "chem_ann_hrr_coeffs: need 0 <= n <= ld");
+  if (!(dt > 0.0) || !(scale > 0.0)) return set_error(CHEM_E_ARG, "chem_ann_hrr_coeffs: dt and scale must be positive");
+  if (n == 0) return CHEM_OK;
+  if (!T0 || !p || !Y0 || !Y1 || !hrr_c || !hrr_r) return set_error(CHEM_E_ARG, "chem_ann_hrr_coeffs: null array");
+  hrr_coeff_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(a->dm, n, ld, T0, p, Y0, Y1, dt, scale,
+                                                                      hrr_c, hrr_r);
+  return cuda_check(cudaGetLastError(), "hrr_coeff_kernel launch");
+}
+
 // forward pass over rows [0, M) of X (BF16 [M, 64]) into U (FP32 [M, n_out_pad]), through
 // BF16 activation buffers act[l] ([M, dims[l+1]]); optionally keeping pre-activations zs[l]
 static int forward_rows(chem_ann a, const bf16* X, int64_t M, bf16* const* act, bf16* const* zs, float* U,
@@ -859,12 +920,15 @@ int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, 
   return CHEM_OK;
 }
 
-int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float* bcty, int64_t B,
-                        const chem_train_opts* opts, float* loss_out, chem_stream stream) {
+int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float* bcty, const float* hrr_c,
+                        const float* hrr_r, int64_t B, const chem_train_opts* opts, float* loss_out,
+                        chem_stream stream) {
   int rc = check_ann(a);
   if (rc) return rc;
   if (B < 8 || B > (1 << 20) || B % 8 != 0 || !Xv || !Ut || !opts)
     return set_error(CHEM_E_ARG, "chem_ann_train_step: bad arguments (B must be a multiple of 8)");
+  if (opts->w_hrr != 0.0f && (!bcty || !hrr_c || !hrr_r))
+    return set_error(CHEM_E_ARG, "chem_ann_train_step: w_hrr != 0 needs bcty, hrr_c and hrr_r");
   cudaStream_t s = (cudaStream_t)stream;
   const bf16* X = (const bf16*)Xv;
   if (B > a->tcap) {
@@ -900,8 +964,9 @@ int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float
   const int nbl = (int)std::min<int64_t>((B + 255) / 256, 2048);
   const int Lo = a->L - 1;
   loss_grad_kernel<<<nbl, 256, 0, s>>>(B, a->K, a->n_out_pad, t.Up, Ut, bcty, om, om + a->n_out, opts->w_data,
-                                      opts->w_mass, t.dZ[Lo], t.dZT[Lo], a->loss_part);
-  if (loss_out) loss_final_kernel<<<1, 32, 0, s>>>(nbl, a->loss_part, opts->w_data, opts->w_mass, loss_out);
+                                      opts->w_mass, hrr_c, hrr_r, opts->w_hrr, t.dZ[Lo], t.dZT[Lo], a->loss_part);
+  if (loss_out)
+    loss_final_kernel<<<1, 32, 0, s>>>(nbl, a->loss_part, opts->w_data, opts->w_mass, opts->w_hrr, loss_out);
   // backward
   dim3 tb(32, 8);
   for (int l = Lo; l >= 0; --l) {

@@ -187,6 +187,8 @@ struct chem_mech_s {
   void* dmem = nullptr;
   int device = 0;
   int K = 0, I = 0, E = 0;
+  int i_n2 = -1;                          // species N2 (-1: none)
+  int el_C = -1, el_H = -1, el_O = -1, el_N = -1;   // element indices (-1: absent)
 };
 
 using namespace chem;
@@ -473,6 +475,15 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   m.rsp2 = (const int4*)(b + orsp2);
   cm->dmem = d;
   cm->K = K; cm->I = I; cm->E = m.E;
+  for (int k = 0; k < K; ++k)
+    if (hm.species[k] == "N2") cm->i_n2 = k;
+  for (int e = 0; e < (int)hm.elements.size(); ++e) {
+    const std::string& nm = hm.elements[e];
+    if (nm == "C") cm->el_C = e;
+    if (nm == "H") cm->el_H = e;
+    if (nm == "O") cm->el_O = e;
+    if (nm == "N") cm->el_N = e;
+  }
   return CHEM_OK;
 }
 
@@ -607,6 +618,28 @@ int chem_pasr_source(chem_mech m, int64_t n, int64_t ld, double dt, const double
   if (y_min < 0.0) y_min = 1e-10;
   if (r_min < 0.0) r_min = 1e-9;
   return launch_pasr(m->dev, n, ld, dt, rho, Y0, Y1, k_sgs, eps, nu, y_min, r_min, omega, kappa,
+                     (cudaStream_t)stream);
+}
+
+size_t chem_hfrd_workspace_bytes(void) { return 256; }
+
+int chem_hfrd_augment(chem_mech m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                      const double* gamma, const chem_hfrd_opts* opts, double* T_out, double* p_out,
+                      double* Y_out, int32_t* keep, void* workspace, size_t ws_bytes, chem_stream stream) {
+  int rc = check_mech(m);
+  if (rc) return rc;
+  if (n < 0 || ld < n) return set_error(CHEM_E_ARG, "chem_hfrd_augment: need 0 <= n <= ld");
+  if (n == 0) return CHEM_OK;
+  if (!T || !p || !Y || !gamma || !T_out || !p_out || !Y_out || !keep)
+    return set_error(CHEM_E_ARG, "chem_hfrd_augment: null array argument");
+  if (!workspace || ws_bytes < chem_hfrd_workspace_bytes())
+    return set_error(CHEM_E_WORKSPACE, "chem_hfrd_augment: workspace missing or smaller than chem_hfrd_workspace_bytes()");
+  if (m->i_n2 < 0 || m->el_H < 0 || m->el_O < 0 || m->el_N < 0)
+    return set_error(CHEM_E_UNSUPPORTED, "chem_hfrd_augment: the mechanism needs species N2 and elements H, O, N");
+  chem_hfrd_opts o{0.125, 10.0, 0.1, {2.65, 4.67}, {0.254, 0.320}, {0.20, 1.15}};
+  if (opts) o = *opts;
+  HfrdIdx ix{m->i_n2, m->el_C, m->el_H, m->el_O, m->el_N};
+  return launch_hfrd(m->dev, n, ld, T, p, Y, gamma, o, ix, T_out, p_out, Y_out, keep, (double*)workspace,
                      (cudaStream_t)stream);
 }
 

@@ -1,14 +1,15 @@
 // tcgen05 / TMA / mbarrier building blocks for the BF16 MLP GEMMs (sm_103a), inline PTX.
 //
 // C[M, N] = A[M, K] * B[N, K]^T with A and B BF16, K-major (row-major with K contiguous),
-// FP32 accumulation in tensor memory.  One CTA of 4 warps computes a 128 x BN tile:
+// FP32 accumulation in tensor memory.  One CTA of 8 warps computes a 128 x BN tile:
 //   thread 0   -- TMA producer: 64-wide K slabs of A and B into a ring of shared-memory stages
 //                 (128-byte swizzle), completion counted on the stage's "full" mbarrier;
 //   thread 32  -- MMA issuer: four tcgen05.mma (K = 16 each) per slab, then tcgen05.commit
 //                 frees the stage ("empty" mbarrier) and, after the last slab, signals the
 //                 epilogue ("done" mbarrier);
-//   warps 0-3  -- epilogue: tcgen05.ld of their 32 accumulator rows (TMEM lanes), fused
-//                 bias / GELU / GELU' / conversion, stores.
+//   warps 0-7  -- epilogue: tcgen05.ld of the 32 accumulator rows (TMEM lanes) of warp % 4,
+//                 alternate 32-column chunks per warp pair, fused bias / GELU / GELU' /
+//                 conversion, stores.
 // Every mbarrier wait is bounded; a wait that runs out sets the caller's error flag and the
 // kernel still runs to its end (TMEM is freed, nothing hangs).
 #pragma once

@@ -196,6 +196,14 @@ int launch_pasr(const DevMech& m, int64_t n, int64_t ld, double dt, const double
                 const double* Y1, const double* ksgs, const double* eps, const double* nu, double y_min,
                 double r_min, double* omega, double* kappa, cudaStream_t s);
 
+// hfrd.cu
+struct HfrdIdx {
+  int i_n2, el_C, el_H, el_O, el_N;
+};
+int launch_hfrd(const DevMech& m, int64_t n, int64_t ld, const double* T, const double* p, const double* Y,
+                const double* gamma, const chem_hfrd_opts& o, const HfrdIdx& ix, double* T_out, double* p_out,
+                double* Y_out, int32_t* keep, double* ranges, cudaStream_t s);
+
 // probe.cu
 int launch_fp64_probe(double* gflops, cudaStream_t s);
 

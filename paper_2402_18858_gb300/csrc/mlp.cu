@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdint>
@@ -19,11 +20,32 @@ namespace chem {
 using bf16 = __nv_bfloat16;
 
 // ------------------------------------------------------------------------------------------
-// GELU (exact erf form, Hendrycks & Gimpel 2016) and its derivative
+// GELU (erf form, Hendrycks & Gimpel 2016) and its derivative.  erf by the rational
+// approximation of Abramowitz & Stegun, Handbook of Mathematical Functions, eq. 7.1.26
+// (Hastings): erf z = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-z^2}, t = 1 / (1 + p z),
+// z >= 0, |error| <= 1.5e-7 (6e-7 in FP32 arithmetic); GELU within 2.1e-7 max(1, |x|), far below
+// the BF16 rounding of the outputs.  One reciprocal and one exponential on the special-function
+// unit, shared by GELU' through e^{-z^2} = e^{-x^2/2}.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float erf_as(float z, float& ez2) {
+  const float az = fabsf(z);
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, az, 1.0f));
+  float q = fmaf(t, 1.061405429f, -1.453152027f);
+  q = fmaf(q, t, 1.421413741f);
+  q = fmaf(q, t, -0.284496736f);
+  q = fmaf(q, t, 0.254829592f);
+  ez2 = __expf(-az * az);
+  return copysignf(fmaf(-q * t, ez2, 1.0f), z);
+}
+__device__ __forceinline__ float gelu_f(float x) {
+  float ez2;
+  const float e = erf_as(x * 0.70710678118654752f, ez2);
+  return 0.5f * x * (1.0f + e);
+}
 __device__ __forceinline__ float dgelu_f(float x) {
-  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+  float ez2;
+  const float e = erf_as(x * 0.70710678118654752f, ez2);
+  return fmaf(x * 0.39894228040143268f, ez2, 0.5f * (1.0f + e));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -45,12 +67,72 @@ struct TileCfg {
   static constexpr size_t SMEM = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 2) * 8 + 16;
 };
 
+// epilogue of one 32-column chunk of one accumulator row: columns col0 .. col0 + nv - 1 of row
+template <int EPI>
+__device__ __forceinline__ void epi_chunk(float (&v)[32], int row, int col0, int nv, const GemmEpi& e) {
+  if (EPI == 0 || EPI == 1) {   // + bias
+    if (e.bias) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] += (i < nv) ? __ldg(e.bias + col0 + i) : 0.0f;
+    }
+  }
+  if (EPI == 0) {
+    // hidden layer forward: out = bf16(GELU(acc + b)); optional pre-activation copy
+    bf16* o = (bf16*)e.out + (size_t)row * e.ldo + col0;
+    bf16* zo = e.zout ? e.zout + (size_t)row * e.ldo + col0 : nullptr;
+    if (nv == 32) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        __align__(16) bf16 t[8], u[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          t[i] = __float2bfloat16_rn(gelu_f(v[8 * q + i]));
+          u[i] = __float2bfloat16_rn(v[8 * q + i]);
+        }
+        *(uint4*)(o + 8 * q) = *(const uint4*)t;
+        if (zo) *(uint4*)(zo + 8 * q) = *(const uint4*)u;
+      }
+    } else {
+      for (int i = 0; i < nv; ++i) {
+        o[i] = __float2bfloat16_rn(gelu_f(v[i]));
+        if (zo) zo[i] = __float2bfloat16_rn(v[i]);
+      }
+    }
+  } else if (EPI == 1 || EPI == 3) {
+    // output layer (acc + b) or weight gradient (acc), FP32
+    float* o = (float*)e.out + (size_t)row * e.ldo + col0;
+    if (nv == 32) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) *(float4*)(o + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+      for (int i = 0; i < nv; ++i) o[i] = v[i];
+    }
+  } else if (EPI == 2) {
+    // hidden-layer backward: dZ = acc * GELU'(z)
+    const bf16* zz = e.z + (size_t)row * e.ldz + col0;
+    bf16* o = (bf16*)e.out + (size_t)row * e.ldo + col0;
+    if (nv == 32) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        __align__(16) bf16 zin[8], t[8];
+        *(uint4*)zin = __ldg((const uint4*)(zz + 8 * q));
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = __float2bfloat16_rn(v[8 * q + i] * dgelu_f(__bfloat162float(zin[i])));
+        *(uint4*)(o + 8 * q) = *(const uint4*)t;
+      }
+    } else {
+      for (int i = 0; i < nv; ++i) o[i] = __float2bfloat16_rn(v[i] * dgelu_f(__bfloat162float(zz[i])));
+    }
+  }
+}
+
+// S (1..STAGES, a launch argument) stages in the ring: min(STAGES, K slabs), so that a
+// short K takes less shared memory and more CTAs share an SM
 template <int BN, int EPI>
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
+__global__ void __launch_bounds__(256) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
                                                            const __grid_constant__ CUtensorMap tb,
-                                                           GemmEpi e, int M, int N, int K, int* err) {
+                                                           GemmEpi e, int M, int N, int K, int S, int* err) {
   using C = TileCfg<BN>;
-  constexpr int S = C::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -109,76 +191,158 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __grid_constant__ 
   const bool ok = tc::mbar_wait(done, 0, err, 3);
   tc::tc_fence_after();
   if (ok) {
-    const int row = m0 + warp * 32 + lane;
+    // 8 epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (the rows it may access) and
+    // every second 32-column chunk starting at chunk w / 4
+    const int quarter = warp & 3;
+    const int row = m0 + quarter * 32 + lane;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
+    for (int c0 = (warp >> 2) * 32; c0 < BN; c0 += 64) {
       if (n0 + c0 >= N) break;
       float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (row < M) {   // no early exit: the next tcgen05.ld needs the whole warp
-      const int col0 = n0 + c0;
-      const int nv = min(32, N - col0);
-      if (EPI == 0 || EPI == 1) {   // + bias
-        if (e.bias) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += (i < nv) ? __ldg(e.bias + col0 + i) : 0.0f;
-        }
-      }
-      if (EPI == 0) {
-        // hidden layer forward: out = bf16(GELU(acc + b)); optional pre-activation copy
-        bf16* o = (bf16*)e.out + (size_t)row * e.ldo + col0;
-        bf16* zo = e.zout ? e.zout + (size_t)row * e.ldo + col0 : nullptr;
-        if (nv == 32) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            __align__(16) bf16 t[8], u[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              t[i] = __float2bfloat16_rn(gelu_f(v[8 * q + i]));
-              u[i] = __float2bfloat16_rn(v[8 * q + i]);
-            }
-            *(uint4*)(o + 8 * q) = *(const uint4*)t;
-            if (zo) *(uint4*)(zo + 8 * q) = *(const uint4*)u;
-          }
-        } else {
-          for (int i = 0; i < nv; ++i) {
-            o[i] = __float2bfloat16_rn(gelu_f(v[i]));
-            if (zo) zo[i] = __float2bfloat16_rn(v[i]);
-          }
-        }
-      } else if (EPI == 1 || EPI == 3) {
-        // output layer (acc + b) or weight gradient (acc), FP32
-        float* o = (float*)e.out + (size_t)row * e.ldo + col0;
-        if (nv == 32) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) *(float4*)(o + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        } else {
-          for (int i = 0; i < nv; ++i) o[i] = v[i];
-        }
-      } else if (EPI == 2) {
-        // hidden-layer backward: dZ = acc * GELU'(z)
-        const bf16* zz = e.z + (size_t)row * e.ldz + col0;
-        bf16* o = (bf16*)e.out + (size_t)row * e.ldo + col0;
-        if (nv == 32) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            __align__(16) bf16 zin[8], t[8];
-            *(uint4*)zin = __ldg((const uint4*)(zz + 8 * q));
-#pragma unroll
-            for (int i = 0; i < 8; ++i) t[i] = __float2bfloat16_rn(v[8 * q + i] * dgelu_f(__bfloat162float(zin[i])));
-            *(uint4*)(o + 8 * q) = *(const uint4*)t;
-          }
-        } else {
-          for (int i = 0; i < nv; ++i) o[i] = __float2bfloat16_rn(v[i] * dgelu_f(__bfloat162float(zz[i])));
-        }
-      }
-      }
+      tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+      if (row < M)   // no early exit: the next tcgen05.ld needs the whole warp
+        epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), e);
       __syncwarp();
     }
   }
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 2) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------------------------------
+// Persistent variant for long K: one CTA per SM walks a static tile schedule (N tiles fastest,
+// so the CTAs working at one time share the A row block in L2).  Warp 0 (one thread) streams
+// A/B slabs through an S-stage ring, warp 1 (one thread) issues the MMAs into one of two TMEM
+// accumulators, warps 2-9 run the epilogue of the previous tile from the other accumulator, so
+// the tensor core does not wait for the epilogue.  Barriers: full/empty per stage (TMA ->
+// MMA -> TMA), acc_full/acc_empty per accumulator (MMA -> epilogue -> MMA).  All waits are
+// bounded; after a timeout every role stops at its next wait.
+// ------------------------------------------------------------------------------------------
+template <int BN>
+struct PersistCfg {
+  static constexpr size_t A_BYTES = (size_t)tc::BM * tc::BK * 2;
+  static constexpr size_t B_BYTES = (size_t)BN * tc::BK * 2;
+  static constexpr int STAGES = (int)((200 * 1024) / (A_BYTES + B_BYTES)) < 8
+                                    ? (int)((200 * 1024) / (A_BYTES + B_BYTES)) : 8;
+  static constexpr uint32_t ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+  static constexpr size_t SMEM = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 4) * 8 + 16;
+};
+
+__device__ __forceinline__ bool gemm_failed(const int* err) { return *(const volatile int*)err != 0; }
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(320, 1) gemm_bf16_persistent(const __grid_constant__ CUtensorMap ta,
+                                                                 const __grid_constant__ CUtensorMap tb,
+                                                                 GemmEpi e, int M, int N, int K, int S, int* err) {
+  using C = PersistCfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + S * C::A_BYTES;
+  uint64_t* full = (uint64_t*)(sB + S * C::B_BYTES);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;    // [2]
+  uint64_t* acce = accf + 2;     // [2]
+  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkb = (K + tc::BK - 1) / tc::BK;
+  const int n_tiles = (N + BN - 1) / BN;
+  const int total = n_tiles * ((M + tc::BM - 1) / tc::BM);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&accf[b], 1);
+      tc::mbar_init(&acce[b], 8);    // one arrival per epilogue warp
+    }
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer over every K slab of every tile of this CTA
+      int g = 0;
+      for (int t = blockIdx.x; t < total && !gemm_failed(err); t += gridDim.x) {
+        const int m0 = (t / n_tiles) * tc::BM, n0 = (t % n_tiles) * BN;
+        bool stop = false;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % S;
+          if (g >= S && !tc::mbar_wait(&empty[s], ((g / S) & 1) ^ 1, err, 11)) { stop = true; break; }
+          tc::mbar_expect_tx(&full[s], (uint32_t)(C::A_BYTES + C::B_BYTES));
+          tc::tma_load_2d(sA + s * C::A_BYTES, &ta, &full[s], kb * tc::BK, m0);
+          tc::tma_load_2d(sB + s * C::B_BYTES, &tb, &full[s], kb * tc::BK, n0);
+        }
+        if (stop) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // single-thread MMA issue into the two accumulators in turn
+      constexpr uint32_t idesc = tc::idesc_bf16_f32<tc::BM, BN>();
+      int g = 0, it = 0;
+      for (int t = blockIdx.x; t < total && !gemm_failed(err); t += gridDim.x, ++it) {
+        const int b = it & 1, u = it >> 1;
+        // accumulator b was last used by tile it - 2: wait for its epilogue
+        if (u > 0 && !tc::mbar_wait(&acce[b], (u & 1) ^ 1, err, 12)) break;
+        tc::tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)b * C::ACC_COLS;
+        bool stop = false;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % S;
+          if (!tc::mbar_wait(&full[s], (g / S) & 1, err, 13)) { stop = true; break; }
+          tc::tc_fence_after();
+          const uint64_t da = tc::sw128_desc(sA + s * C::A_BYTES);
+          const uint64_t db = tc::sw128_desc(sB + s * C::B_BYTES);
+#pragma unroll
+          for (int k = 0; k < tc::BK / tc::UMMA_K; ++k)
+            tc::mma_bf16(acc, da + (uint64_t)((k * tc::UMMA_K * 2) >> 4), db + (uint64_t)((k * tc::UMMA_K * 2) >> 4),
+                         idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          tc::mma_commit(&empty[s]);
+        }
+        if (stop) break;
+        tc::mma_commit(&accf[b]);
+      }
+    }
+  } else {
+    // epilogue warps 2..9: warp w reads TMEM lanes 32 (w % 4) .. +31 and every second
+    // 32-column chunk starting at chunk (w - 2) / 4
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    int it = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+      const int b = it & 1, u = it >> 1;
+      if (gemm_failed(err) || !tc::mbar_wait(&accf[b], u & 1, err, 14)) break;
+      tc::tc_fence_after();
+      const int m0 = (t / n_tiles) * tc::BM, n0 = (t % n_tiles) * BN;
+      const int row = m0 + quarter * 32 + lane;
+      const uint32_t acc = tmem + (uint32_t)b * C::ACC_COLS + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int c0 = half * 32; c0 < BN; c0 += 64) {
+        if (n0 + c0 >= N) break;
+        float v[32];
+        tc::tmem_ld32(acc + (uint32_t)c0, v);
+        if (row < M)   // no early exit: the next tcgen05.ld needs the whole warp
+          epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), e);
+        __syncwarp();
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acce[b])) : "memory");
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, C::TMEM_COLS);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -225,17 +389,47 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
   int rc;
   if ((rc = make_map(&ta, A, M, K, lda, tc::BM))) return rc;
   if ((rc = make_map(&tb, B, N, K, ldb, BN))) return rc;
-  constexpr size_t smem = TileCfg<BN>::SMEM;
+  const int nkb_all = (K + tc::BK - 1) / tc::BK;
+  if (nkb_all > 2) {
+    // long K: persistent warp-specialised kernel, one CTA per SM
+    using P = PersistCfg<BN>;
+    static bool pconfigured = false;
+    if (!pconfigured) {
+      if ((rc = cuda_check(cudaFuncSetAttribute(gemm_bf16_persistent<BN, EPI>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM),
+                           "gemm smem attribute")))
+        return rc;
+      pconfigured = true;
+    }
+    const int S = nkb_all < P::STAGES ? nkb_all : P::STAGES;
+    const size_t smem = 1024 + (size_t)S * (P::A_BYTES + P::B_BYTES) + (2 * (size_t)S + 4) * 8 + 16;
+    const int64_t total = (int64_t)((N + BN - 1) / BN) * ((M + tc::BM - 1) / tc::BM);
+    if (total > 0x7fffffff) return set_error(CHEM_E_ARG, "gemm: too many tiles in one call");
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 1;
+    }
+    const int grid = (int)std::min<int64_t>(total, (int64_t)sms);
+    gemm_bf16_persistent<BN, EPI><<<grid, 320, smem, s>>>(ta, tb, e, M, N, K, S, err);
+    return cuda_check(cudaGetLastError(), "gemm_bf16_persistent launch");
+  }
+  using Cfg = TileCfg<BN>;
   static bool configured = false;
   if (!configured) {
     if ((rc = cuda_check(cudaFuncSetAttribute(gemm_bf16_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem), "gemm smem attribute")))
+                                              (int)Cfg::SMEM), "gemm smem attribute")))
       return rc;
     configured = true;
   }
+  const int nkb = (K + tc::BK - 1) / tc::BK;
+  const int S = nkb < Cfg::STAGES ? nkb : Cfg::STAGES;
+  const size_t smem = 1024 + (size_t)S * (Cfg::A_BYTES + Cfg::B_BYTES) + (2 * (size_t)S + 2) * 8 + 16;
   if ((M + tc::BM - 1) / tc::BM > 65535) return set_error(CHEM_E_ARG, "gemm: more than 65535 row blocks in one call");
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + tc::BM - 1) / tc::BM));
-  gemm_bf16_kernel<BN, EPI><<<grid, 128, smem, s>>>(ta, tb, e, M, N, K, err);
+  gemm_bf16_kernel<BN, EPI><<<grid, 256, smem, s>>>(ta, tb, e, M, N, K, S, err);
   return cuda_check(cudaGetLastError(), "gemm_bf16_kernel launch");
 }
 
@@ -245,14 +439,20 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
 int gemm_bf16(int epi, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int M, int N, int K,
               const GemmEpi& e, int* err, cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return CHEM_OK;
-  // tile width: the least padded width ceil(N / BN) BN, ties to the wider tile (N = 1600 and
-  // 800 take 160, N = 400 and 2000 take 224, N = 1000 and 500 take 256)
-  static const int kBN[] = {256, 224, 160, 128, 64, 32};
-  int bn = 256;
-  int64_t best = INT64_MAX;
-  for (int c : kBN) {
-    const int64_t padded = (int64_t)((N + c - 1) / c) * c;
-    if (padded < best) { best = padded; bn = c; }
+  // tile width: N <= 128 takes the narrowest of 32/64/128 that covers it; wider layers take the
+  // tile of at least 128 columns with the least padded width ceil(N / BN) BN, ties to the wider
+  // (N = 1600 and 800 take 160, N = 400 and 2000 take 224, N = 1000 and 500 take 256) -- narrow
+  // tiles on wide layers would reload the A tile once per 32 columns.  A short K (<= 128, the
+  // first layer) takes 128: its time is the epilogue, and 128 TMEM columns per CTA let four
+  // CTAs share an SM instead of two.
+  int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+  if (N > 128 && K > 128) {
+    static const int kBN[] = {256, 224, 160, 128};
+    int64_t best = INT64_MAX;
+    for (int c : kBN) {
+      const int64_t padded = (int64_t)((N + c - 1) / c) * c;
+      if (padded < best) { best = padded; bn = c; }
+    }
   }
 #define CHEM_GEMM_CASE(BNV)                                                                    \
   if (bn == BNV) {                                                                             \

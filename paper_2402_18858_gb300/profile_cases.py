@@ -5,6 +5,7 @@
     python -m paper_2402_18858_gb300.profile_cases mlp --cells 65536
     python -m paper_2402_18858_gb300.profile_cases rates --cells 65536
     python -m paper_2402_18858_gb300.profile_cases jacobian --cells 8192
+    python -m paper_2402_18858_gb300.profile_cases pasr --cells 1048576
 
 Each case loads the 30-species workload mechanism, builds seeded inputs, runs the operation
 `--repeats` times (the first is the warm-up) and prints the CUDA-event time of the last one.
@@ -26,7 +27,7 @@ CKPT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models", "ann_c
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["di", "thermo", "mlp", "rates", "jacobian"])
+    ap.add_argument("case", choices=["di", "thermo", "mlp", "rates", "jacobian", "pasr"])
     ap.add_argument("--cells", type=int, default=8192)
     ap.add_argument("--repeats", type=int, default=2)
     a = ap.parse_args()
@@ -61,6 +62,16 @@ def main():
 
         def run():
             chem.chem_jacobian(gm, T0, p, Y0, jac)
+    elif a.case == "pasr":
+        tf = wl.make_turbulence(n, 102)
+        rho, k, eps, nu = (torch.as_tensor(x, device=dev) for x in (tf.rho, tf.k, tf.eps, tf.nu))
+        Y1 = (Y0 * (1.0 + 1e-3 * torch.randn(Y0.shape, dtype=torch.float64, device=dev,
+                                               generator=torch.Generator(device=dev).manual_seed(5)))).contiguous()
+        omega = torch.empty_like(Y0)
+        kap = torch.empty_like(T0)
+
+        def run():
+            chem.chem_pasr_source(gm, 5e-6, rho, Y0, Y1, k, eps, nu, omega, kap)
     elif a.case == "thermo":
         outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
 

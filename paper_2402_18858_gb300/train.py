@@ -40,8 +40,54 @@ def di_states(gm, m: wl.Mechanism, n: int, seed: int, dt: float, device="cuda", 
     return dict(T0=T0, p=p, Y0=Y0, T1=T1, Y1=Y1, status=status, states=st)
 
 
-def prepare(ann, data, fit: bool = True):
-    """Normalisation (if fit), BF16 features, raw Box-Cox inputs and normalised targets."""
+def hfrd_states(gm, m: wl.Mechanism, n: int, seed: int, dt: float, device="cuda"):
+    """Training states by the random augmentation of Eqs. 3-6 applied to seeded base states
+    (chem_hfrd_augment), the kept ones integrated by DI over dt.  Draws base states until n are
+    kept."""
+    dev = torch.device(device)
+    K = m.n_species
+    parts, got, r = [], 0, 0
+    while got < n:
+        nb = max(2 * (n - got), 1024)
+        st = wl.make_states(m, nb, seed + 1000 * r)
+        g = torch.as_tensor(wl.uniform_draws(3 + K, nb, seed + 1000 * r + 1), device=dev)
+        T = torch.as_tensor(st.T, device=dev)
+        p = torch.as_tensor(st.p, device=dev)
+        Y = torch.as_tensor(st.Y, device=dev)
+        keep = torch.empty(nb, dtype=torch.int32, device=dev)
+        ws = torch.empty(chem.chem_hfrd_workspace_bytes(), dtype=torch.uint8, device=dev)
+        chem.chem_hfrd_augment(gm, T, p, Y, g, T, p, Y, keep, ws)
+        sel = torch.nonzero(keep).flatten()[: n - got]
+        parts.append((T[sel], p[sel], Y[:, sel]))
+        got += sel.numel()
+        r += 1
+    T0 = torch.cat([a[0] for a in parts]).contiguous()
+    p = torch.cat([a[1] for a in parts]).contiguous()
+    Y0 = torch.cat([a[2] for a in parts], dim=1).contiguous()
+    T1, Y1 = T0.clone(), Y0.clone()
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = torch.zeros(chem.chem_workspace_bytes(gm, n), dtype=torch.uint8, device=dev)
+    chem.chem_step_di(gm, dt, T1, p, Y1, status, workspace=ws)
+    torch.cuda.synchronize()
+    return dict(T0=T0, p=p, Y0=Y0, T1=T1, Y1=Y1, status=status, states=None)
+
+
+def hrr_terms(ann, T0, p, Y0, Y1, dt: float):
+    """Coefficients and targets of the heat-release loss term (Eq. 10) in units of the training
+    set's RMS step-mean heat release (first pass in W/m^3 to find that scale)."""
+    n, K = T0.numel(), ann.n_out
+    c = torch.empty((n, K), dtype=torch.float32, device=T0.device)
+    r = torch.empty(n, dtype=torch.float32, device=T0.device)
+    chem.chem_ann_hrr_coeffs(ann, dt, 1.0, T0, p, Y0, Y1, c, r)
+    scale = float(torch.sqrt((r.double() ** 2).mean()).item()) or 1.0
+    chem.chem_ann_hrr_coeffs(ann, dt, scale, T0, p, Y0, Y1, c, r)
+    torch.cuda.synchronize()
+    return c, r, scale
+
+
+def prepare(ann, data, fit: bool = True, dt: Optional[float] = None):
+    """Normalisation (if fit), BF16 features, raw Box-Cox inputs and normalised targets; with dt,
+    also the heat-release loss terms (returned as a fourth item (c, r, scale))."""
     ok = data["status"] == 0
     T0, p, Y0, Y1 = data["T0"], data["p"], data["Y0"], data["Y1"]
     if not bool(ok.all()):
@@ -57,17 +103,19 @@ def prepare(ann, data, fit: bool = True):
     chem.chem_ann_features(ann, T0, p, Y0, X, bcty=bcty)
     chem.chem_ann_targets(ann, Y0, Y1, U)
     torch.cuda.synchronize()
+    if dt is not None:
+        return X, bcty, U, hrr_terms(ann, T0, p, Y0, Y1, dt)
     return X, bcty, U
 
 
 def train(ann, X, bcty, U, epochs: int = 20, batch: int = 8192, lr: float = 1e-3, lr_min: float = 2e-5,
-          w_data: float = 1.0, w_mass: float = 0.1, log_every: int = 0) -> Dict:
+          w_data: float = 1.0, w_mass: float = 0.1, log_every: int = 0, hrr=None, w_hrr: float = 0.0) -> Dict:
     """Adam over minibatches (contiguous slices, offset each epoch), cosine learning rate."""
     n = X.shape[0] - X.shape[0] % 8
     batch = min(batch, n) - min(batch, n) % 8
     steps_per_epoch = max(1, n // batch)
     total = epochs * steps_per_epoch
-    loss = torch.zeros(3, dtype=torch.float32, device=X.device)
+    loss = torch.zeros(4, dtype=torch.float32, device=X.device)
     hist = []
     t0 = time.perf_counter()
     step = 0
@@ -76,8 +124,11 @@ def train(ann, X, bcty, U, epochs: int = 20, batch: int = 8192, lr: float = 1e-3
         for s in range(steps_per_epoch):
             a = off + s * batch
             cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / max(total - 1, 1)))
+            hc = hrr[0][a:a + batch] if hrr is not None and w_hrr != 0.0 else None
+            hr = hrr[1][a:a + batch] if hrr is not None and w_hrr != 0.0 else None
             chem.chem_ann_train_step(ann, X[a:a + batch], U[a:a + batch], bcty[a:a + batch], lr=cur,
-                                     w_data=w_data, w_mass=w_mass, loss_out=loss)
+                                     w_data=w_data, w_mass=w_mass, loss_out=loss, hrr_c=hc, hrr_r=hr,
+                                     w_hrr=w_hrr if hrr is not None else 0.0)
             step += 1
             if log_every and step % log_every == 0:
                 hist.append((step, float(loss[1].item())))
@@ -165,6 +216,9 @@ def main():
     ap.add_argument("--infer-cells", type=int, default=0,
                     help="> 0: also time the learned step with fallback on this many fresh cells")
     ap.add_argument("--elem-tol", type=float, default=1e-2)
+    ap.add_argument("--w-hrr", type=float, default=0.0, help="weight W3 of the heat-release loss term (Eq. 10)")
+    ap.add_argument("--hfrd", action="store_true",
+                    help="train on states augmented by Eqs. 3-6 (random data method) instead of the plain draws")
     args = ap.parse_args()
     build.build()
     m = wl.make_mechanism(args.kind, args.mech_seed)
@@ -172,17 +226,26 @@ def main():
     gm = chem.chem_load_mech(path)
     ann = chem.chem_ann_create(gm, HIDDEN_30 if m.n_species <= 32 else HIDDEN_53, seed=args.seed)
     t0 = time.perf_counter()
-    data = di_states(gm, m, args.train_cells, args.seed, args.dt)
+    if args.hfrd:
+        data = hfrd_states(gm, m, args.train_cells, args.seed, args.dt)
+    else:
+        data = di_states(gm, m, args.train_cells, args.seed, args.dt)
     gen_s = time.perf_counter() - t0
-    X, bcty, U = prepare(ann, data)
+    hrr = None
+    if args.w_hrr != 0.0:
+        X, bcty, U, hrr = prepare(ann, data, dt=args.dt)
+    else:
+        X, bcty, U = prepare(ann, data)
     del data
-    tr = train(ann, X, bcty, U, epochs=args.epochs, batch=args.batch, lr=args.lr, log_every=500)
+    tr = train(ann, X, bcty, U, epochs=args.epochs, batch=args.batch, lr=args.lr, log_every=500,
+               hrr=hrr, w_hrr=args.w_hrr)
     if args.out:
         chem.chem_ann_save(ann, args.out, with_moments=args.with_moments)
     del X, bcty, U
     ev = evaluate(gm, ann, di_states(gm, m, args.eval_cells, args.eval_seed, args.dt), args.dt,
                   repeats=args.repeats, elem_tol=args.elem_tol)
-    out = dict(kind=args.kind, hidden=ann.dims, data_generation_s=gen_s,
+    out = dict(kind=args.kind, hidden=ann.dims, hfrd=bool(args.hfrd), w_hrr=args.w_hrr,
+               hrr_scale=hrr[2] if hrr is not None else None, data_generation_s=gen_s,
                di_generation_cells_per_s=args.train_cells / gen_s, train=tr, eval=ev)
     if args.infer_cells > 0:
         out["inference"] = time_inference(gm, m, ann, args.infer_cells, args.eval_seed + 1, args.dt,

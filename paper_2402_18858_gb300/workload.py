@@ -545,6 +545,12 @@ WORKLOADS = {
 }
 
 
+def uniform_draws(rows: int, n: int, seed: int) -> np.ndarray:
+    """Seeded uniform numbers in [-1, 1], shape [rows, n] (the gamma of the random
+    augmentation of training states)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(rows, n))
+
+
 @dataclasses.dataclass
 class TurbulenceFields:
     """Per-cell LES sub-grid quantities for the PaSR source: density (kg/m^3), sub-grid kinetic

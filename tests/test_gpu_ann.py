@@ -108,7 +108,7 @@ def test_training_is_deterministic_and_resumable(lc, setup, tmp_path, mechs):
     gm, ann0, st, X, bcty, U = setup
     ann = lc.chem_ann_create(gm, HIDDEN, seed=3)
     lc.chem_ann_set_norm(ann, lc.chem_ann_get_norm(ann0))
-    loss = torch.zeros(3, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(4, dtype=torch.float32, device="cuda")
     B = 1024
     hist = []
     for it in range(30):
@@ -162,3 +162,55 @@ def test_widths_that_are_not_multiples_of_8(lc, setup):
     Uo, _ = mlp.forward(real, X.float().cpu().numpy().astype(np.float64), bf16=True)
     d = Ug.cpu().numpy() - Uo
     assert np.abs(d).max() <= 2e-3 * np.abs(Uo).max() + 1e-3
+
+
+def test_gradient_parity_with_heat_release_term(lc, setup):
+    """Eq. 11 with W3 = 0.5: the GPU gradient of all three loss terms against the FP64 oracle."""
+    gm, ann, st, X, bcty, U = setup
+    B, K = 512, ann.n_out
+    rng = np.random.default_rng(9)
+    c = torch.as_tensor(rng.standard_normal((B, K)) * 0.3, dtype=torch.float32, device="cuda")
+    r = torch.as_tensor(rng.standard_normal(B) * 0.2, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(4, dtype=torch.float32, device="cuda")
+    lc.chem_ann_train_step(ann, X[:B].contiguous(), U[:B].contiguous(), bcty[:B].contiguous(), apply=False,
+                           hrr_c=c, hrr_r=r, w_hrr=0.5, loss_out=loss)
+    torch.cuda.synchronize()
+    assert lc.chem_ann_error(ann) == 0
+    g_gpu = mlp.unflatten(lc.chem_ann_get_params(ann, which=1), ann.dims)
+    params = mlp.unflatten(lc.chem_ann_get_params(ann), ann.dims)
+    norm = lc.chem_ann_get_norm(ann)
+    om, osd = norm[4 * ann.n_in:4 * ann.n_in + K].astype(np.float64), norm[4 * ann.n_in + K:].astype(np.float64)
+    Uo, cache = mlp.forward(params, X[:B].float().cpu().numpy().astype(np.float64), bf16=True)
+    Lt, Ld, Lm, Lh, dU = mlp.loss_and_grad(Uo, U[:B].cpu().numpy().astype(np.float64), K,
+                                           bcty[:B].cpu().numpy().astype(np.float64), om, osd, 1.0, 0.1,
+                                           0.5, c.double().cpu().numpy(), r.double().cpu().numpy(), with_hrr=True)
+    lg = loss.cpu().numpy()
+    assert lg[3] == pytest.approx(Lh, rel=2e-2) and Lh > 0
+    assert lg[0] == pytest.approx(Lt, rel=2e-2)
+    g_or = mlp.backward(params, cache, dU)
+    for l, ((gw, gb), (ow, ob)) in enumerate(zip(g_gpu, g_or)):
+        assert np.linalg.norm(gw - ow) <= 3e-2 * np.linalg.norm(ow), l
+        assert np.linalg.norm(gb - ob) <= 3e-2 * np.linalg.norm(ob) + 1e-12, l
+
+
+def test_heat_release_coefficients(lc, setup, mechs, oracles):
+    """chem_ann_hrr_coeffs against the oracle's definition with its own NASA-7 enthalpies."""
+    gm, ann, st, X, bcty, U = setup
+    m, _ = mechs["c_30"]
+    o = oracles["c_30"]
+    n, K, dt, scale = 700, m.n_species, 5e-6, 3.0e9
+    dev = torch.device("cuda")
+    T0 = torch.as_tensor(st.T[:n], device=dev)
+    p = torch.as_tensor(st.p[:n], device=dev)
+    Y0 = torch.as_tensor(st.Y[:, :n].copy(), device=dev)
+    dY = np.random.default_rng(10).standard_normal((K, n)) * 1e-3 * st.Y[:, :n]
+    Y1 = torch.as_tensor(st.Y[:, :n] + dY, device=dev)
+    c = torch.empty((n, K), dtype=torch.float32, device=dev)
+    r = torch.empty(n, dtype=torch.float32, device=dev)
+    lc.chem_ann_hrr_coeffs(ann, dt, scale, T0, p, Y0, Y1, c, r)
+    torch.cuda.synchronize()
+    h = np.stack([o.species_thermo(st.T[i])[1] * 8.314462618 * st.T[i] for i in range(n)], axis=1)
+    c_o, r_o = mlp.hrr_coefficients(st.T[:n], st.p[:n], st.Y[:, :n], st.Y[:, :n] + dY, dt, np.asarray(m.W), h, scale)
+    # FP64 arithmetic on both sides, FP32 results
+    np.testing.assert_allclose(c.cpu().numpy(), c_o, rtol=2e-7, atol=1e-30)
+    np.testing.assert_allclose(r.cpu().numpy(), r_o, rtol=2e-6, atol=1e-6 * np.abs(r_o).max())

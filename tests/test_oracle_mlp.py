@@ -73,3 +73,52 @@ def test_adam_first_step_closed_form():
     g = np.array([0.3, -2.0, 1e-3, 0.0])
     p, m, v = mlp.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, lr=0.01)
     assert np.allclose(p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+
+
+def test_hrr_term_against_finite_differences_and_by_hand():
+    rng = np.random.default_rng(2)
+    dims = [6, 7, 5, 4]
+    params = _tiny(rng, dims)
+    X = rng.standard_normal((9, 6))
+    Ut = rng.standard_normal((9, 4))
+    bcty = mlp.bct(rng.uniform(1e-6, 0.3, (9, 4)))
+    om, osd = rng.standard_normal(4) * 0.1, rng.uniform(0.5, 2.0, 4)
+    c = rng.standard_normal((9, 4))
+    r = rng.standard_normal(9) * 0.1
+
+    def L(flat):
+        p = mlp.unflatten(flat, dims)
+        U, _ = mlp.forward(p, X)
+        return mlp.loss_and_grad(U, Ut, 4, bcty, om, osd, 1.0, 0.1, 0.7, c, r)[0]
+
+    U, cache = mlp.forward(params, X)
+    Lt, Ld, Lm, Lh, dU = mlp.loss_and_grad(U, Ut, 4, bcty, om, osd, 1.0, 0.1, 0.7, c, r, with_hrr=True)
+    # the term by hand: one sample's squared heat-release error
+    Ys = mlp.ibct(bcty + U[:, :4] * osd + om)
+    e0 = float(np.dot(c[0], Ys[0] - mlp.ibct(bcty[0])) - r[0])
+    assert Lh == pytest.approx(np.mean([(np.dot(c[b], Ys[b] - mlp.ibct(bcty[b])) - r[b]) ** 2
+                                         for b in range(9)]), rel=1e-13)
+    assert Lt == pytest.approx(Ld + 0.1 * Lm + 0.7 * Lh, rel=1e-14) and e0 != 0.0
+    g = mlp.flatten(mlp.backward(params, cache, dU))
+    flat = mlp.flatten(params)
+    fd = np.zeros_like(flat)
+    for i in range(flat.size):
+        e = np.zeros_like(flat)
+        e[i] = 1e-6
+        fd[i] = (L(flat + e) - L(flat - e)) / 2e-6
+    assert np.allclose(g, fd, rtol=1e-5, atol=1e-9)
+
+
+def test_hrr_coefficients_by_hand():
+    # two species with h = (-100, +50) kJ/mol, W = (0.02, 0.03) kg/mol: the step-mean heat
+    # release of converting 1 % of the mass from species 2 to species 1
+    T0, p, dt, scale = np.array([1000.0]), np.array([101325.0]), 1e-6, 2.0
+    W = np.array([0.02, 0.03])
+    h = np.array([[-1.0e5], [5.0e4]])
+    Y0 = np.array([[0.5], [0.5]])
+    Y1 = np.array([[0.51], [0.49]])
+    c, r = mlp.hrr_coefficients(T0, p, Y0, Y1, dt, W, h, scale)
+    rho = 101325.0 / (8.314462618 * 1000.0 * (0.5 / 0.02 + 0.5 / 0.03))
+    hrr = -(rho / dt) * (-1.0e5 / 0.02 * 0.01 + 5.0e4 / 0.03 * (-0.01))
+    assert r[0] == pytest.approx(hrr / scale, rel=1e-13)
+    assert c[0, 0] == pytest.approx(rho * 1.0e5 / 0.02 / (dt * scale), rel=1e-14)
