@@ -182,9 +182,11 @@ typedef struct {
 
 /* Per-sample coefficients of L_HRR (Eq. 10), read as the step-mean heat release
  * HRR = -(rho / dt) sum_k h_k(T0) (Y_k(t+dt) - Y_k(t)) with mass enthalpies at the initial
- * temperature and rho = p / (R T0 sum_k Y0_k / W_k):  hrr_c [n, K] = -rho h_k / (dt scale) and
- * the DI target hrr_r [n] = sum_k hrr_c (Y1 - Y0), both FP32 in units of `scale` (W/m^3, e.g.
- * the RMS heat release of the training set; pass 1 to obtain raw values). */
+ * temperature and rho = p / (R T0 sum_k Y0_k / W_k):  hrr_c [n, K] = -rho (h_k - hbar) /
+ * (dt scale), hbar = sum_k Y0_k h_k (a shift that leaves the heat release of mass-conserving
+ * changes unchanged and keeps mass-sum errors out of the term), and the DI target
+ * hrr_r [n] = sum_k hrr_c (Y1 - Y0), both FP32 in units of `scale` (W/m^3, e.g. the RMS heat
+ * release of the training set; pass 1 to obtain raw values). */
 int chem_ann_hrr_coeffs(chem_ann ann, int64_t n, int64_t ld, const double* T0, const double* p,
                         const double* Y0, const double* Y1, double dt, double scale, float* hrr_c,
                         float* hrr_r, chem_stream stream);

@@ -147,12 +147,17 @@ def hrr_coefficients(T0, p, Y0, Y1, dt, W, h_molar, scale):
     """Per-sample coefficients of the heat-release loss term (Eq. 10), read as the step-mean
     heat release HRR = -(rho / dt) sum_k h_k(T0) (Y_k(t + dt) - Y_k(t)) (W/m^3) with the mass
     enthalpies h_k = h_k,molar / W_k at the initial temperature and the initial density
-    rho = p / (R T0 sum_k Y_k / W_k):  c_bk = -rho h_k / (dt scale) and the DI target
-    r_b = sum_k c_bk (Y1_bk - Y0_bk).  h_molar [K, N] (J/mol) from the oracle's NASA-7;
-    Y0, Y1 [K, N]; returns c [N, K], r [N]."""
+    rho = p / (R T0 sum_k Y_k / W_k):  c_bk = -rho (h_k - hbar) / (dt scale) and the DI target
+    r_b = sum_k c_bk (Y1_bk - Y0_bk).  hbar = sum_k Y0_k h_k, the cell's mean enthalpy: a
+    common shift of the enthalpies leaves the heat release of a mass-conserving change
+    unchanged, and removing the mean keeps a predicted change whose mass fractions do not sum
+    to one (L_mass's concern) from reading as heat release.  h_molar [K, N] (J/mol) from the
+    oracle's NASA-7; Y0, Y1 [K, N]; returns c [N, K], r [N]."""
     R = 8.314462618
     rho = p / (R * T0 * (Y0 / W[:, None]).sum(axis=0))
-    c = -(rho[None, :] * h_molar / W[:, None]) / (dt * scale)
+    h = h_molar / W[:, None]
+    hbar = (Y0 * h).sum(axis=0)
+    c = -(rho[None, :] * (h - hbar[None, :])) / (dt * scale)
     r = (c * (Y1 - Y0)).sum(axis=0)
     return c.T.copy(), r
 def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):

@@ -82,9 +82,11 @@ __device__ __forceinline__ float raw_feature(int j, int64_t i, int64_t ld, const
   return bct_f(Y[(size_t)(j - 2) * ld + i]);
 }
 
-// heat-release coefficients of the L_HRR term (Eq. 10) per sample: c_bk = -rho h_k(T0) / (dt s)
-// (h_k the mass enthalpy from NASA-7 at the initial temperature, rho = p / (R T0 sum Y/W)) and
-// the DI target r_b = sum_k c_bk (Y1_bk - Y0_bk); FP64 arithmetic, FP32 results [n, K], [n]
+// heat-release coefficients of the L_HRR term (Eq. 10) per sample: c_bk = -rho (h_k(T0) - hbar)
+// / (dt s) (h_k the mass enthalpy from NASA-7 at the initial temperature, hbar = sum Y0_k h_k,
+// rho = p / (R T0 sum Y/W)) and the DI target r_b = sum_k c_bk (Y1_bk - Y0_bk); FP64
+// arithmetic, FP32 results [n, K], [n].  The shift by hbar leaves the heat release of any
+// mass-conserving change unchanged and keeps mass-sum errors (L_mass) out of L_HRR.
 __global__ void hrr_coeff_kernel(DevMech m, int64_t n, int64_t ld, const double* T0, const double* p,
                                  const double* Y0, const double* Y1, double dt, double scale, float* c, float* r) {
   const int K = m.K;
@@ -95,11 +97,18 @@ __global__ void hrr_coeff_kernel(DevMech m, int64_t n, int64_t ld, const double*
     const double rho = p[i] / (kR * T * sYW);
     const double f = -rho * kR * T / (dt * scale);
     const int hi = T >= m.Tmid ? 1 : 0;
+    // mass enthalpies over RT (the common factor R T goes into f) and their mean over Y0
+    double hbar = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
+      const double hRT = a[5] + T * (a[6] + T * (a[7] + T * (a[8] + T * a[9]))) + a[10] * invT;
+      hbar += Y0[(size_t)k * ld + i] * hRT * m.invW[k];
+    }
     double acc = 0.0;
     for (int k = 0; k < K; ++k) {
       const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
       const double hRT = a[5] + T * (a[6] + T * (a[7] + T * (a[8] + T * a[9]))) + a[10] * invT;
-      const double ck = f * hRT * m.invW[k];
+      const double ck = f * (hRT * m.invW[k] - hbar);
       c[(size_t)i * K + k] = (float)ck;
       acc += ck * (Y1[(size_t)k * ld + i] - Y0[(size_t)k * ld + i]);
     }

@@ -223,8 +223,9 @@ template <int BN>
 struct PersistCfg {
   static constexpr size_t A_BYTES = (size_t)tc::BM * tc::BK * 2;
   static constexpr size_t B_BYTES = (size_t)BN * tc::BK * 2;
-  static constexpr int STAGES = (int)((200 * 1024) / (A_BYTES + B_BYTES)) < 8
-                                    ? (int)((200 * 1024) / (A_BYTES + B_BYTES)) : 8;
+  // as many stages as fit in 220 KB (at most 8): the ring must cover the L2 latency
+  static constexpr int STAGES = (int)((220 * 1024) / (A_BYTES + B_BYTES)) < 8
+                                    ? (int)((220 * 1024) / (A_BYTES + B_BYTES)) : 8;
   static constexpr uint32_t ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
   static constexpr size_t SMEM = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 4) * 8 + 16;

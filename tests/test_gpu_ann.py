@@ -214,3 +214,29 @@ def test_heat_release_coefficients(lc, setup, mechs, oracles):
     # FP64 arithmetic on both sides, FP32 results
     np.testing.assert_allclose(c.cpu().numpy(), c_o, rtol=2e-7, atol=1e-30)
     np.testing.assert_allclose(r.cpu().numpy(), r_o, rtol=2e-6, atol=1e-6 * np.abs(r_o).max())
+
+
+def test_forward_full_size_sampled(lc, setup, mechs):
+    """The benchmark's 2,000,000-row forward (61 chunks of 32,768 rows, ragged last chunk):
+    512 sampled rows against the FP64 oracle with BF16 storage emulated."""
+    gm, ann, st, X, bcty, U = setup
+    m, _ = mechs["c_30"]
+    n = 2_000_000
+    big = w.make_states(m, n, 56)
+    dev = torch.device("cuda")
+    Xb = torch.empty((n, 64), dtype=torch.bfloat16, device=dev)
+    lc.chem_ann_features(ann, torch.as_tensor(big.T, device=dev), torch.as_tensor(big.p, device=dev),
+                         torch.as_tensor(big.Y, device=dev), Xb)
+    Ug = torch.empty((n, ann.n_out_pad), dtype=torch.float32, device=dev)
+    ws = torch.empty(lc.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device=dev)
+    lc.chem_ann_forward(ann, Xb, Ug, ws)
+    torch.cuda.synchronize()
+    assert lc.chem_ann_error(ann) == 0
+    pick = np.sort(np.random.default_rng(57).choice(n, 512, replace=False))
+    pick[-1] = n - 1
+    params = mlp.unflatten(lc.chem_ann_get_params(ann), ann.dims)
+    Uo, _ = mlp.forward(params, Xb[torch.as_tensor(pick, device=dev)].float().cpu().numpy().astype(np.float64),
+                        bf16=True)
+    d = Ug[torch.as_tensor(pick, device=dev)].cpu().numpy() - Uo
+    assert np.abs(d).max() <= 2e-3 * np.abs(Uo).max() + 1e-3
+    assert np.sqrt((d ** 2).mean()) <= 1e-3 * np.sqrt((Uo ** 2).mean())
