@@ -214,10 +214,11 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
   const double* __restrict__ et = m.exptab;
   const int hi = T >= m.Tmid ? 1 : 0;
   // pass 1: c_p/R per species and the two mixture sums sum Y/W and sum Y c_p/(R W)
-  double sYW = 0.0, cpp = 0.0;
+  double sYW = 0.0, cpp = 0.0, ywr[NPL];
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
     const int k = lane + 32 * s;
+    ywr[s] = 0.0;
     sp.cpR[s] = sp.dcpR[s] = sp.hRT[s] = 0.0;
     if (k < K) {
       const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
@@ -225,6 +226,7 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
       const double cpR = a0 + T * (a1 + T * (a2 + T * (a3 + T * a4)));
       if (JAC) sp.dcpR[s] = a1 + T * (2.0 * a2 + T * (3.0 * a3 + T * 4.0 * a4));
       const double yw = y[s] * __ldg(m.invW + k);
+      ywr[s] = yw;
       sYW += yw;
       cpp += yw * cpR;
       sp.cpR[s] = cpR;
@@ -260,7 +262,7 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
                          + __ldg(a + 10) * invT;
       const double sR = __ldg(a + 11) * lnT + T * (__ldg(a + 12) + T * (__ldg(a + 13) + T * (__ldg(a + 14) + T * __ldg(a + 15))))
                         + __ldg(a + 16);
-      const double Ck = rho * y[s] * __ldg(m.invW + k);
+      const double Ck = rho * ywr[s];
       w.C[k] = Ck;
       Cs[s] = Ck;
       w.hRT[k] = hRT;
@@ -291,7 +293,14 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
   // lane below) and the five exponentials of each falloff reaction (into w.tr), all items
   // packed over the lanes
   const int nb = m.n_tb_end;
-  for (int t = lane; t < m.n_x; t += 32) {
+  // whole rounds before the first falloff item: k_f only, no T term in the argument
+  const int n_plain = (nb / 32) * 32;
+  for (int t = lane; t < n_plain; t += 32) {
+    const double2 x01 = __ldg((const double2*)(m.xarg + 4 * (size_t)t));
+    const double x2 = __ldg(m.xarg + 4 * (size_t)t + 2);
+    w.q[t] = exp_t(fma(-x2, invT, fma(x01.y, lnT, x01.x)), et);
+  }
+  for (int t = n_plain + lane; t < m.n_x; t += 32) {
     const double2 x01 = __ldg((const double2*)(m.xarg + 4 * (size_t)t));
     const double2 x23 = __ldg((const double2*)(m.xarg + 4 * (size_t)t + 2));
     const double e = exp_t(fma(x23.y, T, fma(-x23.x, invT, fma(x01.y, lnT, x01.x))), et);

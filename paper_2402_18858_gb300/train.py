@@ -48,6 +48,8 @@ def hfrd_states(gm, m: wl.Mechanism, n: int, seed: int, dt: float, device="cuda"
     K = m.n_species
     parts, got, r = [], 0, 0
     while got < n:
+        if r >= 8:
+            raise RuntimeError(f"HFRD augmentation kept only {got} of {n} states after {r} rounds of draws")
         nb = max(2 * (n - got), 1024)
         st = wl.make_states(m, nb, seed + 1000 * r)
         g = torch.as_tensor(wl.uniform_draws(3 + K, nb, seed + 1000 * r + 1), device=dev)
