@@ -11,9 +11,15 @@
 * Optional emulation of BF16 storage (round to nearest even) of inputs, weights and hidden
   activations, so that the GPU's BF16 tensor-core forward can be compared element by element.
 
+* Per-species networks (Sec. 2.2: each species' transformed mass fraction is trained and
+  predicted by its own MLP): K independent networks with one output each, evaluated one after
+  the other on the same inputs; their parameters as one flat array stacked by species.
+
 Parity status: forward, backward, loss gradient (all three terms), the heat-release
 coefficients and Adam are pinned by the tests in tests/test_oracle_mlp.py (finite differences,
-closed forms, special values).  The loss weights W1, W2, W3 of Eq. 11 are unstated in the
+closed forms, special values); the per-species networks by their equality with one network
+of block-diagonal weights, by the independence of each output from the other species'
+weights and by finite differences.  The loss weights W1, W2, W3 of Eq. 11 are unstated in the
 paper: W1 = 1, W2 = 0.1 and W3 = 0 by default.
 """
 from __future__ import annotations
@@ -107,6 +113,47 @@ def backward(params: Params, cache, dU: np.ndarray) -> Params:
         if l > 0:
             d = (d @ W) * dgelu(zs[l - 1])
     return grads
+
+
+def unflatten_per_species(flat: np.ndarray, dims: List[int], K: int) -> List[Params]:
+    """Flat parameters of K networks of widths dims (dims[-1] = 1), stored per layer as
+    W [K dims[l+1], dims[l]] then b [K dims[l+1]] with species k in rows k dims[l+1] ...,
+    -> one parameter list per species."""
+    nets: List[Params] = [[] for _ in range(K)]
+    o = 0
+    for l in range(len(dims) - 1):
+        h, c = dims[l + 1], dims[l]
+        W = flat[o:o + K * h * c].reshape(K, h, c).astype(np.float64)
+        o += K * h * c
+        b = flat[o:o + K * h].reshape(K, h).astype(np.float64)
+        o += K * h
+        for k in range(K):
+            nets[k].append((W[k], b[k]))
+    return nets
+
+
+def flatten_per_species(nets: List[Params]) -> np.ndarray:
+    """Inverse of unflatten_per_species."""
+    parts = []
+    for l in range(len(nets[0])):
+        parts.append(np.concatenate([net[l][0].ravel() for net in nets]))
+        parts.append(np.concatenate([net[l][1] for net in nets]))
+    return np.concatenate(parts)
+
+
+def forward_per_species(nets: List[Params], X: np.ndarray, bf16: bool = False):
+    """U[:, k] = MLP_k(X) for each species' own network; returns (U [n, K], caches)."""
+    cols, caches = [], []
+    for net in nets:
+        U, cache = forward(net, X, bf16)
+        cols.append(U[:, 0])
+        caches.append(cache)
+    return np.stack(cols, axis=1), caches
+
+
+def backward_per_species(nets: List[Params], caches, dU: np.ndarray) -> List[Params]:
+    """Gradients of every species' network, given dL/dU [n, >= K]."""
+    return [backward(net, cache, dU[:, k:k + 1]) for k, (net, cache) in enumerate(zip(nets, caches))]
 
 
 def loss_and_grad(U, Ut, K, bcty=None, out_mean=None, out_std=None, w_data=1.0, w_mass=0.1,

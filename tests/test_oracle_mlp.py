@@ -130,3 +130,95 @@ def test_hrr_coefficients_by_hand():
     eps = 1e-3
     assert abs(np.dot(c[0], eps * Y0[:, 0])) <= 1e-12 * eps * np.abs(c[0]).sum()
     assert abs(np.dot(c[0], np.array([eps, 0.0]))) > 1e-3 * eps * np.abs(c[0]).sum()
+
+
+def _block_diagonal(nets):
+    """One network equal to the K per-species networks: the first layer stacks the species'
+    units (shared input), later layers are block diagonal, the output row k reads species k's
+    last hidden block only."""
+    from scipy.linalg import block_diag
+    layers = []
+    for l in range(len(nets[0])):
+        if l == 0:
+            W = np.concatenate([net[0][0] for net in nets], axis=0)
+        else:
+            W = block_diag(*[net[l][0] for net in nets])
+        b = np.concatenate([net[l][1] for net in nets])
+        layers.append((W, b))
+    return layers
+
+
+def test_per_species_equals_block_diagonal_network():
+    # Sec. 2.2 per-species networks written out as one network with zero off-diagonal weights;
+    # the one-network forward and backward are pinned above by finite differences
+    rng = np.random.default_rng(4)
+    K, dims = 5, [6, 7, 5, 3, 1]
+    nets = [_tiny(rng, dims) for _ in range(K)]
+    X = rng.standard_normal((11, 6))
+    big = _block_diagonal(nets)
+    for bf16 in (False, True):
+        U, caches = mlp.forward_per_species(nets, X, bf16=bf16)
+        Ub, cache_b = mlp.forward(big, X, bf16=bf16)
+        assert U.shape == (11, K)
+        assert np.allclose(U, Ub, rtol=1e-13, atol=1e-13)
+    dU = rng.standard_normal((11, K))
+    U, caches = mlp.forward_per_species(nets, X)
+    Ub, cache_b = mlp.forward(big, X)
+    g = mlp.backward_per_species(nets, caches, dU)
+    gb = mlp.backward(big, cache_b, dU)
+    for l in range(len(dims) - 1):
+        h, c = dims[l + 1], dims[l]
+        for k in range(K):
+            rows = slice(k * h, (k + 1) * h)
+            cols = slice(None) if l == 0 else slice(k * c, (k + 1) * c)
+            assert np.allclose(g[k][l][0], gb[l][0][rows, cols], rtol=1e-12, atol=1e-14)
+            assert np.allclose(g[k][l][1], gb[l][1][rows], rtol=1e-12, atol=1e-14)
+
+
+def test_per_species_outputs_are_independent_and_layout_round_trips():
+    rng = np.random.default_rng(5)
+    K, dims = 4, [6, 8, 8, 1]
+    nets = [_tiny(rng, dims) for _ in range(K)]
+    X = rng.standard_normal((7, 6))
+    U0, _ = mlp.forward_per_species(nets, X)
+    # changing species 2's network changes column 2 only
+    nets2 = [list(net) for net in nets]
+    W, b = nets2[2][1]
+    nets2[2][1] = (W + 0.3, b)
+    U1, _ = mlp.forward_per_species(nets2, X)
+    changed = np.abs(U1 - U0).max(axis=0) > 0
+    assert changed.tolist() == [False, False, True, False]
+    # the stacked layout: species k's layer-l weights are rows k h .. (k + 1) h of the layer
+    flat = mlp.flatten_per_species(nets)
+    assert flat.size == K * sum(dims[l + 1] * (dims[l] + 1) for l in range(len(dims) - 1))
+    back = mlp.unflatten_per_species(flat, dims, K)
+    for k in range(K):
+        for (W, b), (W2, b2) in zip(nets[k], back[k]):
+            assert np.array_equal(W, W2) and np.array_equal(b, b2)
+    assert np.array_equal(flat[dims[1] * dims[0]:2 * dims[1] * dims[0]], nets[1][0][0].ravel())
+
+
+def test_per_species_backward_against_finite_differences():
+    # the mass term of the loss couples the species' networks
+    rng = np.random.default_rng(6)
+    K, dims = 3, [5, 4, 3, 1]
+    nets = [_tiny(rng, dims) for _ in range(K)]
+    X = rng.standard_normal((6, 5))
+    Ut = rng.standard_normal((6, K))
+    bcty = mlp.bct(rng.uniform(1e-6, 0.4, (6, K)))
+    om, osd = rng.standard_normal(K) * 0.1, rng.uniform(0.5, 2.0, K)
+
+    def L(flat):
+        U, _ = mlp.forward_per_species(mlp.unflatten_per_species(flat, dims, K), X)
+        return mlp.loss_and_grad(U, Ut, K, bcty, om, osd, 1.0, 0.1)[0]
+
+    U, caches = mlp.forward_per_species(nets, X)
+    _, _, _, dU = mlp.loss_and_grad(U, Ut, K, bcty, om, osd, 1.0, 0.1)
+    g = mlp.flatten_per_species(mlp.backward_per_species(nets, caches, dU))
+    flat = mlp.flatten_per_species(nets)
+    fd = np.zeros_like(flat)
+    for i in range(flat.size):
+        e = np.zeros_like(flat)
+        e[i] = 1e-6
+        fd[i] = (L(flat + e) - L(flat - e)) / 2e-6
+    assert np.allclose(g, fd, rtol=1e-5, atol=1e-9)
