@@ -34,10 +34,10 @@ WORKLOAD = "di_c_30sp_1m"
 DI_RTOL = 1e-9           # library defaults (rtol 1e-9, atol_Y 1e-18, Newton 0.1): what the parity tests validate
 MECH_DIR = os.path.join(tempfile.gettempdir(), "chem_bench_mech")
 EXP_FLOPS = 20           # flop convention for exp/log/log10/pow in the algorithmic count
-# DRAM bytes of one di_kernel launch per cell, from the 8,192-cell ncu capture of the current
-# kernel (dram__bytes_read.sum + dram__bytes_write.sum = 2,909,696 + 0 B; the written state
+# DRAM bytes of one di_kernel launch per cell, from an 8,202-cell ncu capture of the current
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum = 2,979,840 + 0 B; the written state
 # stayed in L2 there), scaled to a launch by the cells processed
-DI_DRAM_BYTES_PER_CELL = 2909696 / 8192
+DI_DRAM_BYTES_PER_CELL = 2979840 / 8202
 
 
 # ------------------------------------------------------------------------------------------
@@ -298,7 +298,39 @@ def run_ann(args, m, gm, di_rate):
     roof = {"bound": "tensor", "achieved": mlp_tf, "peak": 1937.2, "unit": "TFLOP/s", "frac": mlp_tf / 1937.2,
             "traffic": None, "kernel": "gemm_bf16_kernel (MLP forward, 2 M cells)",
             "peak_source": "MEASURED_PEAKS bf16_tflops (burst)"}
+    report["per_species_mlp"] = run_per_species_forward(gm, ann, X, Uo, mlp_tf)
     return {"report": report, "roofline": roof, "ann": ann}
+
+
+def run_per_species_forward(gm, ann, X, Uo, multi_tflops):
+    """Forward cost of one 1600-800-400 network per species (Sec. 2.2) on the same features:
+    grouped tensor-core GEMMs, one launch per layer for all species (random weights: the cost
+    does not depend on them; accuracy of trained per-species networks is measured offline)."""
+    import torch
+    from paper_2402_18858_gb300 import chem, train as tr
+    ps = chem.chem_ann_create_per_species(gm, tr.HIDDEN_30, seed=2)
+    chem.chem_ann_set_norm(ps, chem.chem_ann_get_norm(ann))
+    n = min(X.shape[0], 262_144)
+    ws = torch.empty(chem.chem_ann_workspace_bytes(ps, n), dtype=torch.uint8, device=X.device)
+    s = torch.cuda.current_stream()
+    chem.chem_ann_forward(ps, X[:n], Uo[:n], ws)
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        chem.chem_ann_forward(ps, X[:n], Uo[:n], ws)
+        e1.record(s)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    if chem.chem_ann_error(ps) != 0:
+        raise RuntimeError("tensor-core pipeline timed out in the per-species forward")
+    fpc = ps.groups * mlp_flops_per_cell(ps.dims)
+    tf = fpc * n / (best * 1e-3) / 1e12
+    multi = mlp_flops_per_cell(ann.dims)
+    return {"workload": f"{ps.groups} networks {ps.dims}, BF16 tcgen05 grouped GEMMs, {n} cells",
+            "cells": n, "ms": best, "cells_per_s": n / (best * 1e-3), "flops_per_cell": fpc,
+            "flops_vs_multi_output": fpc / multi, "tflops": tf, "frac_of_bf16_peak": tf / 1937.2,
+            "time_vs_multi_output": (fpc / multi) * multi_tflops / tf}
 
 
 # ------------------------------------------------------------------------------------------

@@ -153,6 +153,20 @@ typedef struct chem_ann_s* chem_ann;
  * multiples of 8 are stored rounded up with zero-weight units that stay zero, so chem_ann_info
  * reports the stored widths), weights N(0, 2/fan_in), zero biases, seeded. */
 int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t seed, chem_ann* out);
+/* One network per species (Sec. 2.2: each species' transformed mass fraction is trained and
+ * predicted by its own MLP, hidden widths 1600, 800, 400): K networks of the given hidden
+ * widths with one output each, sharing the input x.  Their weights are stored stacked by
+ * species (layer l: W [K dims[l+1], dims[l]], species k in rows k dims[l+1] ..), the first
+ * layer runs as one GEMM over all species' units and every later layer as one launch of K
+ * GEMMs; outputs, normalisation, checks, training options and the rest of the API are those
+ * of chem_ann_create's network, and the loss of Eq. 11 sums over the species as for it (with
+ * w_mass = w_hrr = 0 training the K networks jointly equals training each one alone).
+ * chem_ann_info reports the widths of one species' network (output width 1). */
+int chem_ann_create_per_species(chem_mech mech, const int* hidden, int n_hidden, uint64_t seed,
+                                chem_ann* out);
+/* groups: 1 for chem_ann_create's network, K for per-species networks; n_out_pad: columns of
+ * the output rows U (32 or 64). */
+int chem_ann_layout(chem_ann ann, int* groups, int* n_out_pad);
 void chem_ann_free(chem_ann ann);
 int chem_ann_info(chem_ann ann, int* n_in, int* n_out, int* n_layers, int* dims /* [n_layers+1] */,
                   int64_t* n_params);
@@ -200,7 +214,8 @@ int chem_ann_hrr_coeffs(chem_ann ann, int64_t n, int64_t ld, const double* T0, c
 int chem_ann_train_step(chem_ann ann, const void* X, const float* Ut, const float* bcty,
                         const float* hrr_c, const float* hrr_r, int64_t B,
                         const chem_train_opts* opts, float* loss_out, chem_stream stream);
-/* Flat FP32 parameters (which = 0) or last gradients (which = 1), per layer W [out, in] then b. */
+/* Flat FP32 parameters (which = 0) or last gradients (which = 1), per layer W [out, in] then b
+ * (per-species networks: W [K out, in] and b [K out], stacked by species). */
 int chem_ann_get_params(chem_ann ann, int which, float* host, int64_t count);
 int chem_ann_set_params(chem_ann ann, const float* host, int64_t count);
 /* Checkpoint (weights, normalisation, Adam step and, if with_moments, the Adam moments; a
@@ -358,6 +373,20 @@ int chem_selftest_log(chem_mech mech, int64_t n, const double* x, double* y, che
  * non-zero site code if a pipeline wait timed out.  Device pointers. */
 int chem_selftest_gemm(int epi, int M, int N, int K, const void* A, const void* B, const float* bias,
                        const void* z, void* out, int* err, chem_stream stream);
+
+/* Testing hook: G GEMMs of the per-species layers in one launch, for g = 0..G-1:
+ * out_g = epi(A_g B_g^T) with A_g [M, K] the block of A (row stride lda) starting at row
+ * g a_row, column g a_col, B_g [N, K] the block of B (row stride ldb) starting at row g b_row,
+ * column g b_col, out_g at out + g out_goff (row stride ldo), bias_g at bias + g bias_goff, z_g
+ * at z + g z_goff (row stride ldz); epilogues as chem_selftest_gemm.  A's extent is
+ * [M + (G-1) a_row, K + (G-1) a_col], B's [N + (G-1) b_row, K + (G-1) b_col]; entries of A past
+ * a group's K inside that extent must be finite (they meet B's zero fill).  Column offsets
+ * and strides multiples of 8, pointers 16-byte aligned.  Device pointers. */
+int chem_selftest_gemm_grouped(int epi, int G, int M, int N, int K, const void* A, int64_t lda, int a_row,
+                               int a_col, const void* B, int64_t ldb, int b_row, int b_col,
+                               const float* bias, int bias_goff, const void* z, int64_t ldz,
+                               int64_t z_goff, void* out, int64_t ldo, int64_t out_goff, int* err,
+                               chem_stream stream);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* chem_last_error(void);

@@ -71,6 +71,8 @@ def lib(auto_build: bool = False):
         L.chem_selftest_exp.argtypes = [vp, i64, vp, vp, vp]
         L.chem_selftest_log.argtypes = [vp, i64, vp, vp, vp]
         L.chem_selftest_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.chem_selftest_gemm_grouped.argtypes = [i32, i32, i32, i32, i32, vp, i64, i32, i32, vp, i64, i32, i32,
+                                                 vp, i32, vp, i64, i64, vp, i64, i64, vp, vp]
         _lib = L
         return L
 
@@ -254,6 +256,21 @@ def chem_selftest_gemm(epi: int, A, B, out, bias=None, z=None, err=None, stream=
     return err
 
 
+def chem_selftest_gemm_grouped(epi: int, G: int, M: int, N: int, K: int, A, a_off, B, b_off, out, ldo: int,
+                               out_goff: int, bias=None, bias_goff: int = 0, z=None, ldz: int = 0,
+                               z_goff: int = 0, err=None, stream=None) -> None:
+    """G GEMMs in one launch (see include/chem.h); a_off = (a_row, a_col), b_off = (b_row, b_col)."""
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib().chem_selftest_gemm_grouped(int(epi), int(G), int(M), int(N), int(K), _ptr(A, torch.bfloat16),
+                                            A.stride(0), int(a_off[0]), int(a_off[1]), _ptr(B, torch.bfloat16),
+                                            B.stride(0), int(b_off[0]), int(b_off[1]), _ptr(bias, torch.float32),
+                                            int(bias_goff), _ptr(z, torch.bfloat16), int(ldz), int(z_goff),
+                                            _ptr(out), int(ldo), int(out_goff), _ptr(err, torch.int32),
+                                            _stream(stream)))
+    return err
+
+
 # ------------------------------------------------------------------------------------------
 # learned reaction step
 # ------------------------------------------------------------------------------------------
@@ -278,6 +295,8 @@ def _ann_sigs():
     L = lib()
     vp, i64, i32, fp = C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_float)
     L.chem_ann_create.argtypes = [vp, C.POINTER(i32), i32, C.c_uint64, C.POINTER(vp)]
+    L.chem_ann_create_per_species.argtypes = [vp, C.POINTER(i32), i32, C.c_uint64, C.POINTER(vp)]
+    L.chem_ann_layout.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
     L.chem_ann_free.argtypes = [vp]
     L.chem_ann_free.restype = None
     L.chem_ann_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
@@ -316,7 +335,10 @@ class Ann:
                                    C.byref(npar)))
         self.n_in, self.n_out, self.L = n_in.value, n_out.value, nl.value
         self.dims = [dims[i] for i in range(self.L + 1)]
-        self.n_out_pad = self.dims[-1]
+        groups, n_out_pad = C.c_int(), C.c_int()
+        _check(lib().chem_ann_layout(self.handle, C.byref(groups), C.byref(n_out_pad)))
+        self.groups = groups.value          # 1: one network; K: one network per species
+        self.n_out_pad = n_out_pad.value
         self.n_params = npar.value
         self.norm_size = 4 * self.n_in + 2 * self.n_out
 
@@ -334,6 +356,15 @@ def chem_ann_create(m: Mech, hidden, seed: int = 0) -> Ann:
     h = C.c_void_p()
     arr = (C.c_int * len(hidden))(*hidden)
     _check(lib().chem_ann_create(m.handle, arr, len(hidden), int(seed), C.byref(h)))
+    return Ann(h.value, m)
+
+
+def chem_ann_create_per_species(m: Mech, hidden, seed: int = 0) -> Ann:
+    """One network of the given hidden widths per species (output width 1 each)."""
+    _ann_sigs()
+    h = C.c_void_p()
+    arr = (C.c_int * len(hidden))(*hidden)
+    _check(lib().chem_ann_create_per_species(m.handle, arr, len(hidden), int(seed), C.byref(h)))
     return Ann(h.value, m)
 
 

@@ -53,6 +53,10 @@ struct chem_ann_s {
   chem_mech_s* mech = nullptr;
   DevMech dm{};
   int K = 0, n_in = 0, n_out = 0, n_out_pad = 0, L = 0;
+  // groups = 1: one network with K outputs.  groups = K: one network per species (Sec. 2.2),
+  // all sharing the input; dims[] are then the widths of one species' network (output 1) and
+  // every layer stores the K networks' weights stacked by species, W_l [K dims[l+1], dims[l]]
+  int groups = 1;
   int dims[kMaxLayers + 1] = {0};
   int64_t n_params = 0;        // including padding
   void* dmem = nullptr;        // all parameter-sized device memory
@@ -472,18 +476,28 @@ __global__ void transpose_kernel(const bf16* in, int64_t R, int64_t C, bf16* out
   }
 }
 
-// column sums of a BF16 [B, N] matrix (bias gradients), one thread per column, fixed order
-__global__ void colsum_kernel(const bf16* dZ, int64_t B, int N, float* out) {
+// column sums of the first N columns of a BF16 [B, ld] matrix (bias gradients), one thread per
+// column, fixed order
+__global__ void colsum_kernel(const bf16* dZ, int64_t B, int N, int ld, float* out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
   float s = 0.0f;
-  for (int64_t b = 0; b < B; ++b) s += __bfloat162float(dZ[b * N + c]);
+  for (int64_t b = 0; b < B; ++b) s += __bfloat162float(dZ[b * ld + c]);
   out[c] = s;
 }
 
+// position in the per-group transposes W^T [groups cols, ldt] of element i of W [groups gh, cols]
+// (one group: the plain transpose [cols, rows])
+__device__ __forceinline__ int64_t wt_index(int64_t i, int gh, int ldt, int cols) {
+  const int64_t r = i / cols;
+  const int c = (int)(i - r * cols);
+  const int64_t g = r / gh;
+  return (g * cols + c) * ldt + (r - g * gh);
+}
+
 // Adam (Kingma & Ba 2015) on FP32 masters; refreshes the BF16 copy and its transpose
-__global__ void adam_kernel(int64_t n, int rows, int cols, float* w, const float* g, float* mom, float* vel, float lr,
-                            float b1, float b2, float eps, float bc1, float bc2, bf16* wb, bf16* wt) {
+__global__ void adam_kernel(int64_t n, int gh, int ldt, int cols, float* w, const float* g, float* mom, float* vel,
+                            float lr, float b1, float b2, float eps, float bc1, float bc2, bf16* wb, bf16* wt) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * mom[i] + (1.0f - b1) * gi;
@@ -495,18 +509,16 @@ __global__ void adam_kernel(int64_t n, int rows, int cols, float* w, const float
     if (wb) {
       const bf16 q = __float2bfloat16_rn(wi);
       wb[i] = q;
-      const int r = (int)(i / cols), c = (int)(i % cols);
-      wt[(int64_t)c * rows + r] = q;
+      wt[wt_index(i, gh, ldt, cols)] = q;
     }
   }
 }
 
-__global__ void to_bf16_kernel(int64_t n, int rows, int cols, const float* w, bf16* wb, bf16* wt) {
+__global__ void to_bf16_kernel(int64_t n, int gh, int ldt, int cols, const float* w, bf16* wb, bf16* wt) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const bf16 q = __float2bfloat16_rn(w[i]);
     wb[i] = q;
-    const int r = (int)(i / cols), c = (int)(i % cols);
-    wt[(int64_t)c * rows + r] = q;
+    wt[wt_index(i, gh, ldt, cols)] = q;
   }
 }
 
@@ -542,6 +554,12 @@ int check_ann(chem_ann a) {
 }
 
 
+// parameter rows of layer l (all groups) and the width of its output activations
+int rows_of(const chem_ann_s* a, int l) { return a->groups * a->dims[l + 1]; }
+int width_of(const chem_ann_s* a, int l) { return l == a->L - 1 ? a->n_out_pad : rows_of(a, l); }
+// row length of the per-group transposed weights W_l^T [groups dims[l], ldt]
+int ldt_of(const chem_ann_s* a, int l) { return (a->dims[l + 1] + 7) & ~7; }
+
 // training scratch for a batch of B rows
 struct TrainBufs {
   bf16 *Z[kMaxLayers], *A[kMaxLayers], *AT[kMaxLayers], *dZ[kMaxLayers], *dZT[kMaxLayers];
@@ -551,7 +569,7 @@ struct TrainBufs {
 size_t train_bytes(const chem_ann_s* a, int64_t B) {
   size_t s = 0;
   for (int l = 0; l < a->L; ++l) {
-    const size_t w = (size_t)a->dims[l + 1];
+    const size_t w = (size_t)width_of(a, l);
     s += 5 * B * w * 2 + 5 * 256;       // Z, A, AT, dZ, dZT
   }
   s += (size_t)B * kInPad * 2 + 256;   // XT
@@ -564,9 +582,8 @@ size_t train_bytes(const chem_ann_s* a, int64_t B) {
 // ------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------
-extern "C" {
-
-int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t seed, chem_ann* out) {
+static int ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t seed, bool per_species,
+                      chem_ann* out) {
   if (!mech || !hidden || n_hidden < 1 || n_hidden > kMaxLayers - 1 || !out)
     return set_error(CHEM_E_ARG, "chem_ann_create: bad arguments");
   *out = nullptr;
@@ -578,6 +595,7 @@ int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t se
   if (a->n_in > kInPad) { delete a; return set_error(CHEM_E_UNSUPPORTED, "chem_ann_create: more than 62 species"); }
   a->n_out = a->K;
   a->n_out_pad = a->K <= 32 ? 32 : 64;
+  a->groups = per_species ? a->K : 1;
   a->L = n_hidden + 1;
   a->dims[0] = kInPad;
   // hidden widths are stored rounded up to a multiple of 8 (16-byte rows for the TMA loads);
@@ -593,8 +611,9 @@ int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t se
     a->dims[l + 1] = (hidden[l] + 7) & ~7;
     real[l + 1] = hidden[l];
   }
-  real[a->L] = a->n_out;
-  a->dims[a->L] = a->n_out_pad;
+  real[a->L] = per_species ? 1 : a->n_out;
+  a->dims[a->L] = per_species ? 1 : a->n_out_pad;
+
   int rc = cuda_check(cudaGetDevice(&a->device), "cudaGetDevice");
   if (rc) { delete a; return rc; }
   // parameter-sized memory: masters, grads, Adam m/v (FP32) and BF16 W, W^T per layer
@@ -602,10 +621,10 @@ int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t se
   std::vector<size_t> off;
   auto take = [&](size_t bytes) { off.push_back(total); total += (bytes + 255) & ~size_t(255); };
   for (int l = 0; l < a->L; ++l) {
-    const size_t nw = (size_t)a->dims[l + 1] * a->dims[l], nb = a->dims[l + 1];
+    const size_t nw = (size_t)rows_of(a, l) * a->dims[l], nb = rows_of(a, l);
     for (int t = 0; t < 4; ++t) { take(nw * 4); take(nb * 4); }   // master, grad, m, v
     take(nw * 2);
-    take(nw * 2);
+    take((size_t)a->groups * a->dims[l] * ldt_of(a, l) * 2);
     a->n_params += (int64_t)(nw + nb);
   }
   take((size_t)(4 * a->n_in + 2 * a->n_out) * 4);   // normalisation
@@ -629,18 +648,20 @@ int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t se
   a->norm = (float*)(b + off[q++]);
   a->err = (int*)(b + off[q++]);
   a->loss_part = (float*)(b + off[q++]);
-  // initial weights: N(0, 2/fan_in) on the real (unpadded) inputs, units and outputs, zero
-  // biases and zero padding
+  // initial weights: N(0, 2/fan_in) on the real (unpadded) inputs, units and outputs of every
+  // group, zero biases and zero padding
   uint64_t st = seed * 0x9E3779B97F4A7C15ull + 12345;
   for (int l = 0; l < a->L; ++l) {
-    const int rows = a->dims[l + 1], cols = a->dims[l];
+    const int gh = a->dims[l + 1], rows = rows_of(a, l), cols = a->dims[l];
     const int real_cols = real[l], real_rows = real[l + 1];
     std::vector<float> w((size_t)rows * cols, 0.0f);
     const double sd = std::sqrt(2.0 / real_cols) * (l == a->L - 1 ? 0.5 : 1.0);
-    for (int r = 0; r < real_rows; ++r)
-      for (int c = 0; c < real_cols; ++c) w[(size_t)r * cols + c] = (float)(sd * normal01(st));
+    for (int g = 0; g < a->groups; ++g)
+      for (int r = 0; r < real_rows; ++r)
+        for (int c = 0; c < real_cols; ++c) w[((size_t)g * gh + r) * cols + c] = (float)(sd * normal01(st));
     cudaMemcpy(a->Wm[l], w.data(), w.size() * 4, cudaMemcpyHostToDevice);
-    to_bf16_kernel<<<grid_for((int64_t)w.size(), 256), 256>>>((int64_t)w.size(), rows, cols, a->Wm[l], a->W[l], a->WT[l]);
+    to_bf16_kernel<<<grid_for((int64_t)w.size(), 256), 256>>>((int64_t)w.size(), gh, ldt_of(a, l), cols, a->Wm[l],
+                                                             a->W[l], a->WT[l]);
   }
   // identity normalisation until chem_ann_set_norm / chem_ann_fit_norm
   a->hnorm.assign((size_t)4 * a->n_in + 2 * a->n_out, 0.0f);
@@ -657,6 +678,23 @@ int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t se
     return rc;
   }
   *out = a;
+  return CHEM_OK;
+}
+
+extern "C" {
+
+int chem_ann_create(chem_mech mech, const int* hidden, int n_hidden, uint64_t seed, chem_ann* out) {
+  return ann_create(mech, hidden, n_hidden, seed, false, out);
+}
+
+int chem_ann_create_per_species(chem_mech mech, const int* hidden, int n_hidden, uint64_t seed, chem_ann* out) {
+  return ann_create(mech, hidden, n_hidden, seed, true, out);
+}
+
+int chem_ann_layout(chem_ann a, int* groups, int* n_out_pad) {
+  if (!a) return set_error(CHEM_E_ARG, "null ANN handle");
+  if (groups) *groups = a->groups;
+  if (n_out_pad) *n_out_pad = a->n_out_pad;
   return CHEM_OK;
 }
 
@@ -777,36 +815,52 @@ int chem_ann_hrr_coeffs(chem_ann a, int64_t n, int64_t ld, const double* T0, con
 }
 
 // forward pass over rows [0, M) of X (BF16 [M, 64]) into U (FP32 [M, n_out_pad]), through
-// BF16 activation buffers act[l] ([M, dims[l+1]]); optionally keeping pre-activations zs[l]
+// BF16 activation buffers act[l] ([M, width_of(l)]); optionally keeping pre-activations zs[l].
+// Per-species networks: the first layer is one GEMM over all species' units (shared input),
+// every later layer one launch of `groups` GEMMs, species g reading its own slice of the
+// previous activations and writing its own slice (the output layer: column g of U).
 static int forward_rows(chem_ann a, const bf16* X, int64_t M, bf16* const* act, bf16* const* zs, float* U,
                         cudaStream_t s) {
   int rc;
   const bf16* in = X;
   int64_t ld_in = kInPad;
   for (int l = 0; l < a->L; ++l) {
-    const int N = a->dims[l + 1], Kd = a->dims[l];
+    const int Kd = a->dims[l];
+    const bool grouped = a->groups > 1 && l > 0;
+    const int N = grouped ? a->dims[l + 1] : rows_of(a, l);
     GemmEpi e{};
     e.bias = a->bm[l];
-    if (l < a->L - 1) {
-      e.out = act[l];
-      e.ldo = N;
-      e.zout = zs ? zs[l] : nullptr;
-      if ((rc = gemm_bf16(0, in, ld_in, a->W[l], Kd, (int)M, N, Kd, e, a->err, s))) return rc;
-      in = act[l];
-      ld_in = N;
-    } else {
-      e.out = U;
-      e.ldo = N;
-      if ((rc = gemm_bf16(1, in, ld_in, a->W[l], Kd, (int)M, N, Kd, e, a->err, s))) return rc;
+    if (grouped) {
+      e.groups = a->groups;
+      e.a_col = Kd;
+      e.b_row = N;
+      e.out_goff = N;
+      e.bias_goff = N;
     }
+    const bool last = l == a->L - 1;
+    // the per-species output layer writes columns 0..K-1 of U; the padding columns read zero,
+    // as the one-network output layer's zero padding rows give
+    if (last && grouped &&
+        (rc = cuda_check(cudaMemsetAsync(U, 0, (size_t)M * a->n_out_pad * sizeof(float), s), "U padding")))
+      return rc;
+    e.out = last ? (void*)U : (void*)act[l];
+    e.ldo = width_of(a, l);
+    e.zout = (!last && zs) ? zs[l] : nullptr;
+    if ((rc = gemm_bf16(last ? 1 : 0, in, ld_in, a->W[l], Kd, (int)M, N, Kd, e, a->err, s))) return rc;
+    in = act[l];
+    ld_in = width_of(a, l);
   }
   return CHEM_OK;
 }
 
-// rows of the activation chunk used by inference (keeps a chunk's activations in L2)
+// rows of the activation chunk used by inference: 32768 for one network; for per-species
+// networks as many as keep the widest activation chunk near 400 MB
 static int64_t infer_chunk(const chem_ann_s* a) {
-  (void)a;
-  return 32768;
+  if (a->groups == 1) return 32768;
+  int wmax = 1;
+  for (int l = 0; l < a->L - 1; ++l) wmax = std::max(wmax, width_of(a, l));
+  const int64_t rows = ((int64_t)400 * 1024 * 1024 / (2 * (int64_t)wmax)) & ~(int64_t)127;
+  return std::min<int64_t>(32768, std::max<int64_t>(128, rows));
 }
 
 size_t chem_ann_workspace_bytes(chem_ann a, int64_t n) {
@@ -815,7 +869,7 @@ size_t chem_ann_workspace_bytes(chem_ann a, int64_t n) {
   size_t s = 0;
   s += (size_t)n * kInPad * 2 + 256;                 // X
   s += (size_t)n * a->n_out_pad * 4 + 256;           // U
-  for (int l = 0; l < a->L - 1; ++l) s += (size_t)mc * a->dims[l + 1] * 2 + 256;
+  for (int l = 0; l < a->L - 1; ++l) s += (size_t)mc * width_of(a, l) * 2 + 256;
   s += 4 * ((size_t)n * 4 + 256);                     // flags, slots, cell columns, DI slot status
   s += ((size_t)(n / kCompactBlock + 2) * 4 + 256) + 256 + 256;   // block counts, total, queue
   return s;
@@ -835,7 +889,7 @@ int chem_ann_forward(chem_ann a, const void* X, int64_t n, float* U, void* works
   size_t o = (size_t)n * kInPad * 2 + 256 + (size_t)n * a->n_out_pad * 4 + 256;
   for (int l = 0; l < a->L - 1; ++l) {
     act[l] = (bf16*)(w + ((o + 255) & ~size_t(255)));
-    o = ((o + 255) & ~size_t(255)) + (size_t)mc * a->dims[l + 1] * 2;
+    o = ((o + 255) & ~size_t(255)) + (size_t)mc * width_of(a, l) * 2;
   }
   for (int64_t r0 = 0; r0 < n; r0 += mc) {
     const int64_t m = std::min(mc, n - r0);
@@ -884,7 +938,7 @@ int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, 
   bf16* act[kMaxLayers];
   for (int l = 0; l < a->L - 1; ++l) {
     act[l] = (bf16*)(w + off);
-    off = al(off + (size_t)mc * a->dims[l + 1] * 2);
+    off = al(off + (size_t)mc * width_of(a, l) * 2);
   }
   int32_t* flags = (int32_t*)(w + off);
   off = al(off + (size_t)n * 4);
@@ -954,7 +1008,7 @@ int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float
   size_t off = 0;
   auto take = [&](size_t bytes) { void* p = w + off; off = (off + bytes + 255) & ~size_t(255); return p; };
   for (int l = 0; l < a->L; ++l) {
-    const size_t n = (size_t)B * a->dims[l + 1];
+    const size_t n = (size_t)B * width_of(a, l);
     t.Z[l] = (bf16*)take(n * 2);
     t.A[l] = (bf16*)take(n * 2);
     t.AT[l] = (bf16*)take(n * 2);
@@ -978,34 +1032,63 @@ int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float
     loss_final_kernel<<<1, 32, 0, s>>>(nbl, a->loss_part, opts->w_data, opts->w_mass, opts->w_hrr, loss_out);
   // backward
   dim3 tb(32, 8);
+  const int G = a->groups;
   for (int l = Lo; l >= 0; --l) {
-    const int N = a->dims[l + 1], Kd = a->dims[l];
-    // input activations of layer l, transposed: [Kd, B]
+    const int Kd = a->dims[l], wl = width_of(a, l);
+    const bool grouped = G > 1 && l > 0;
+    const int Ng = a->dims[l + 1];
+    // input activations of layer l, transposed: [width, B]
     const bf16* inT;
     if (l == 0) {
       transpose_kernel<<<dim3((kInPad + 31) / 32, (unsigned)((B + 31) / 32)), tb, 0, s>>>(X, B, kInPad, XT);
       inT = XT;
     } else {
-      transpose_kernel<<<dim3((unsigned)((Kd + 31) / 32), (unsigned)((B + 31) / 32)), tb, 0, s>>>(t.A[l - 1], B, Kd,
-                                                                                                  t.AT[l - 1]);
+      const int win = width_of(a, l - 1);
+      transpose_kernel<<<dim3((unsigned)((win + 31) / 32), (unsigned)((B + 31) / 32)), tb, 0, s>>>(t.A[l - 1], B, win,
+                                                                                                   t.AT[l - 1]);
       inT = t.AT[l - 1];
     }
     if (l != Lo)
-      transpose_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)((B + 31) / 32)), tb, 0, s>>>(t.dZ[l], B, N, t.dZT[l]);
-    // dW_l [N, Kd] = dZ_l^T [N, B] (A_{l-1}^T [Kd, B])^T
+      transpose_kernel<<<dim3((unsigned)((wl + 31) / 32), (unsigned)((B + 31) / 32)), tb, 0, s>>>(t.dZ[l], B, wl, t.dZT[l]);
+    // dW_l [rows, Kd] = dZ_l^T [rows, B] (A_{l-1}^T [Kd, B])^T, per species for grouped layers
     GemmEpi e{};
     e.out = a->gW[l];
     e.ldo = Kd;
-    if ((rc = gemm_bf16(3, t.dZT[l], B, inT, B, N, Kd, (int)B, e, a->err, s))) return rc;
-    colsum_kernel<<<(N + 127) / 128, 128, 0, s>>>(t.dZ[l], B, N, a->gb[l]);
-    if (l > 0) {
-      // dZ_{l-1} [B, Kd] = (dZ_l [B, N] W_l [N, Kd]) * GELU'(Z_{l-1}); B operand = W_l^T [Kd, N]
+    if (grouped) {
+      e.groups = G;
+      e.a_row = Ng;
+      e.b_row = Kd;
+      e.out_goff = (int64_t)Ng * Kd;
+      if ((rc = gemm_bf16(3, t.dZT[l], B, inT, B, Ng, Kd, (int)B, e, a->err, s))) return rc;
+    } else if ((rc = gemm_bf16(3, t.dZT[l], B, inT, B, rows_of(a, l), Kd, (int)B, e, a->err, s))) {
+      return rc;
+    }
+    colsum_kernel<<<(rows_of(a, l) + 127) / 128, 128, 0, s>>>(t.dZ[l], B, rows_of(a, l), wl, a->gb[l]);
+    if (l == 0) continue;
+    // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1}); B operand = W_l^T
+    const int win = width_of(a, l - 1);
+    if (!grouped) {
       GemmEpi e2{};
       e2.out = t.dZ[l - 1];
       e2.ldo = Kd;
       e2.z = t.Z[l - 1];
       e2.ldz = Kd;
-      if ((rc = gemm_bf16(2, t.dZ[l], N, a->WT[l], N, (int)B, Kd, N, e2, a->err, s))) return rc;
+      if ((rc = gemm_bf16(2, t.dZ[l], wl, a->WT[l], ldt_of(a, l), (int)B, Kd, rows_of(a, l), e2, a->err, s))) return rc;
+    } else if (l == Lo) {
+      // one output per species: dZ_{l-1}[b, g Kd + j] = dU[b, g] W[g, j] GELU'(Z)
+      if ((rc = launch_group_out_dgrad(t.dZ[l], wl, a->W[l], t.Z[l - 1], B, G, Kd, t.dZ[l - 1], s))) return rc;
+    } else {
+      GemmEpi e2{};
+      e2.out = t.dZ[l - 1];
+      e2.ldo = win;
+      e2.z = t.Z[l - 1];
+      e2.ldz = win;
+      e2.groups = G;
+      e2.a_col = Ng;
+      e2.b_row = Kd;
+      e2.out_goff = Kd;
+      e2.z_goff = Kd;
+      if ((rc = gemm_bf16(2, t.dZ[l], wl, a->WT[l], ldt_of(a, l), (int)B, Kd, Ng, e2, a->err, s))) return rc;
     }
   }
   if ((rc = cuda_check(cudaGetLastError(), "training launches"))) return rc;
@@ -1014,17 +1097,19 @@ int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float
   a->step++;
   const float bc1 = 1.0f - std::pow(opts->beta1, (float)a->step), bc2 = 1.0f - std::pow(opts->beta2, (float)a->step);
   for (int l = 0; l < a->L; ++l) {
-    const int rows = a->dims[l + 1], cols = a->dims[l];
+    const int rows = rows_of(a, l), cols = a->dims[l];
     const int64_t nw = (int64_t)rows * cols;
-    adam_kernel<<<grid_for(nw, 256), 256, 0, s>>>(nw, rows, cols, a->Wm[l], a->gW[l], a->mW[l], a->vW[l], opts->lr,
-                                                   opts->beta1, opts->beta2, opts->eps, bc1, bc2, a->W[l], a->WT[l]);
-    adam_kernel<<<grid_for(rows, 256), 256, 0, s>>>(rows, rows, 1, a->bm[l], a->gb[l], a->mb[l], a->vb[l], opts->lr,
+    adam_kernel<<<grid_for(nw, 256), 256, 0, s>>>(nw, a->dims[l + 1], ldt_of(a, l), cols, a->Wm[l], a->gW[l], a->mW[l],
+                                                   a->vW[l], opts->lr, opts->beta1, opts->beta2, opts->eps, bc1, bc2,
+                                                   a->W[l], a->WT[l]);
+    adam_kernel<<<grid_for(rows, 256), 256, 0, s>>>(rows, 1, 1, 1, a->bm[l], a->gb[l], a->mb[l], a->vb[l], opts->lr,
                                                     opts->beta1, opts->beta2, opts->eps, bc1, bc2, nullptr, nullptr);
   }
   return cuda_check(cudaGetLastError(), "adam launch");
 }
 
-// parameters/gradients as one flat FP32 host array: per layer W [dims[l+1], dims[l]] then b
+// parameters/gradients as one flat FP32 host array: per layer W [rows, dims[l]] then b [rows]
+// (rows = groups dims[l+1], per-species networks stacked by species)
 int chem_ann_get_params(chem_ann a, int which, float* host, int64_t count) {
   int rc = check_ann(a);
   if (rc) return rc;
@@ -1032,7 +1117,7 @@ int chem_ann_get_params(chem_ann a, int which, float* host, int64_t count) {
   cudaDeviceSynchronize();
   float* p = host;
   for (int l = 0; l < a->L; ++l) {
-    const size_t nw = (size_t)a->dims[l + 1] * a->dims[l], nb = a->dims[l + 1];
+    const size_t nw = (size_t)rows_of(a, l) * a->dims[l], nb = rows_of(a, l);
     if ((rc = cuda_check(cudaMemcpy(p, which ? a->gW[l] : a->Wm[l], nw * 4, cudaMemcpyDeviceToHost), "get params"))) return rc;
     p += nw;
     if ((rc = cuda_check(cudaMemcpy(p, which ? a->gb[l] : a->bm[l], nb * 4, cudaMemcpyDeviceToHost), "get params"))) return rc;
@@ -1047,18 +1132,20 @@ int chem_ann_set_params(chem_ann a, const float* host, int64_t count) {
   if (!host || count != a->n_params) return set_error(CHEM_E_ARG, "chem_ann_set_params: bad arguments");
   const float* p = host;
   for (int l = 0; l < a->L; ++l) {
-    const int rows = a->dims[l + 1], cols = a->dims[l];
+    const int rows = rows_of(a, l), cols = a->dims[l];
     const size_t nw = (size_t)rows * cols;
     if ((rc = cuda_check(cudaMemcpy(a->Wm[l], p, nw * 4, cudaMemcpyHostToDevice), "set params"))) return rc;
     p += nw;
     if ((rc = cuda_check(cudaMemcpy(a->bm[l], p, rows * 4, cudaMemcpyHostToDevice), "set params"))) return rc;
     p += rows;
-    to_bf16_kernel<<<grid_for((int64_t)nw, 256), 256>>>((int64_t)nw, rows, cols, a->Wm[l], a->W[l], a->WT[l]);
+    to_bf16_kernel<<<grid_for((int64_t)nw, 256), 256>>>((int64_t)nw, a->dims[l + 1], ldt_of(a, l), cols, a->Wm[l],
+                                                       a->W[l], a->WT[l]);
   }
   return cuda_check(cudaDeviceSynchronize(), "set params");
 }
 
-// checkpoint: header, dims, normalisation, Adam step, then masters and Adam moments
+// checkpoint: header (species, layers, Adam step, normalisation size, flags: bit 0 Adam moments
+// stored, bit 1 per-species networks), dims, normalisation, then masters and Adam moments
 int chem_ann_save(chem_ann a, const char* path, int with_moments) {
   int rc = check_ann(a);
   if (rc) return rc;
@@ -1066,13 +1153,13 @@ int chem_ann_save(chem_ann a, const char* path, int with_moments) {
   if (!f) return set_error(CHEM_E_ARG, "chem_ann_save: cannot open file");
   cudaDeviceSynchronize();
   const char magic[8] = {'C', 'H', 'E', 'M', 'A', 'N', 'N', '2'};
-  int hdr[5] = {a->K, a->L, a->step, (int)a->hnorm.size(), with_moments ? 1 : 0};
+  int hdr[5] = {a->K, a->L, a->step, (int)a->hnorm.size(), (with_moments ? 1 : 0) | (a->groups > 1 ? 2 : 0)};
   std::fwrite(magic, 1, 8, f);
   std::fwrite(hdr, 4, 5, f);
   std::fwrite(a->dims, 4, a->L + 1, f);
   std::fwrite(a->hnorm.data(), 4, a->hnorm.size(), f);
   for (int l = 0; l < a->L; ++l) {
-    const size_t nw = (size_t)a->dims[l + 1] * a->dims[l], nb = a->dims[l + 1];
+    const size_t nw = (size_t)rows_of(a, l) * a->dims[l], nb = rows_of(a, l);
     const float* parts[6] = {a->Wm[l], a->bm[l], a->mW[l], a->mb[l], a->vW[l], a->vb[l]};
     const size_t sizes[6] = {nw, nb, nw, nb, nw, nb};
     for (int q = 0; q < (with_moments ? 6 : 2); ++q) {
@@ -1104,21 +1191,21 @@ int chem_ann_load(chem_mech mech, const char* path, chem_ann* out) {
     return set_error(CHEM_E_PARSE, "chem_ann_load: checkpoint does not match the mechanism");
   }
   chem_ann a = nullptr;
-  int rc = chem_ann_create(mech, dims + 1, hdr[1] - 1, 0, &a);
+  int rc = ann_create(mech, dims + 1, hdr[1] - 1, 0, (hdr[4] & 2) != 0, &a);
   if (rc) { std::fclose(f); return rc; }
   std::vector<float> norm(hdr[3]);
   bool ok = hdr[3] == (int)a->hnorm.size() && std::fread(norm.data(), 4, norm.size(), f) == norm.size();
   for (int l = 0; ok && l < a->L; ++l) {
-    const size_t nw = (size_t)a->dims[l + 1] * a->dims[l], nb = a->dims[l + 1];
+    const size_t nw = (size_t)rows_of(a, l) * a->dims[l], nb = rows_of(a, l);
     float* parts[6] = {a->Wm[l], a->bm[l], a->mW[l], a->mb[l], a->vW[l], a->vb[l]};
     const size_t sizes[6] = {nw, nb, nw, nb, nw, nb};
-    for (int q = 0; ok && q < (hdr[4] ? 6 : 2); ++q) {   // without moments: Adam restarts from zero
+    for (int q = 0; ok && q < ((hdr[4] & 1) ? 6 : 2); ++q) {   // without moments: Adam restarts from zero
       std::vector<float> h(sizes[q]);
       ok = std::fread(h.data(), 4, h.size(), f) == h.size();
       if (ok) cudaMemcpy(parts[q], h.data(), h.size() * 4, cudaMemcpyHostToDevice);
     }
-    const int rows = a->dims[l + 1], cols = a->dims[l];
-    to_bf16_kernel<<<grid_for((int64_t)nw, 256), 256>>>((int64_t)nw, rows, cols, a->Wm[l], a->W[l], a->WT[l]);
+    to_bf16_kernel<<<grid_for((int64_t)nw, 256), 256>>>((int64_t)nw, a->dims[l + 1], ldt_of(a, l), a->dims[l], a->Wm[l],
+                                                       a->W[l], a->WT[l]);
   }
   std::fclose(f);
   if (!ok) { chem_ann_free(a); return set_error(CHEM_E_PARSE, "chem_ann_load: truncated checkpoint"); }

@@ -178,9 +178,21 @@ struct GemmEpi {
   const __nv_bfloat16* z;      // epilogue 2: pre-activations [M, ldz]
   int ldz;
   __nv_bfloat16* zout;         // epilogue 0: optional copy of the pre-activations [M, ldo]
+  // groups > 1: that many independent GEMMs of the same M, N, K in one launch.  Group g reads
+  // its A tiles at coordinates offset by (row g a_row, column g a_col) and its B tiles by
+  // (g b_row, g b_col), and writes out/zout at + g out_goff, reads z at + g z_goff and bias at
+  // + g bias_goff (elements).  Column offsets are multiples of 8 (16-byte TMA coordinates).
+  int groups;
+  int a_row, a_col, b_row, b_col;
+  int64_t out_goff, z_goff;
+  int bias_goff;
 };
 int gemm_bf16(int epi, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int M, int N,
               int K, const GemmEpi& e, int* err, cudaStream_t s);
+// output layer of per-species networks, backward to the last hidden layer: dZ[b, g h + j] =
+// dU[b, g] W[g, j] GELU'(Z[b, g h + j]) (BF16 in and out, FP32 arithmetic)
+int launch_group_out_dgrad(const __nv_bfloat16* dU, int ldu, const __nv_bfloat16* W, const __nv_bfloat16* Z,
+                           int64_t B, int G, int h, __nv_bfloat16* dZ, cudaStream_t s);
 size_t di_smem_per_warp(const DevMech& m);
 
 int launch_exp_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s);

@@ -251,7 +251,9 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_persistent(const __grid_cons
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkb = (K + tc::BK - 1) / tc::BK;
   const int n_tiles = (N + BN - 1) / BN;
-  const int total = n_tiles * ((M + tc::BM - 1) / tc::BM);
+  // tile t: group t / per_group, then row block, then N tile (fastest)
+  const int per_group = n_tiles * ((M + tc::BM - 1) / tc::BM);
+  const int total = per_group * (e.groups > 1 ? e.groups : 1);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -275,14 +277,16 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_persistent(const __grid_cons
       // TMA producer over every K slab of every tile of this CTA
       int g = 0;
       for (int t = blockIdx.x; t < total && !gemm_failed(err); t += gridDim.x) {
-        const int m0 = (t / n_tiles) * tc::BM, n0 = (t % n_tiles) * BN;
+        const int gr = t / per_group, r = t - gr * per_group;
+        const int m0 = (r / n_tiles) * tc::BM, n0 = (r % n_tiles) * BN;
+        const int ax = gr * e.a_col, ay = gr * e.a_row + m0, bx = gr * e.b_col, by = gr * e.b_row + n0;
         bool stop = false;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % S;
           if (g >= S && !tc::mbar_wait(&empty[s], ((g / S) & 1) ^ 1, err, 11)) { stop = true; break; }
           tc::mbar_expect_tx(&full[s], (uint32_t)(C::A_BYTES + C::B_BYTES));
-          tc::tma_load_2d(sA + s * C::A_BYTES, &ta, &full[s], kb * tc::BK, m0);
-          tc::tma_load_2d(sB + s * C::B_BYTES, &tb, &full[s], kb * tc::BK, n0);
+          tc::tma_load_2d(sA + s * C::A_BYTES, &ta, &full[s], ax + kb * tc::BK, ay);
+          tc::tma_load_2d(sB + s * C::B_BYTES, &tb, &full[s], bx + kb * tc::BK, by);
         }
         if (stop) break;
       }
@@ -324,8 +328,17 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_persistent(const __grid_cons
       const int b = it & 1, u = it >> 1;
       if (gemm_failed(err) || !tc::mbar_wait(&accf[b], u & 1, err, 14)) break;
       tc::tc_fence_after();
-      const int m0 = (t / n_tiles) * tc::BM, n0 = (t % n_tiles) * BN;
+      const int gr = t / per_group, r = t - gr * per_group;
+      const int m0 = (r / n_tiles) * tc::BM, n0 = (r % n_tiles) * BN;
       const int row = m0 + quarter * 32 + lane;
+      GemmEpi eg = e;
+      if (gr) {
+        constexpr size_t osz = (EPI == 0 || EPI == 2) ? 2 : 4;
+        eg.out = (char*)e.out + (size_t)gr * (size_t)e.out_goff * osz;
+        if (e.zout) eg.zout = e.zout + (size_t)gr * (size_t)e.out_goff;
+        if (e.z) eg.z = e.z + (size_t)gr * (size_t)e.z_goff;
+        if (e.bias) eg.bias = e.bias + (size_t)gr * (size_t)e.bias_goff;
+      }
       const uint32_t acc = tmem + (uint32_t)b * C::ACC_COLS + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
       for (int c0 = half * 32; c0 < BN; c0 += 64) {
@@ -333,7 +346,7 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_persistent(const __grid_cons
         float v[32];
         tc::tmem_ld32(acc + (uint32_t)c0, v);
         if (row < M)   // no early exit: the next tcgen05.ld needs the whole warp
-          epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), e);
+          epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), eg);
         __syncwarp();
       }
       tc::tc_fence_before();
@@ -388,10 +401,13 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
                          const GemmEpi& e, int* err, cudaStream_t s) {
   CUtensorMap ta, tb;
   int rc;
-  if ((rc = make_map(&ta, A, M, K, lda, tc::BM))) return rc;
-  if ((rc = make_map(&tb, B, N, K, ldb, BN))) return rc;
+  const int G = e.groups > 1 ? e.groups : 1;
+  // the maps span every group's operand; a K slab that runs past a group's K reads the next
+  // group's A columns, multiplied by the zeros that B's map supplies past its K extent
+  if ((rc = make_map(&ta, A, M + (int64_t)(G - 1) * e.a_row, K + (int64_t)(G - 1) * e.a_col, lda, tc::BM))) return rc;
+  if ((rc = make_map(&tb, B, N + (int64_t)(G - 1) * e.b_row, K + (int64_t)(G - 1) * e.b_col, ldb, BN))) return rc;
   const int nkb_all = (K + tc::BK - 1) / tc::BK;
-  if (nkb_all > 2) {
+  if (nkb_all > 2 || G > 1) {
     // long K: persistent warp-specialised kernel, one CTA per SM
     using P = PersistCfg<BN>;
     static bool pconfigured = false;
@@ -404,7 +420,7 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
     }
     const int S = nkb_all < P::STAGES ? nkb_all : P::STAGES;
     const size_t smem = 1024 + (size_t)S * (P::A_BYTES + P::B_BYTES) + (2 * (size_t)S + 4) * 8 + 16;
-    const int64_t total = (int64_t)((N + BN - 1) / BN) * ((M + tc::BM - 1) / tc::BM);
+    const int64_t total = (int64_t)((N + BN - 1) / BN) * ((M + tc::BM - 1) / tc::BM) * G;
     if (total > 0x7fffffff) return set_error(CHEM_E_ARG, "gemm: too many tiles in one call");
     static int sms = 0;
     if (!sms) {
@@ -440,6 +456,14 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
 int gemm_bf16(int epi, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int M, int N, int K,
               const GemmEpi& e, int* err, cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return CHEM_OK;
+  if (e.groups > 1) {
+    // TMA column coordinates on 16-byte boundaries; 16-byte vector stores and z loads of
+    // full 32-column chunks at every group's offset
+    const int64_t ov = (epi == 0 || epi == 2) ? 8 : 4;
+    if (e.a_row < 0 || e.b_row < 0 || e.a_col < 0 || e.b_col < 0 || (e.a_col & 7) || (e.b_col & 7) ||
+        e.out_goff < 0 || e.z_goff < 0 || e.bias_goff < 0 || (N >= 32 && (e.out_goff % ov || e.z_goff % 8)))
+      return set_error(CHEM_E_ARG, "gemm: group offsets must be non-negative, column offsets multiples of 8");
+  }
   // tile width: N <= 128 takes the narrowest of 32/64/128 that covers it; wider layers take the
   // tile of at least 128 columns with the least padded width ceil(N / BN) BN, ties to the wider
   // (N = 1600 and 800 take 160, N = 400 and 2000 take 224, N = 1000 and 500 take 256) -- narrow
@@ -474,6 +498,30 @@ int gemm_bf16(int epi, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, i
   return set_error(CHEM_E_ARG, "gemm: unsupported tile");
 }
 
+// output layer of per-species networks, backward: one thread per element of dZ [B, G h]
+__global__ void group_out_dgrad_kernel(const bf16* dU, int ldu, const bf16* W, const bf16* Z, int64_t B, int G, int h,
+                                       bf16* dZ) {
+  const int64_t w = (int64_t)G * h, n = B * w;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / w;
+    const int c = (int)(i - b * w), g = c / h;
+    const float acc = __bfloat162float(dU[b * ldu + g]) * __bfloat162float(W[c]);
+    dZ[i] = __float2bfloat16_rn(acc * dgelu_f(__bfloat162float(Z[i])));
+  }
+}
+
+int launch_group_out_dgrad(const bf16* dU, int ldu, const bf16* W, const bf16* Z, int64_t B, int G, int h, bf16* dZ,
+                           cudaStream_t s) {
+  const int64_t n = B * (int64_t)G * h;
+  if (n <= 0) return CHEM_OK;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 32));
+  group_out_dgrad_kernel<<<grid, 256, 0, s>>>(dU, ldu, W, Z, B, G, h, dZ);
+  return cuda_check(cudaGetLastError(), "group_out_dgrad_kernel launch");
+}
+
 }  // namespace chem
 
 using namespace chem;
@@ -490,4 +538,29 @@ extern "C" int chem_selftest_gemm(int epi, int M, int N, int K, const void* A, c
   e.ldz = N;
   e.zout = nullptr;
   return gemm_bf16(epi, (const bf16*)A, K, (const bf16*)B, K, M, N, K, e, err, (cudaStream_t)stream);
+}
+
+// G GEMMs in one launch with the group offsets of GemmEpi (row strides lda, ldb, ldo, ldz)
+extern "C" int chem_selftest_gemm_grouped(int epi, int G, int M, int N, int K, const void* A, int64_t lda, int a_row,
+                                          int a_col, const void* B, int64_t ldb, int b_row, int b_col,
+                                          const float* bias, int bias_goff, const void* z, int64_t ldz, int64_t z_goff,
+                                          void* out, int64_t ldo, int64_t out_goff, int* err, chem_stream stream) {
+  if (G < 1 || M < 0 || N < 0 || K < 0 || !A || !B || !out || !err || ldo > INT_MAX || ldz > INT_MAX)
+    return set_error(CHEM_E_ARG, "chem_selftest_gemm_grouped: bad arguments");
+  if (epi < 0 || epi > 3 || (epi == 2 && !z)) return set_error(CHEM_E_ARG, "chem_selftest_gemm_grouped: bad epilogue");
+  GemmEpi e{};
+  e.bias = bias;
+  e.out = out;
+  e.ldo = (int)ldo;
+  e.z = (const bf16*)z;
+  e.ldz = (int)ldz;
+  e.groups = G;
+  e.a_row = a_row;
+  e.a_col = a_col;
+  e.b_row = b_row;
+  e.b_col = b_col;
+  e.out_goff = out_goff;
+  e.z_goff = z_goff;
+  e.bias_goff = bias_goff;
+  return gemm_bf16(epi, (const bf16*)A, lda, (const bf16*)B, ldb, M, N, K, e, err, (cudaStream_t)stream);
 }

@@ -3,6 +3,7 @@
     python -m paper_2402_18858_gb300.profile_cases di --cells 8192
     python -m paper_2402_18858_gb300.profile_cases thermo --cells 1048576
     python -m paper_2402_18858_gb300.profile_cases mlp --cells 65536
+    python -m paper_2402_18858_gb300.profile_cases mlp_ps --cells 65536
     python -m paper_2402_18858_gb300.profile_cases rates --cells 65536
     python -m paper_2402_18858_gb300.profile_cases jacobian --cells 8192
     python -m paper_2402_18858_gb300.profile_cases pasr --cells 1048576
@@ -27,7 +28,7 @@ CKPT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models", "ann_c
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["di", "thermo", "mlp", "rates", "jacobian", "pasr"])
+    ap.add_argument("case", choices=["di", "thermo", "mlp", "mlp_ps", "rates", "jacobian", "pasr"])
     ap.add_argument("--cells", type=int, default=8192)
     ap.add_argument("--repeats", type=int, default=2)
     a = ap.parse_args()
@@ -77,6 +78,18 @@ def main():
 
         def run():
             chem.thermo_props(gm, T0, Y0, *outs, mixed_precision=True)
+    elif a.case == "mlp_ps":
+        # one 1600-800-400 network per species (grouped GEMMs), random weights
+        ann0 = chem.chem_ann_load(gm, CKPT)
+        ann = chem.chem_ann_create_per_species(gm, [1600, 800, 400], seed=2)
+        chem.chem_ann_set_norm(ann, chem.chem_ann_get_norm(ann0))
+        X = torch.empty((n, 64), dtype=torch.bfloat16, device=dev)
+        chem.chem_ann_features(ann, T0, p, Y0, X)
+        U = torch.empty((n, ann.n_out_pad), dtype=torch.float32, device=dev)
+        ws = torch.empty(chem.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device=dev)
+
+        def run():
+            chem.chem_ann_forward(ann, X, U, ws)
     else:
         ann = chem.chem_ann_load(gm, CKPT)
         X = torch.empty((n, 64), dtype=torch.bfloat16, device=dev)

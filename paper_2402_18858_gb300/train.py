@@ -221,12 +221,18 @@ def main():
     ap.add_argument("--w-hrr", type=float, default=0.0, help="weight W3 of the heat-release loss term (Eq. 10)")
     ap.add_argument("--hfrd", action="store_true",
                     help="train on states augmented by Eqs. 3-6 (random data method) instead of the plain draws")
+    ap.add_argument("--per-species", action="store_true",
+                    help="one 1600-800-400 network per species (Sec. 2.2) instead of one multi-output network")
+    ap.add_argument("--dT-max", type=float, default=0.0, help="fallback cap on the predicted |dT| (0: none)")
     args = ap.parse_args()
     build.build()
     m = wl.make_mechanism(args.kind, args.mech_seed)
     path = wl.mechanism_file(args.kind, args.mech_seed, os.path.join(tempfile.gettempdir(), "chem_mech"))
     gm = chem.chem_load_mech(path)
-    ann = chem.chem_ann_create(gm, HIDDEN_30 if m.n_species <= 32 else HIDDEN_53, seed=args.seed)
+    if args.per_species:
+        ann = chem.chem_ann_create_per_species(gm, HIDDEN_30, seed=args.seed)
+    else:
+        ann = chem.chem_ann_create(gm, HIDDEN_30 if m.n_species <= 32 else HIDDEN_53, seed=args.seed)
     t0 = time.perf_counter()
     if args.hfrd:
         data = hfrd_states(gm, m, args.train_cells, args.seed, args.dt)
@@ -245,13 +251,13 @@ def main():
         chem.chem_ann_save(ann, args.out, with_moments=args.with_moments)
     del X, bcty, U
     ev = evaluate(gm, ann, di_states(gm, m, args.eval_cells, args.eval_seed, args.dt), args.dt,
-                  repeats=args.repeats, elem_tol=args.elem_tol)
-    out = dict(kind=args.kind, hidden=ann.dims, hfrd=bool(args.hfrd), w_hrr=args.w_hrr,
+                  repeats=args.repeats, elem_tol=args.elem_tol, dT_max=args.dT_max)
+    out = dict(kind=args.kind, hidden=ann.dims, groups=ann.groups, hfrd=bool(args.hfrd), w_hrr=args.w_hrr,
                hrr_scale=hrr[2] if hrr is not None else None, data_generation_s=gen_s,
                di_generation_cells_per_s=args.train_cells / gen_s, train=tr, eval=ev)
     if args.infer_cells > 0:
         out["inference"] = time_inference(gm, m, ann, args.infer_cells, args.eval_seed + 1, args.dt,
-                                          ev["di_cells_per_s"], elem_tol=args.elem_tol)
+                                          ev["di_cells_per_s"], elem_tol=args.elem_tol, dT_max=args.dT_max)
     hist = tr.pop("loss_history", None)
     out["loss_history"] = hist[-20:] if hist else None
     print(json.dumps(out))
