@@ -35,9 +35,9 @@ DI_RTOL = 1e-9           # library defaults (rtol 1e-9, atol_Y 1e-18, Newton 0.1
 MECH_DIR = os.path.join(tempfile.gettempdir(), "chem_bench_mech")
 EXP_FLOPS = 20           # flop convention for exp/log/log10/pow in the algorithmic count
 # DRAM bytes of one di_kernel launch per cell, from an 8,202-cell ncu capture of the current
-# kernel (dram__bytes_read.sum + dram__bytes_write.sum = 2,932,224 + 0 B; the written state
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum = 2,973,440 + 0 B; the written state
 # stayed in L2 there), scaled to a launch by the cells processed
-DI_DRAM_BYTES_PER_CELL = 2932224 / 8202
+DI_DRAM_BYTES_PER_CELL = 2973440 / 8202
 
 
 # ------------------------------------------------------------------------------------------
