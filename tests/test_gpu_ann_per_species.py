@@ -274,3 +274,33 @@ def test_per_species_training_checkpoint_and_step(lc, setup, tmp_path, mechs):
     Yh = Y.cpu().numpy()
     assert np.isfinite(Yh).all() and np.isfinite(T.cpu().numpy()).all()
     assert np.allclose(Yh.sum(axis=0), 1.0, atol=1e-9)
+
+
+def test_per_species_53_species_multi_chunk(lc, mechs):
+    """53 species (64-column output rows, 53 groups) over 40,000 rows: two inference chunks
+    with a ragged second one; sampled rows against the oracle."""
+    m, path = mechs["c_53"]
+    gm = lc.chem_load_mech(path)
+    n = 40_000
+    st = w.make_states(m, n, 66)
+    dev = torch.device("cuda")
+    T = torch.as_tensor(st.T, device=dev)
+    p = torch.as_tensor(st.p, device=dev)
+    Y0 = torch.as_tensor(st.Y, device=dev)
+    Y1 = (Y0 * (1.0 + 0.01 * torch.as_tensor(np.random.default_rng(3).standard_normal(st.Y.shape),
+                                             device=dev))).contiguous()
+    ann = lc.chem_ann_create_per_species(gm, [40, 24, 16], seed=14)
+    assert ann.groups == 53 and ann.n_out_pad == 64
+    lc.chem_ann_fit_norm(ann, T, p, Y0, Y1)
+    X = torch.empty((n, 64), dtype=torch.bfloat16, device=dev)
+    lc.chem_ann_features(ann, T, p, Y0, X)
+    Ug = _forward(lc, ann, X)
+    pick = np.sort(np.random.default_rng(67).choice(n, 300, replace=False))
+    pick[-1] = n - 1
+    nets = mlp.unflatten_per_species(lc.chem_ann_get_params(ann), ann.dims, 53)
+    Xs = X[torch.as_tensor(pick, device=dev)].float().cpu().numpy().astype(np.float64)
+    Uo, _ = mlp.forward_per_species(nets, Xs, bf16=True)
+    d = Ug[torch.as_tensor(pick, device=dev)].cpu().numpy()[:, :53] - Uo
+    assert np.abs(d).max() <= 2e-3 * np.abs(Uo).max() + 1e-3
+    assert np.sqrt((d ** 2).mean()) <= 1e-3 * np.sqrt((Uo ** 2).mean())
+    assert (Ug[:, 53:] == 0).all()
