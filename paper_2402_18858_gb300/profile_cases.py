@@ -1,6 +1,7 @@
 """One kernel case per invocation, for profilers (ncu) and quick timing.
 
     python -m paper_2402_18858_gb300.profile_cases di --cells 8192
+    python -m paper_2402_18858_gb300.profile_cases di --kind c_53 --mech-seed 5 --dt 1e-5 --cells 16384
     python -m paper_2402_18858_gb300.profile_cases thermo --cells 1048576
     python -m paper_2402_18858_gb300.profile_cases mlp --cells 65536
     python -m paper_2402_18858_gb300.profile_cases mlp_ps --cells 65536
@@ -8,8 +9,9 @@
     python -m paper_2402_18858_gb300.profile_cases jacobian --cells 8192
     python -m paper_2402_18858_gb300.profile_cases pasr --cells 1048576
 
-Each case loads the 30-species workload mechanism, builds seeded inputs, runs the operation
-`--repeats` times (the first is the warm-up) and prints the CUDA-event time of the last one.
+Each case loads the 30-species workload mechanism (the DI case any mechanism kind and seed,
+with its own dt), builds seeded inputs, runs the operation `--repeats` times (the first is the
+warm-up) and prints the CUDA-event time of the last one.
 """
 from __future__ import annotations
 
@@ -31,10 +33,16 @@ def main():
     ap.add_argument("case", choices=["di", "thermo", "mlp", "mlp_ps", "rates", "jacobian", "pasr"])
     ap.add_argument("--cells", type=int, default=8192)
     ap.add_argument("--repeats", type=int, default=2)
+    ap.add_argument("--kind", default=MECH[0], help="mechanism kind (the DI case only; default c_30)")
+    ap.add_argument("--mech-seed", type=int, default=MECH[1])
+    ap.add_argument("--dt", type=float, default=5e-6, help="flow step of the DI case (s)")
     a = ap.parse_args()
+    if (a.kind, a.mech_seed) != MECH and a.case != "di":
+        ap.error("--kind/--mech-seed apply to the di case only")
     build.build()
-    m = wl.make_mechanism(*MECH)
-    gm = chem.chem_load_mech(wl.mechanism_file(*MECH, os.path.join(tempfile.gettempdir(), "chem_mech")))
+    mech = (a.kind, a.mech_seed)
+    m = wl.make_mechanism(*mech)
+    gm = chem.chem_load_mech(wl.mechanism_file(*mech, os.path.join(tempfile.gettempdir(), "chem_mech")))
     st = wl.make_states(m, a.cells, 101)
     dev = torch.device("cuda")
     T0 = torch.as_tensor(st.T, device=dev)
@@ -50,7 +58,7 @@ def main():
         def run():
             T.copy_(T0)
             Y.copy_(Y0)
-            chem.chem_step_di(gm, 5e-6, T, p, Y, status, workspace=ws, stats=stats)
+            chem.chem_step_di(gm, a.dt, T, p, Y, status, workspace=ws, stats=stats)
     elif a.case == "rates":
         wdot = torch.empty_like(Y0)
         hrr = torch.empty_like(T0)
@@ -107,7 +115,7 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-    out = {"case": a.case, "cells": n, "ms": ms}
+    out = {"case": a.case, "kind": a.kind, "cells": n, "ms": ms}
     if a.case == "di":
         # per-cell means of the kernel's counters: BDF steps, RHS, Jacobians, LU factorisations
         c = stats.view(4, n).double().mean(dim=1).tolist()
