@@ -126,13 +126,15 @@ size_t chem_workspace_bytes(chem_mech mech, int64_t n);
  * (the cell work-queue counter) lives in a fixed 256-byte device array inside this library,
  * held by every GPU that loads the library until the process exits.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress) in the CUDA
+ *     context current on the calling thread, so a device reset or another context made
+ *     current on the device between calls is followed correctly.
  *   - All calls share the one array: the call clears the counter on `stream` before its
  *     launch, but calls whose work overlaps on the GPU (other streams, other threads) race
  *     on it and must be serialised by the caller.
- *   - Returns CHEM_E_ARG if the call needs more scratch than the array holds (more than
- *     2^31 - 1 cells), otherwise the codes of chem_step_di. */
+ *   - The array always holds the call's scratch; n is limited to 2^31 - 1 cells per call by
+ *     the 32-bit work-queue counter (CHEM_E_ARG beyond), otherwise the codes of
+ *     chem_step_di. */
 int chem_step_di_noalloc(chem_mech mech, int64_t n, int64_t ld, double dt, double* T,
                          const double* p, double* Y, const int32_t* idx,
                          const chem_di_opts* opts, int32_t* status, int32_t* stats,
@@ -177,9 +179,13 @@ int chem_ann_get_norm(chem_ann ann, float* host_norm);
 int chem_ann_fit_norm(chem_ann ann, int64_t n, int64_t ld, const double* T, const double* p,
                       const double* Y0, const double* Y1, chem_stream stream);
 /* Normalised BF16 features X [n, 64]; if bcty is not NULL also the raw F(Y) as FP32 [n, K]
- * (needed by the mass term of the loss). */
+ * (needed by the mass term of the loss).  If flags is not NULL, flags[i] receives the range
+ * flag of the learned step (1 when a raw feature of cell i lies outside [min - m (max - min),
+ * max + m (max - min)] of the training set, m = range_margin >= 0; else 0): the first stage
+ * of chem_step_ann, exposed so that its stages can be run and checked one by one. */
 int chem_ann_features(chem_ann ann, int64_t n, int64_t ld, const double* T, const double* p,
-                      const double* Y, void* X, float* bcty, chem_stream stream);
+                      const double* Y, void* X, float* bcty, double range_margin, int32_t* flags,
+                      chem_stream stream);
 /* Normalised FP32 targets U [n, n_out_pad] from the states before (Y0) and after (Y1) DI. */
 int chem_ann_targets(chem_ann ann, int64_t n, int64_t ld, const double* Y0, const double* Y1,
                      float* U, chem_stream stream);
@@ -246,6 +252,30 @@ int chem_step_ann(chem_mech mech, chem_ann ann, int64_t n, int64_t ld, double dt
                   const double* p, double* Y, const int32_t* idx, const chem_ann_opts* opts,
                   int32_t* status, void* workspace, size_t ws_bytes, chem_stream stream);
 size_t chem_ann_workspace_bytes(chem_ann ann, int64_t n);
+
+/* The update stage of chem_step_ann on given network outputs U [n, n_out_pad] (FP32, rows by
+ * entry of idx or by cell; from chem_ann_forward), in place on T and Y (layout and idx as
+ * chem_step_ann).  The paper defines the output as the change of the Box-Cox transformed
+ * species over dt (Sec. 2.2, Eq. 7); T follows from the adiabatic constant-pressure energy
+ * balance.  Per cell, in FP32:
+ *   1. Y*_k = F^-1(F(Y_k) + sigma_k U_k + mu_k), 0 where the inverse's base is <= 0; a
+ *      non-finite argument or a sum of Y* that is not finite and positive sets bit 2 and
+ *      ends the cell;
+ *   2. Y* /= sum Y*; the largest relative change of element moles over the elements present
+ *      in Y above opts->elem_tol sets bit 4;
+ *   3. without bit 4, Y* is projected onto exact element conservation (the least-squares
+ *      change weighted by 1/Y*_k, clipped at 0);
+ *   4. T' solves h(T', Y*) = h(T, Y) by Newton's method; T' non-finite sets bit 2, else T'
+ *      outside [T_min, T_max] bit 8, else |T' - T| > dT_max (when dT_max > 0) bit 16.
+ * flags (in/out, int32 [n]): on input the range flag (bit 1, e.g. from chem_ann_features;
+ * 0 to skip the range check); a cell with a non-zero input flag is left alone.  On output
+ * the flag word; status[] = 0 for accepted cells (T, Y overwritten) and
+ * CHEM_CELL_ANN_FALLBACK for flagged ones (T, Y unchanged; chem_step_ann then integrates
+ * them by DI).  opts NULL selects the defaults (fields as chem_ann_opts; range_margin, di
+ * and no_fallback are not used here). */
+int chem_ann_update(chem_ann ann, int64_t n, int64_t ld, double* T, const double* p, double* Y,
+                    const float* U, const int32_t* idx, const chem_ann_opts* opts, int32_t* flags,
+                    int32_t* status, chem_stream stream);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Serving loop: continuous batching of chemistry-step requests (the paper keeps fields      */

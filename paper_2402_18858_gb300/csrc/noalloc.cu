@@ -8,39 +8,30 @@
 // fixed file-scope device array, so it allocates nothing.
 //
 // The array is part of this library's device image: every GPU that loads the library holds it
-// until the process exits.  Host code only knows a stand-in for the array's name, so the
-// device address is looked up once per device with cudaGetSymbolAddress (the first call on
-// each device does this set-up, with that device current) and passed to the kernel.
+// until the process exits.  Host code only knows a stand-in for the array's name, so every
+// call looks up the array's device address in the CUDA context current on the calling thread
+// (cudaGetSymbolAddress allocates nothing) and passes it to the kernel.  Looking it up per
+// call, rather than caching it per device ordinal, keeps the address right when the caller
+// resets the device or makes another context current on it: the module is then loaded again
+// and the array may sit at a different address.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "internal.h"
 
 namespace chem {
 
-// Scratch capacity: one 256-byte line, enough for the work-queue counter of any call.
+// Scratch capacity: one 256-byte line.  The call's only scratch is the 4-byte work-queue
+// counter, so the array always suffices; the guard below only protects against a future
+// growth of chem_step_di's workspace.
 constexpr size_t kNoallocScratchBytes = 256;
 static __device__ __align__(256) unsigned int g_noalloc_scratch[kNoallocScratchBytes / sizeof(unsigned int)];
 
-constexpr int kMaxDevices = 64;
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array in the current context.
 static int noalloc_scratch(void** out) {
-  int dev = -1;
-  int rc = cuda_check(cudaGetDevice(&dev), "chem_step_di_noalloc: cudaGetDevice");
+  void* p = nullptr;
+  const int rc = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "chem_step_di_noalloc: cudaGetSymbolAddress");
   if (rc) return rc;
-  if (dev < 0 || dev >= kMaxDevices) return set_error(CHEM_E_ARG, "chem_step_di_noalloc: device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    rc = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "chem_step_di_noalloc: cudaGetSymbolAddress");
-    if (rc) return rc;
-    g_noalloc_addr[dev] = p;
-  }
-  *out = g_noalloc_addr[dev];
+  *out = p;
   return CHEM_OK;
 }
 
@@ -53,10 +44,12 @@ extern "C" int chem_step_di_noalloc(chem_mech m, int64_t n, int64_t ld, double d
                                     const chem_di_opts* opts, int32_t* status, int32_t* stats,
                                     chem_stream stream) {
   if (n < 0 || ld < n) return set_error(CHEM_E_ARG, "chem_step_di_noalloc: need 0 <= n <= ld");
-  const size_t need = chem_workspace_bytes(m, n);
-  if (need > kNoallocScratchBytes || n > (int64_t)0x7fffffff)
-    return set_error(CHEM_E_ARG, "chem_step_di_noalloc: the call needs more scratch than the fixed "
-                                 "256-byte device array holds (at most 2^31-1 cells per call)");
+  // The work-queue counter is 32-bit: at most 2^31 - 1 cells per call (chem_step_di has the
+  // same limit).
+  if (n > (int64_t)0x7fffffff)
+    return set_error(CHEM_E_ARG, "chem_step_di_noalloc: at most 2^31 - 1 cells per call (32-bit work-queue counter)");
+  if (chem_workspace_bytes(m, n) > kNoallocScratchBytes)
+    return set_error(CHEM_E_ARG, "chem_step_di_noalloc: the call needs more scratch than the fixed 256-byte device array");
   void* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
   if (rc) return rc;

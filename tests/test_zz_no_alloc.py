@@ -5,7 +5,13 @@ pool already owns the free HBM, or a time-step loop that must not synchronise th
 through cudaMalloc).  This test calls it through the C ABI and checks it against the
 workspace entry point on two calls in a row, within the direct-integration tolerance the
 parity tests use (1e-6 relative on T and on every Y_k above 1e-10); the kernels are
-deterministic, so the results are expected to be identical.  This file is collected last.
+deterministic, so the results are expected to be identical.  It also checks the property the
+entry point exists for: the device's free memory is the same before and after the calls, and
+a call on a caller's own (non-default) stream gives the same result.
+
+The file name sorts last so that a run stopping at the first failure (`pytest -x`) has already
+run every other test when this one runs; nothing here depends on what ran before it (the
+scratch address is looked up in the current context on every call).
 """
 import numpy as np
 import pytest
@@ -13,6 +19,13 @@ import pytest
 torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
+
+
+def _check(T, Y, s, Tr, Yr, sr, what):
+    assert np.array_equal(s, sr), what
+    assert np.all(np.abs(T - Tr) <= 1e-6 * np.abs(Tr)), what
+    big = Yr > 1e-10
+    assert np.all(np.where(big, np.abs(Y - Yr) <= 1e-6 * np.abs(Yr), True)), what
 
 
 def test_noalloc_matches_workspace_entry_point(mechs):
@@ -37,13 +50,26 @@ def test_noalloc_matches_workspace_entry_point(mechs):
     Tr, Yr, sr = Tr.cpu().numpy(), Yr.cpu().numpy(), sr.cpu().numpy()
     assert (sr == 0).all()
 
-    for call in range(2):
-        T, Y = T0.clone(), Y0.clone()
-        s = torch.full((n,), -1, dtype=torch.int32, device=dev)
+    # all buffers of the calls below exist before the free-memory reading
+    bufs = [(T0.clone(), Y0.clone(), torch.full((n,), -1, dtype=torch.int32, device=dev)) for _ in range(4)]
+    side = torch.cuda.Stream(device=dev)
+    free_before = None
+    for call in range(3):
+        T, Y, s = bufs[call]
         chem.chem_step_di_noalloc(gm, 5e-6, T, p, Y, s)
         torch.cuda.synchronize()
-        T, Y, s = T.cpu().numpy(), Y.cpu().numpy(), s.cpu().numpy()
-        assert np.array_equal(s, sr), call
-        assert np.all(np.abs(T - Tr) <= 1e-6 * np.abs(Tr)), call
-        big = Yr > 1e-10
-        assert np.all(np.where(big, np.abs(Y - Yr) <= 1e-6 * np.abs(Yr), True)), call
+        _check(T.cpu().numpy(), Y.cpu().numpy(), s.cpu().numpy(), Tr, Yr, sr, f"call {call}")
+        if call == 0:
+            # the first call may load the library's device module for this context (CUDA's
+            # lazy module loading), which the driver allocates; later calls allocate nothing
+            free_before, _ = torch.cuda.mem_get_info(dev)
+    # on a stream of the caller's own
+    side.wait_stream(torch.cuda.current_stream(dev))
+    T, Y, s = bufs[3]
+    with torch.cuda.stream(side):
+        chem.chem_step_di_noalloc(gm, 5e-6, T, p, Y, s, stream=side)
+    side.synchronize()
+    _check(T.cpu().numpy(), Y.cpu().numpy(), s.cpu().numpy(), Tr, Yr, sr, "side stream")
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info(dev)
+    assert free_after == free_before, (free_before, free_after)
