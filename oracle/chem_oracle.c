@@ -13,10 +13,11 @@
  *   NASA-7 polynomials (two ranges), k = A T^b exp(-Ea/RT), third-body [M] = sum alpha_k C_k,
  *   Lindemann falloff with the Troe broadening factor (Gilbert, Luther & Troe 1983),
  *   K_c = exp(-sum nu g/RT) (p0/RT)^{sum nu}, k_r = k_f / K_c.
- * The integrator is a variable-order (1..5), variable-step BDF in backward-difference form
- * with quasi-constant step size (Shampine & Reichelt, "The MATLAB ODE Suite", SIAM J. Sci.
- * Comput. 18, 1997), the family CVODE/VODE belong to (the paper's integrator, Sec. 2.2),
- * here with a FULL Newton iteration: the analytic Jacobian and a fresh LU at every iterate.
+ * The integrator is the three-stage Radau IIA method (order 5, L-stable; Hairer & Wanner,
+ * "Solving ODEs II", Sec. IV.5) with a FULL Newton iteration on its stage equations (the
+ * analytic Jacobian at every stage value and a fresh LU at every iterate) and step-size
+ * control by step doubling -- a one-step implicit Runge-Kutta method, deliberately unrelated
+ * to the multistep BDF scheme of the paper's CVODE (Sec. 2.2) and of the GPU kernel.
  * A fixed-step classical RK4 is the second, independent path for small checks.
  * Mixture properties: c_p, h mass-weighted; Wilke's rule for viscosity; the Mathur-Saxena
  * average for conductivity; T from h by Newton (the paper's Sec. 2.1 "Newton's method and
@@ -580,8 +581,17 @@ int or_dense_solve(int n, double* A, double* b) {
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* BDF integrator                                                                        */
+/* Radau IIA integrator                                                                  */
 /* ------------------------------------------------------------------------------------ */
+/* The three-stage Radau IIA collocation method (Ehle 1969; Hairer & Wanner, "Solving
+ * Ordinary Differential Equations II", Sec. IV.5): order 5, stage order 3, L-stable, stiffly
+ * accurate (the new state is the last stage).  Chosen as the oracle's method because it is a
+ * one-step implicit Runge-Kutta method, unrelated to the multistep (BDF) scheme the GPU
+ * kernel uses, so the two agree only through the solution of Eq. 2 itself.
+ *
+ * Nodes c_i are the zeros of the Radau right polynomial d^2/dx^2 [x^2 (x - 1)^3]:
+ * c = ((4 - sqrt 6)/10, (4 + sqrt 6)/10, 1); the coefficients a_ij = int_0^{c_i} l_j(s) ds
+ * integrate the Lagrange basis l_j of those nodes (collocation). */
 typedef struct {
   double rtol, atol_Y, atol_T;
   int max_steps;
@@ -591,8 +601,29 @@ typedef struct {
   int steps, rhs_evals, jac_evals, lu, failed_err, failed_newton;
 } or_stats;
 
-#define MAXORD 5
-#define NEWTON_MAXIT 4
+static void radau_tableau(double A[3][3], double c[3]) {
+  const double s6 = sqrt(6.0);
+  c[0] = (4.0 - s6) / 10.0;
+  c[1] = (4.0 + s6) / 10.0;
+  c[2] = 1.0;
+  A[0][0] = (88.0 - 7.0 * s6) / 360.0;
+  A[0][1] = (296.0 - 169.0 * s6) / 1800.0;
+  A[0][2] = (-2.0 + 3.0 * s6) / 225.0;
+  A[1][0] = (296.0 + 169.0 * s6) / 1800.0;
+  A[1][1] = (88.0 + 7.0 * s6) / 360.0;
+  A[1][2] = (-2.0 - 3.0 * s6) / 225.0;
+  A[2][0] = (16.0 - s6) / 36.0;
+  A[2][1] = (16.0 + s6) / 36.0;
+  A[2][2] = 1.0 / 9.0;
+}
+
+/* Testing hook: the tableau, A row-major [9], c [3]. */
+void or_radau_tableau(double* A, double* c) {
+  double a[3][3];
+  radau_tableau(a, c);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A[i * 3 + j] = a[i][j];
+}
 
 static double wrms(const double* x, const double* scale, int n) {
   double s = 0;
@@ -600,190 +631,184 @@ static double wrms(const double* x, const double* scale, int n) {
   return sqrt(s / n);
 }
 
-/* Rescale the difference array D[0..order] for a step-size change by `factor`:
- * D <- (R(factor) U)^T D, with R(r)_{ij} = prod_{l=1..i} (l - 1 - r j)/l (row 0 = 1). */
-static void rescale_differences(double* D, int n, int order, double factor) {
-  double R[MAXORD + 1][MAXORD + 1], U[MAXORD + 1][MAXORD + 1], RU[MAXORD + 1][MAXORD + 1];
-  for (int j = 0; j <= order; ++j) { R[0][j] = 1; U[0][j] = 1; }
-  for (int i = 1; i <= order; ++i)
-    for (int j = 0; j <= order; ++j) {
-      if (j == 0) { R[i][j] = 0; U[i][j] = 0; continue; }
-      R[i][j] = R[i - 1][j] * (i - 1 - factor * j) / i;
-      U[i][j] = U[i - 1][j] * (i - 1 - 1.0 * j) / i;
-    }
-  for (int i = 0; i <= order; ++i)
-    for (int j = 0; j <= order; ++j) {
-      double s = 0;
-      for (int l = 0; l <= order; ++l) s += R[i][l] * U[l][j];
-      RU[i][j] = s;
-    }
-  double* tmp = (double*)malloc(sizeof(double) * (order + 1) * n);
-  for (int j = 0; j <= order; ++j)
-    for (int c = 0; c < n; ++c) {
-      double s = 0;
-      for (int i = 0; i <= order; ++i) s += RU[i][j] * D[i * n + c];
-      tmp[j * n + c] = s;
-    }
-  memcpy(D, tmp, sizeof(double) * (order + 1) * n);
-  free(tmp);
+typedef struct {
+  double *Z, *Ys, *F, *J, *M, *G;
+  int* piv;
+} radau_buf;
+
+static void radau_alloc(int n, radau_buf* r) {
+  r->Z = (double*)calloc((size_t)3 * n, sizeof(double));
+  r->Ys = (double*)calloc((size_t)3 * n, sizeof(double));
+  r->F = (double*)calloc((size_t)3 * n, sizeof(double));
+  r->G = (double*)calloc((size_t)3 * n, sizeof(double));
+  r->J = (double*)calloc((size_t)3 * n * n, sizeof(double));
+  r->M = (double*)calloc((size_t)9 * n * n, sizeof(double));
+  r->piv = (int*)calloc((size_t)3 * n, sizeof(int));
 }
 
-/* status: 0 ok, 1 max steps, 2 step-size/Newton failure, 3 non-finite */
+static void radau_free(radau_buf* r) {
+  free(r->Z); free(r->Ys); free(r->F); free(r->G); free(r->J); free(r->M); free(r->piv);
+}
+
+#define RADAU_NEWTON_MAXIT 12
+
+/* One Radau IIA step of length h from y into ynew.  The stage increments Z_i = Y_i - y solve
+ *   Z_i = h sum_j a_ij f(y + Z_j),   i = 1..3,
+ * by a full Newton iteration from Z = 0: at every iterate the exact Jacobian of this 3n
+ * system (block (i, j) = delta_ij I - h a_ij J(y + Z_j)) is formed from the analytic Jacobian
+ * at the three stage values and factored afresh.  The iteration stops when the correction's
+ * weighted RMS norm (weights `scale`, repeated per stage) is below kappa, or when it has
+ * stalled at the rounding floor (from the third iterate on, no longer halving) below a tenth
+ * of the error tolerance.  ynew = y + Z_3.  Returns 0, or -1 when the iteration fails (no
+ * convergence in RADAU_NEWTON_MAXIT iterates, growing corrections, a singular matrix or a
+ * non-finite value). */
+static int radau_step(const omech* m, double p, const double* y, double h, const double* scale,
+                      double kappa, double* ynew, radau_buf* r, or_stats* st, work* w) {
+  const int n = m->K + 1, N = 3 * n;
+  double A[3][3], c[3];
+  radau_tableau(A, c);
+  for (int i = 0; i < N; ++i) r->Z[i] = 0.0;
+  double prev = INFINITY;
+  for (int it = 0; it < RADAU_NEWTON_MAXIT; ++it) {
+    for (int j = 0; j < 3; ++j) {
+      for (int q = 0; q < n; ++q) r->Ys[j * n + q] = y[q] + r->Z[j * n + q];
+      jac_w(m, p, &r->Ys[j * n], &r->F[j * n], &r->J[(size_t)j * n * n], w);
+      st->jac_evals++;
+      st->rhs_evals++;
+    }
+    for (int i = 0; i < N; ++i) if (!isfinite(r->F[i])) return -1;
+    /* residual G_i = Z_i - h sum_j a_ij F_j  and matrix delta_ij I - h a_ij J_j */
+    for (int i = 0; i < 3; ++i)
+      for (int q = 0; q < n; ++q) {
+        double s = 0;
+        for (int j = 0; j < 3; ++j) s += A[i][j] * r->F[j * n + q];
+        r->G[i * n + q] = -(r->Z[i * n + q] - h * s);
+      }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        for (int q = 0; q < n; ++q)
+          for (int u = 0; u < n; ++u) {
+            double v = -h * A[i][j] * r->J[(size_t)j * n * n + (size_t)q * n + u];
+            if (i == j && q == u) v += 1.0;
+            r->M[(size_t)(i * n + q) * N + (j * n + u)] = v;
+          }
+    if (lu_factor(r->M, N, r->piv) != 0) return -1;
+    st->lu++;
+    lu_solve(r->M, N, r->piv, r->G);   /* G now holds the correction */
+    double s2 = 0;
+    for (int i = 0; i < 3; ++i)
+      for (int q = 0; q < n; ++q) {
+        const double v = r->G[i * n + q] / scale[q];
+        s2 += v * v;
+        r->Z[i * n + q] += r->G[i * n + q];
+      }
+    const double nrm = sqrt(s2 / N);
+    if (!isfinite(nrm)) return -1;
+    if (nrm <= kappa || (it >= 2 && nrm <= 0.1 && nrm >= 0.5 * prev)) {
+      for (int q = 0; q < n; ++q) ynew[q] = y[q] + r->Z[2 * n + q];
+      for (int q = 0; q < n; ++q) if (!isfinite(ynew[q])) return -1;
+      return 0;
+    }
+    if (it >= 3 && nrm > prev) return -1;
+    prev = nrm;
+  }
+  return -1;
+}
+
+/* z(t + tend) from z(t) by Radau IIA steps with step-size control by step doubling
+ * (Richardson extrapolation, Hairer, Norsett & Wanner, "Solving ODEs I", Sec. II.4): every
+ * step of length h is taken once whole (y1) and once as two halves (y2); y2 is kept, and its
+ * error is estimated by the whole difference |y2 - y1| -- the extrapolated estimate
+ * |y2 - y1|/(2^5 - 1) assumes the full order 5, which stiff components do not reach (stage
+ * order 3), so the undivided difference is the safe bound.  The step is accepted when the
+ * weighted RMS norm of that estimate, weights atol + rtol max(|y|, |y2|), is at most 1; the
+ * next step is h * min(4, max(0.2, 0.9 err^(-1/6))) (no growth right after a rejection).
+ * Newton failures halve h.  Status: 0 ok, 1 max steps, 2 step size underflow, 3 non-finite. */
 static int integrate_w(const omech* m, double p, double* z, double tend, const or_opts* o,
                        or_stats* st, work* w) {
-  int K = m->K, n = K + 1;
+  const int K = m->K, n = K + 1;
   const double EPS = 2.220446049250313e-16;
-  double gamma[MAXORD + 2], errc[MAXORD + 2];
-  gamma[0] = 0;
-  for (int k = 1; k <= MAXORD + 1; ++k) gamma[k] = gamma[k - 1] + 1.0 / k;
-  for (int k = 0; k <= MAXORD + 1; ++k) errc[k] = 1.0 / (k + 1);
-  double newton_tol = fmax(10 * EPS / o->rtol, fmin(0.03, sqrt(o->rtol)));
   memset(st, 0, sizeof(*st));
   for (int i = 0; i < n; ++i) if (!isfinite(z[i])) return 3;
   if (tend <= 0) return 0;
-
-  double* D = (double*)calloc((size_t)(MAXORD + 3) * n, sizeof(double));
-  double* buf = (double*)calloc((size_t)n * 8 + (size_t)n * n, sizeof(double));
-  double *f = buf, *y = buf + n, *ypred = buf + 2 * n, *psi = buf + 3 * n, *d = buf + 4 * n;
-  double *dy = buf + 5 * n, *scale = buf + 6 * n, *tmp = buf + 7 * n, *Mx = buf + 8 * n;
-  int* piv = (int*)calloc(n, sizeof(int));
-  double* atol = (double*)malloc(sizeof(double) * n);
+  radau_buf r;
+  radau_alloc(n, &r);
+  double* buf = (double*)malloc(sizeof(double) * (size_t)n * 6);
+  double *y1 = buf, *ym = buf + n, *y2 = buf + 2 * n, *scale = buf + 3 * n, *d = buf + 4 * n;
+  double* atol = buf + 5 * n;
   for (int i = 0; i < K; ++i) atol[i] = o->atol_Y;
   atol[K] = o->atol_T;
-  int status = 0;
-
-  /* initial step (Hairer, Norsett & Wanner, Sec. II.4) for order 1 */
-  rhs_w(m, p, z, f, w); st->rhs_evals++;
-  for (int i = 0; i < n; ++i) scale[i] = atol[i] + o->rtol * fabs(z[i]);
-  double d0 = wrms(z, scale, n), d1 = wrms(f, scale, n);
-  double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
-  if (h0 > tend) h0 = tend;
-  for (int i = 0; i < n; ++i) y[i] = z[i] + h0 * f[i];
-  rhs_w(m, p, y, tmp, w); st->rhs_evals++;
-  for (int i = 0; i < n; ++i) dy[i] = tmp[i] - f[i];
-  double d2 = wrms(dy, scale, n) / h0;
-  double h1 = (d1 <= 1e-15 && d2 <= 1e-15) ? fmax(1e-6, h0 * 1e-3) : pow(0.01 / fmax(d1, d2), 0.5);
-  double h = fmin(100 * h0, h1);
-  if (!(h > 0) || !isfinite(h)) h = 1e-12 * tend;
-  if (h > tend) h = tend;
-
-  for (int i = 0; i < n; ++i) { D[i] = z[i]; D[n + i] = h * f[i]; }
-  int order = 1, n_equal = 0;
-  double t = 0;
+  /* Newton stop: 1e-3 of the error tolerance, but not below what rounding allows */
+  const double kappa = fmax(1e-3, 100.0 * EPS / o->rtol);
+  int status = 0, rejected = 0;
+  double t = 0.0, h = fmin(tend, 1e-10);
   while (t < tend) {
     if (st->steps >= o->max_steps) { status = 1; break; }
-    double hmin = 10 * EPS * fabs(t) + 1e-300;
-    if (t + h > tend) {
-      double hn = tend - t;
-      rescale_differences(D, n, order, hn / h);
-      h = hn;
-      n_equal = 0;
+    if (h < 1e-22 * tend || h < 1e-300) { status = 2; break; }
+    const int last = t + h >= tend;
+    if (last) h = tend - t;
+    for (int i = 0; i < n; ++i) scale[i] = atol[i] + o->rtol * fabs(z[i]);
+    int ok = radau_step(m, p, z, h, scale, kappa, y1, &r, st, w) == 0;
+    if (ok) ok = radau_step(m, p, z, 0.5 * h, scale, kappa, ym, &r, st, w) == 0;
+    if (ok) {
+      for (int i = 0; i < n; ++i) scale[i] = atol[i] + o->rtol * fabs(ym[i]);
+      ok = radau_step(m, p, ym, 0.5 * h, scale, kappa, y2, &r, st, w) == 0;
     }
-    int accepted = 0, newton_iters = 0;
-    double err_norm = 0;
-    while (!accepted) {
-      if (h < hmin) { status = 2; goto done; }
-      double t_new = t + h;
-      if (t_new > tend || tend - t_new < hmin) t_new = tend;
-      for (int i = 0; i < n; ++i) {
-        double s = 0;
-        for (int j = 0; j <= order; ++j) s += D[j * n + i];
-        ypred[i] = s;
-        scale[i] = atol[i] + o->rtol * fabs(s);
-        double ps = 0;
-        for (int j = 1; j <= order; ++j) ps += gamma[j] * D[j * n + i];
-        psi[i] = ps / gamma[order];
-      }
-      double c = h / gamma[order];
-      /* full Newton on  d - c f(ypred + d) + psi = 0 */
-      for (int i = 0; i < n; ++i) { d[i] = 0; y[i] = ypred[i]; }
-      int converged = 0;
-      double dy_old = 0;
-      newton_iters = 0;
-      for (int it = 0; it < NEWTON_MAXIT; ++it) {
-        jac_w(m, p, y, f, Mx, w); st->jac_evals++; st->rhs_evals++;
-        int finite = 1;
-        for (int i = 0; i < n; ++i) if (!isfinite(f[i])) finite = 0;
-        if (!finite) break;
-        for (int i = 0; i < n * n; ++i) Mx[i] = -c * Mx[i];
-        for (int i = 0; i < n; ++i) Mx[i * n + i] += 1.0;
-        if (lu_factor(Mx, n, piv) != 0) break;
-        st->lu++;
-        for (int i = 0; i < n; ++i) dy[i] = c * f[i] - psi[i] - d[i];
-        lu_solve(Mx, n, piv, dy);
-        double dn = wrms(dy, scale, n);
-        ++newton_iters;
-        double rate = (it > 0) ? dn / dy_old : -1;
-        if (it > 0 && (rate >= 1 || pow(rate, NEWTON_MAXIT - it) / (1 - rate) * dn > newton_tol)) break;
-        for (int i = 0; i < n; ++i) { y[i] += dy[i]; d[i] += dy[i]; }
-        if (dn == 0 || (it > 0 && rate / (1 - rate) * dn < newton_tol)) { converged = 1; break; }
-        if (it == 0 && dn < newton_tol * 1e-3) { converged = 1; break; }
-        dy_old = dn;
-      }
-      if (!converged) {
-        st->failed_newton++;
-        rescale_differences(D, n, order, 0.5);
-        h *= 0.5;
-        n_equal = 0;
-        continue;
-      }
-      double safety = 0.9 * (2 * NEWTON_MAXIT + 1) / (2 * NEWTON_MAXIT + newton_iters);
-      for (int i = 0; i < n; ++i) {
-        scale[i] = atol[i] + o->rtol * fabs(y[i]);
-        tmp[i] = errc[order] * d[i];
-      }
-      err_norm = wrms(tmp, scale, n);
-      if (err_norm > 1) {
-        st->failed_err++;
-        double fac = fmax(0.2, safety * pow(err_norm, -1.0 / (order + 1)));
-        rescale_differences(D, n, order, fac);
-        h *= fac;
-        n_equal = 0;
-        continue;
-      }
-      accepted = 1;
-      t = t_new;
+    if (!ok) {
+      st->failed_newton++;
+      h *= 0.5;
+      rejected = 1;
+      continue;
+    }
+    for (int i = 0; i < n; ++i) {
+      scale[i] = atol[i] + o->rtol * fmax(fabs(z[i]), fabs(y2[i]));
+      d[i] = y2[i] - y1[i];
+    }
+    const double err = wrms(d, scale, n);
+    double fac = err > 0 ? 0.9 * pow(err, -1.0 / 6.0) : 4.0;
+    fac = fmin(4.0, fmax(0.2, fac));
+    if (err <= 1.0) {
+      for (int i = 0; i < n; ++i) z[i] = y2[i];
+      t = last ? tend : t + h;
       st->steps++;
-      n_equal++;
-      /* update differences: D[order+2] = d - D[order+1]; D[order+1] = d; D[i] += D[i+1] */
-      for (int i = 0; i < n; ++i) {
-        D[(order + 2) * n + i] = d[i] - D[(order + 1) * n + i];
-        D[(order + 1) * n + i] = d[i];
-      }
-      for (int j = order; j >= 0; --j)
-        for (int i = 0; i < n; ++i) D[j * n + i] += D[(j + 1) * n + i];
-      if (n_equal < order + 1) break;
-      /* order and step selection */
-      double em = INFINITY, ep = INFINITY;
-      if (order > 1) {
-        for (int i = 0; i < n; ++i) tmp[i] = errc[order - 1] * D[order * n + i];
-        em = wrms(tmp, scale, n);
-      }
-      if (order < MAXORD) {
-        for (int i = 0; i < n; ++i) tmp[i] = errc[order + 1] * D[(order + 2) * n + i];
-        ep = wrms(tmp, scale, n);
-      }
-      double fm = (em == INFINITY) ? 0 : (em == 0 ? 1e30 : pow(em, -1.0 / order));
-      double f0 = (err_norm == 0) ? 1e30 : pow(err_norm, -1.0 / (order + 1));
-      double fp = (ep == INFINITY) ? 0 : (ep == 0 ? 1e30 : pow(ep, -1.0 / (order + 2)));
-      int delta = 0;
-      double best = f0;
-      if (fm > best) { best = fm; delta = -1; }
-      if (fp > best) { best = fp; delta = 1; }
-      order += delta;
-      double fac = fmin(10.0, safety * best);
-      rescale_differences(D, n, order, fac);
-      h *= fac;
-      n_equal = 0;
+      if (rejected) fac = fmin(fac, 1.0);
+      rejected = 0;
+    } else {
+      st->failed_err++;
+      rejected = 1;
     }
+    h *= fac;
   }
-done:
-  if (status == 0) {
-    for (int i = 0; i < n; ++i) z[i] = D[i];
+  if (status == 0)
     for (int i = 0; i < n; ++i) if (!isfinite(z[i])) status = 3;
-  }
-  free(D); free(buf); free(piv); free(atol);
+  radau_free(&r);
+  free(buf);
   return status;
+}
+
+/* Testing hook: nsteps fixed Radau IIA steps of length h (no error control), Newton stop at
+ * 1e-14 relative.  Returns 0, or -1 if a step's Newton iteration failed. */
+int or_radau_fixed(const void* hd, double p, double* z, double h, int nsteps) {
+  const omech* m = (const omech*)hd;
+  const int n = m->K + 1;
+  work w;
+  work_alloc(m, &w);
+  radau_buf r;
+  radau_alloc(n, &r);
+  or_stats st;
+  memset(&st, 0, sizeof(st));
+  double* buf = (double*)malloc(sizeof(double) * (size_t)n * 2);
+  double *scale = buf, *y = buf + n;
+  int s = 0;
+  for (int k = 0; k < nsteps && s == 0; ++k) {
+    for (int i = 0; i < n; ++i) scale[i] = 1e-30 + 1e-14 * fabs(z[i]);
+    s = radau_step(m, p, z, h, scale, 1.0, y, &r, &st, &w);
+    if (s == 0) memcpy(z, y, sizeof(double) * n);
+  }
+  free(buf);
+  radau_free(&r);
+  work_free(&w);
+  return s;
 }
 
 int or_integrate(const void* h, double p, double* z, double dt, double rtol, double atol_Y,

@@ -65,6 +65,8 @@ def _load():
                                         C.c_void_p, C.c_void_p]
         lib.or_T_from_h.argtypes = [C.c_void_p, C.c_double, _dp, C.c_double,
                                     C.POINTER(C.c_double)]
+        lib.or_radau_tableau.argtypes = [_dp, _dp]
+        lib.or_radau_fixed.argtypes = [C.c_void_p, C.c_double, _dp, C.c_double, C.c_int]
         lib.or_max_threads.restype = C.c_int
         lib.or_dense_solve.argtypes = [C.c_int, _dp, _dp]
         _lib = lib
@@ -149,7 +151,9 @@ class Oracle:
     # -- integration
     def integrate(self, p: float, z: np.ndarray, dt: float, rtol=ORACLE_RTOL, atol_Y=ORACLE_ATOL_Y,
                   atol_T=ORACLE_ATOL_T, max_steps=200000):
-        """z(t+dt) of Eq. 2 by the BDF integrator; returns (z_new, status, stats[6])."""
+        """z(t+dt) of Eq. 2 by the Radau IIA integrator; returns (z_new, status, stats[6]):
+        accepted steps, RHS evaluations, Jacobian evaluations, LU factorisations, error-test
+        rejections, Newton failures."""
         z = np.array(z, dtype=np.float64)
         st = np.zeros(6, dtype=np.int32)
         s = self.lib.or_integrate(self.h, float(p), z, float(dt), rtol, atol_Y, atol_T,
@@ -169,6 +173,20 @@ class Oracle:
         self.lib.or_integrate_batch(self.h, n, n, float(dt), T, p, Y, rtol, atol_Y, atol_T,
                                     int(max_steps), status, steps, int(nthreads))
         return T, Y, status, steps
+
+    def radau_fixed(self, p: float, z: np.ndarray, h: float, nsteps: int) -> np.ndarray:
+        """nsteps Radau IIA steps of fixed length h (no error control; for order checks)."""
+        z = np.array(z, dtype=np.float64)
+        if self.lib.or_radau_fixed(self.h, float(p), z, float(h), int(nsteps)) != 0:
+            raise FloatingPointError("Radau IIA Newton iteration failed")
+        return z
+
+    @staticmethod
+    def radau_tableau():
+        """(A [3, 3], c [3]) of the three-stage Radau IIA method the integrator uses."""
+        A, c = np.zeros(9), np.zeros(3)
+        _load().or_radau_tableau(A, c)
+        return A.reshape(3, 3), c
 
     def rk4(self, p: float, z: np.ndarray, dt: float, nsub: int) -> np.ndarray:
         z = np.array(z, dtype=np.float64)

@@ -178,6 +178,52 @@ def test_integrator_isomerisation_closed_form():
             assert zn[3] == pytest.approx(T0, rel=1e-12)
 
 
+# --- the oracle's method: three-stage Radau IIA (Hairer & Wanner II, Sec. IV.5) -----------
+def test_radau_tableau_order_conditions():
+    """Nodes are the zeros of d^2/dx^2 [x^2 (x-1)^3] (Radau right points); the weights satisfy
+    B(5) (quadrature exact to degree 4, hence order 5), the coefficients C(3) (collocation:
+    stage order 3), and the last row equals the weights (stiffly accurate)."""
+    A, c = Oracle.radau_tableau()
+    P = np.polynomial.Polynomial([0, 0, 1]) * np.polynomial.Polynomial([-1, 1]) ** 3
+    assert np.allclose(np.sort(P.deriv(2).roots().real), c, rtol=0, atol=1e-14)
+    b = A[2]
+    for q in range(1, 6):
+        assert (b * c ** (q - 1)).sum() == pytest.approx(1.0 / q, rel=1e-14)
+    for q in range(1, 4):
+        assert np.allclose(A @ c ** (q - 1), c ** q / q, rtol=1e-14, atol=1e-15)
+    assert c[2] == 1.0
+
+
+def test_radau_fixed_steps_converge_with_order_five():
+    """On the closed-form isomerisation, halving the fixed step divides the global error by
+    about 2^5 (a wrong coefficient drops the order)."""
+    o = Oracle(os.path.join(GOLDEN, "isomer.mech"))
+    YA0, YB0, T0, tend = 0.6, 0.1, 1000.0, 1e-5
+    YAeq = (YA0 + YB0) / 3.0
+    exact = YAeq + (YA0 - YAeq) * math.exp(-3e5 * tend)
+    errs = []
+    for N in (8, 16, 32):
+        z = o.radau_fixed(P, np.array([YA0, YB0, 1 - YA0 - YB0, T0]), tend / N, N)
+        errs.append(abs(z[0] - exact))
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 4.6 < math.log2(e1 / e2) < 5.4, errs
+
+
+@pytest.mark.parametrize("kind,n,dt", [("c_30", 4, 5e-6), ("c_53", 3, 1e-5)])
+def test_integrator_rtol_refinement(oracles, mechs, kind, n, dt):
+    """The oracle's default tolerance (rtol 1e-10) agrees with a 100x tighter run to 1e-9
+    relative on T and on every mass fraction above 1e-10."""
+    o = oracles[kind]
+    m, _ = mechs[kind]
+    st = w.make_states(m, n, 104)
+    T1, Y1, s1, _ = o.integrate_batch(st.T, st.p, st.Y, dt)
+    T2, Y2, s2, _ = o.integrate_batch(st.T, st.p, st.Y, dt, rtol=1e-12)
+    assert (s1 == 0).all() and (s2 == 0).all()
+    assert (np.abs(T1 - T2) <= 1e-9 * T2).all()
+    big = Y2 > 1e-10
+    assert (np.abs(Y1 - Y2)[big] <= 1e-9 * Y2[big]).all()
+
+
 # --- integrator against brute-force fine-step RK4 ------------------------------------------
 def test_integrator_against_rk4(oracles, mechs):
     o = oracles["h2_9"]
@@ -323,6 +369,25 @@ def test_thermo_props_special_cases(oracles, mechs):
         # Newton T-from-h round trip
         h = o.thermo_props(T, st.Y[:, i])[1]
         assert o.T_from_h(h, st.Y[:, i], T0=1000.0) == pytest.approx(T, abs=1e-8)
+
+
+def test_wilke_viscosity_textbook_example():
+    """Wilke's rule on the worked example of Bird, Stewart & Lightfoot (Sec. 1.4): CO2/O2/N2 at
+    mole fractions 0.133/0.039/0.828 give 1714e-7 g/(cm s) = 1.714e-5 Pa s (4 digits)."""
+    o = Oracle(os.path.join(GOLDEN, "wilke_bsl.mech"))
+    x = np.array([0.133, 0.039, 0.828])
+    Y = x * o.W / (x * o.W).sum()
+    mu = o.thermo_props(293.0, Y)[2]
+    assert mu == pytest.approx(1.714e-5, abs=0.5e-8)        # half a unit of the 4th digit
+
+
+def test_conductivity_combining_rule_binary():
+    """Mixture-averaged conductivity (half the sum of the arithmetic and harmonic means over
+    MOLE fractions): 0.25 CO2 (0.02 W/m/K) + 0.75 O2 (0.06) gives (0.05 + 0.04)/2 = 0.045."""
+    o = Oracle(os.path.join(GOLDEN, "wilke_bsl.mech"))
+    x = np.array([0.25, 0.75, 0.0])
+    Y = x * o.W / (x * o.W).sum()
+    assert o.thermo_props(800.0, Y)[3] == pytest.approx(0.045, rel=1e-13)
 
 
 # --- loader rejects malformed input ----------------------------------------------------------
