@@ -15,9 +15,17 @@
   predicted by its own MLP): K independent networks with one output each, evaluated one after
   the other on the same inputs; their parameters as one flat array stacked by species.
 
+* The learned step's update of the cell state (`ann_update`): inverse Box-Cox of the predicted
+  increments, renormalisation, the element-residual check, the weighted least-squares
+  projection onto exact element conservation, T from enthalpy conservation, and the flags of
+  the fallback rules (`range_flags` for the training-range check of the inputs).
+
 Parity status: forward, backward, loss gradient (all three terms), the heat-release
 coefficients and Adam are pinned by the tests in tests/test_oracle_mlp.py (finite differences,
-closed forms, special values); the per-species networks by their equality with one network
+closed forms, special values; the BF16-storage emulation of backward against the unemulated
+pass within its rounding); the update by tests/test_oracle_ann_update.py (the identity on an
+element-conserving integrated state, a hand-computed projection, exact element and enthalpy
+conservation, each flag rule); the per-species networks by their equality with one network
 of block-diagonal weights, by the independence of each output from the other species'
 weights and by finite differences.  The loss weights W1, W2, W3 of Eq. 11 are unstated in the
 paper: W1 = 1, W2 = 0.1 and W3 = 0 by default.
@@ -102,17 +110,28 @@ def forward(params: Params, X: np.ndarray, bf16: bool = False):
     raise AssertionError("empty network")
 
 
-def backward(params: Params, cache, dU: np.ndarray) -> Params:
-    """Gradients of a scalar loss with dL/dU = dU."""
+def backward(params: Params, cache, dU: np.ndarray, bf16: bool = False, with_deltas: bool = False):
+    """Gradients of a scalar loss with dL/dU = dU: dW_l = delta_l^T A_l, db_l = sum_b delta_l,
+    delta_{l-1} = (delta_l W_l) * GELU'(Z_{l-1}).
+
+    bf16=True emulates BF16 storage where a BF16 training pass stores values: dU and every
+    delta_l, the weights W_l and the pre-activations Z_l (GELU' is taken at the stored Z); the
+    cache must come from forward(..., bf16=True).  with_deltas=True also returns the deltas
+    (per layer, the sums' left operands), e.g. for element-wise error bounds."""
     acts, zs = cache
     grads = [None] * len(params)
-    d = dU
+    deltas = [None] * len(params)
+    d = round_bf16(dU) if bf16 else dU
     for l in range(len(params) - 1, -1, -1):
         W, _ = params[l]
+        deltas[l] = d
         grads[l] = (d.T @ acts[l], d.sum(axis=0))
         if l > 0:
-            d = (d @ W) * dgelu(zs[l - 1])
-    return grads
+            if bf16:
+                d = round_bf16((d @ round_bf16(W)) * dgelu(round_bf16(zs[l - 1])))
+            else:
+                d = (d @ W) * dgelu(zs[l - 1])
+    return (grads, deltas) if with_deltas else grads
 
 
 def unflatten_per_species(flat: np.ndarray, dims: List[int], K: int) -> List[Params]:
@@ -151,9 +170,14 @@ def forward_per_species(nets: List[Params], X: np.ndarray, bf16: bool = False):
     return np.stack(cols, axis=1), caches
 
 
-def backward_per_species(nets: List[Params], caches, dU: np.ndarray) -> List[Params]:
-    """Gradients of every species' network, given dL/dU [n, >= K]."""
-    return [backward(net, cache, dU[:, k:k + 1]) for k, (net, cache) in enumerate(zip(nets, caches))]
+def backward_per_species(nets: List[Params], caches, dU: np.ndarray, bf16: bool = False,
+                         with_deltas: bool = False):
+    """Gradients of every species' network, given dL/dU [n, >= K] (options as backward)."""
+    out = [backward(net, cache, dU[:, k:k + 1], bf16, with_deltas)
+           for k, (net, cache) in enumerate(zip(nets, caches))]
+    if with_deltas:
+        return [g for g, _ in out], [d for _, d in out]
+    return out
 
 
 def loss_and_grad(U, Ut, K, bcty=None, out_mean=None, out_std=None, w_data=1.0, w_mass=0.1,
@@ -214,3 +238,103 @@ def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ------------------------------------------------------------------------------------------
+# the learned step's update of the cell state (Sec. 2.2 output definition with Eq. 7, and the
+# fallback rules of the spec reading: range, non-finite values, element conservation,
+# temperature range and an optional cap on |dT|)
+# ------------------------------------------------------------------------------------------
+FLAG_RANGE, FLAG_NONFINITE, FLAG_ELEMENTS, FLAG_T_RANGE, FLAG_DT = 1, 2, 4, 8, 16
+
+
+def range_flags(T, p, Y, in_min, in_max, margin):
+    """Bit FLAG_RANGE per cell when a raw input feature x = [T, p, F(Y_1..Y_K)] lies outside
+    [min - m (max - min), max + m (max - min)] of the training set.  Y [K, n]."""
+    raw = np.concatenate([np.asarray(T, np.float64)[None, :], np.asarray(p, np.float64)[None, :],
+                          bct(Y)], axis=0)
+    span = (in_max - in_min)[:, None]
+    out = (raw < in_min[:, None] - margin * span) | (raw > in_max[:, None] + margin * span)
+    return np.where(out.any(axis=0), FLAG_RANGE, 0).astype(np.int32), raw
+
+
+def ann_update(orc, T, Y, U, out_mean, out_std, elem_tol=1e-2, T_min=250.0, T_max=3500.0,
+               dT_max=0.0, flags_in=None):
+    """New cell states from the network output U [n, >= K] (z-scored Box-Cox increments), FP64.
+
+    Per cell, in this order:
+      1. z_k = F(Y_k) + sigma_k U_k + mu_k and Y*_k = F^-1(z_k) (0 where lambda z + 1 <= 0);
+         a non-finite z_k, or a sum of the Y*_k that is not finite and positive, flags the cell
+         FLAG_NONFINITE and nothing else is evaluated;
+      2. Y* <- Y* / sum_k Y*_k (unit mass);
+      3. element moles e_e = sum_k a_ke Y_k / W_k before (Y) and after (Y*); the residual
+         max_e |e*_e - e_e| / e_e over the elements present before (e_e > 0) above elem_tol
+         flags FLAG_ELEMENTS;
+      4. if not flagged, Y* is projected onto exact element conservation: the change dY
+         minimising sum_k dY_k^2 / Y*_k subject to sum_k a_ke (Y*_k + dY_k)/W_k = e_e is
+         dY_k = Y*_k sum_e (a_ke/W_k) lambda_e with (C diag(Y*) C^T) lambda = e - C Y*
+         (C_ek = a_ke/W_k; elements absent from both states form zero rows and are left
+         out), then Y'_k = max(Y*_k + dY_k, 0);
+      5. T' from enthalpy conservation at constant p, h(T', Y') = h(T, Y) (Newton, the oracle's
+         NASA-7), with Y' the projected state, or Y* itself when FLAG_ELEMENTS is set;
+      6. a non-finite T' flags FLAG_NONFINITE, else T' outside [T_min, T_max] FLAG_T_RANGE,
+         else (dT_max > 0) |T' - T| > dT_max FLAG_DT.
+    Cells with a non-zero flags_in (the range flag, bit FLAG_RANGE) are left as they are.
+    Flagged cells keep (T, Y).  `orc` is the mechanism's Oracle (W, composition, h, T(h)).
+
+    Returns (T_new, Y_new [K, n], flags, info) with info the per-cell element residual and the
+    unchecked T' (nan where not reached), for comparisons near a decision threshold.
+    """
+    T = np.asarray(T, np.float64)
+    Y = np.asarray(Y, np.float64)
+    K, n = Y.shape
+    U = np.asarray(U, np.float64)[:, :K]
+    Cm = orc.comp.astype(np.float64) / orc.W[:, None]          # [K, E] element moles per kg
+    flags = np.zeros(n, np.int32) if flags_in is None else np.array(flags_in, np.int32)
+    T_new, Y_new = T.copy(), Y.copy()
+    res_out = np.full(n, np.nan)
+    Tp_out = np.full(n, np.nan)
+    for i in range(n):
+        if flags[i]:
+            continue
+        y = Y[:, i]
+        with np.errstate(over="ignore", invalid="ignore"):
+            z = bct(y) + U[i] * out_std + out_mean
+            ys = ibct(z)
+            s = ys.sum()
+        if not np.isfinite(z).all() or not (np.isfinite(s) and s > 0):
+            flags[i] = FLAG_NONFINITE
+            continue
+        ys = ys / s
+        e_old = Cm.T @ y
+        e_new = Cm.T @ ys
+        present = e_old > 0
+        res = np.max(np.abs(e_new[present] - e_old[present]) / e_old[present]) if present.any() else 0.0
+        res_out[i] = res
+        f = 0
+        if not (res <= elem_tol):
+            f = FLAG_ELEMENTS
+        else:
+            M = Cm.T @ (ys[:, None] * Cm)
+            act = np.diag(M) > 0
+            rhs = (e_old - e_new)[act]
+            Ma = M[np.ix_(act, act)]
+            try:
+                lam = np.linalg.solve(Ma, rhs)
+            except np.linalg.LinAlgError:
+                lam = np.linalg.lstsq(Ma, rhs, rcond=None)[0]
+            ys = np.maximum(ys * (1.0 + Cm[:, act] @ lam), 0.0)
+        h0 = orc.thermo_props(T[i], y)[1]
+        Tp = orc.T_from_h(h0, ys, T0=T[i])
+        Tp_out[i] = Tp
+        if not np.isfinite(Tp):
+            f |= FLAG_NONFINITE
+        elif Tp < T_min or Tp > T_max:
+            f |= FLAG_T_RANGE
+        elif dT_max > 0 and abs(Tp - T[i]) > dT_max:
+            f |= FLAG_DT
+        flags[i] = f
+        if f == 0:
+            Y_new[:, i] = ys
+            T_new[i] = Tp
+    return T_new, Y_new, flags, {"elem_residual": res_out, "T_prime": Tp_out}

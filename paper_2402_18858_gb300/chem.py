@@ -304,7 +304,8 @@ def _ann_sigs():
     L.chem_ann_set_norm.argtypes = [vp, fp]
     L.chem_ann_get_norm.argtypes = [vp, fp]
     L.chem_ann_fit_norm.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
-    L.chem_ann_features.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+    L.chem_ann_features.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, C.c_double, vp, vp]
+    L.chem_ann_update.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, C.POINTER(AnnOpts), vp, vp, vp]
     L.chem_ann_targets.argtypes = [vp, i64, i64, vp, vp, vp, vp]
     L.chem_ann_forward.argtypes = [vp, vp, i64, vp, vp, C.c_size_t, vp]
     L.chem_ann_train_step.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(TrainOpts), vp, vp]
@@ -404,12 +405,28 @@ def chem_ann_fit_norm(a: Ann, T, p, Y0, Y1, n: Optional[int] = None, stream=None
                                    _ptr(Y1, f64), _stream(stream)))
 
 
-def chem_ann_features(a: Ann, T, p, Y, X, bcty=None, n: Optional[int] = None, stream=None) -> None:
+def chem_ann_features(a: Ann, T, p, Y, X, bcty=None, n: Optional[int] = None, stream=None,
+                      flags=None, range_margin=0.05) -> None:
+    """Features X [n, 64] BF16; optionally raw F(Y) (bcty) and the range flags (int32 [n])."""
     ld = Y.shape[1]
     n = ld if n is None else n
     f64 = torch.float64
     _check(lib().chem_ann_features(a.handle, n, ld, _ptr(T, f64), _ptr(p, f64), _ptr(Y, f64),
-                                   _ptr(X, torch.bfloat16), _ptr(bcty, torch.float32), _stream(stream)))
+                                   _ptr(X, torch.bfloat16), _ptr(bcty, torch.float32), float(range_margin),
+                                   _ptr(flags, torch.int32), _stream(stream)))
+
+
+def chem_ann_update(a: Ann, T, p, Y, U, flags, status, idx=None, elem_tol=1e-2, T_min=250.0, T_max=3500.0,
+                    dT_max=0.0, n: Optional[int] = None, stream=None) -> None:
+    """The learned step's update on given network outputs U; flags in (range bit) / out."""
+    ld = _ld(Y, a.mech)
+    if n is None:
+        n = idx.numel() if idx is not None else ld
+    o = AnnOpts(0.0, elem_tol, T_min, T_max, dT_max, 1, 0, DiOpts(0.0, 0.0, 0.0, 0.0, 0, 0))
+    _check(lib().chem_ann_update(a.handle, n, ld, _ptr(T, torch.float64), _ptr(p, torch.float64),
+                                 _ptr(Y, torch.float64), _ptr(U, torch.float32), _ptr(idx, torch.int32),
+                                 C.byref(o), _ptr(flags, torch.int32), _ptr(status, torch.int32),
+                                 _stream(stream)))
 
 
 def chem_ann_targets(a: Ann, Y0, Y1, U, n: Optional[int] = None, stream=None) -> None:

@@ -216,6 +216,7 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
       const float T0 = (float)T[i];
       // enthalpy of the old state (FP32 NASA-7 sums) and old element moles
       float h0 = 0.0f, ysum = 0.0f;
+      bool finite = true;
       const int hi0 = T0 >= (float)m.Tmid ? 1 : 0;
       for (int k = 0; k < K; ++k) {
         const double y = Y[(size_t)k * ld + i];
@@ -225,12 +226,13 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
         h0 += (float)(y * m.invW[k]) * hRT;
         for (int e = 0; e < E; ++e) eo[e] += (float)(y * m.compW[(size_t)k * E + e]);
         const float z = bct_f(y) + U[(size_t)slot * n_out_pad + k] * out_sd[k] + out_mean[k];
+        finite = finite && isfinite(z);   // ibct_f would map a NaN to 0 (fmaxf)
         const float v = ibct_f(z);
         yn[k] = v;
         ysum += v;
       }
       h0 *= T0;   // h/R per kg
-      if (!(ysum > 0.0f) || !isfinite(ysum)) flag |= 2;
+      if (!finite || !(ysum > 0.0f) || !isfinite(ysum)) flag |= 2;
       if (!flag) {
         const float is = 1.0f / ysum;
         for (int k = 0; k < K; ++k) {
@@ -546,6 +548,15 @@ double normal01(uint64_t& s) {
   return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
 }
 
+// defaults of the learned step's options (chem_ann_opts fields <= 0 or NaN select them)
+void ann_fill_defaults(chem_ann_opts& o) {
+  if (!(o.range_margin >= 0)) o.range_margin = 0.05;
+  if (!(o.elem_tol > 0)) o.elem_tol = 1e-2;
+  if (!(o.T_min > 0)) o.T_min = 250.0;
+  if (!(o.T_max > 0)) o.T_max = 3500.0;
+  di_fill_defaults(o.di);
+}
+
 int check_ann(chem_ann a) {
   if (!a || !a->dmem) return set_error(CHEM_E_ARG, "null or freed ANN handle");
   int dev = -1;
@@ -779,14 +790,35 @@ int chem_ann_fit_norm(chem_ann a, int64_t n, int64_t ld, const double* T, const 
 }
 
 int chem_ann_features(chem_ann a, int64_t n, int64_t ld, const double* T, const double* p, const double* Y, void* X,
-                      float* bcty, chem_stream stream) {
+                      float* bcty, double range_margin, int32_t* flags, chem_stream stream) {
   int rc = check_ann(a);
   if (rc) return rc;
   if (n < 0 || ld < n || (n > 0 && (!T || !p || !Y || !X))) return set_error(CHEM_E_ARG, "chem_ann_features: bad arguments");
+  if (flags && !(range_margin >= 0.0)) return set_error(CHEM_E_ARG, "chem_ann_features: range_margin must be >= 0");
   if (n == 0) return CHEM_OK;
-  features_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, ld, T, p, Y, a->n_in, a->norm, 0.0f,
-                                                                     (bf16*)X, nullptr, bcty, a->K, nullptr);
+  features_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, ld, T, p, Y, a->n_in, a->norm,
+                                                                     (float)range_margin, (bf16*)X, flags, bcty,
+                                                                     a->K, nullptr);
   return cuda_check(cudaGetLastError(), "features_kernel launch");
+}
+
+int chem_ann_update(chem_ann a, int64_t n, int64_t ld, double* T, const double* p, double* Y, const float* U,
+                    const int32_t* idx, const chem_ann_opts* opts, int32_t* flags, int32_t* status,
+                    chem_stream stream) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (n < 0 || ld < n) return set_error(CHEM_E_ARG, "chem_ann_update: need 0 <= n <= ld");
+  if (n == 0) return CHEM_OK;
+  if (!T || !p || !Y || !U || !flags || !status) return set_error(CHEM_E_ARG, "chem_ann_update: null array");
+  chem_ann_opts o{};
+  if (opts) o = *opts;
+  ann_fill_defaults(o);
+  const float* om = a->norm + 4 * a->n_in;
+  update_kernel<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(a->dm, n, ld, T, p, Y, U, a->n_out_pad, om,
+                                                                   om + a->n_out, flags, status, (float)o.elem_tol,
+                                                                   (float)o.T_min, (float)o.T_max, (float)o.dT_max,
+                                                                   idx);
+  return cuda_check(cudaGetLastError(), "update_kernel launch");
 }
 
 int chem_ann_targets(chem_ann a, int64_t n, int64_t ld, const double* Y0, const double* Y1, float* U,
@@ -921,11 +953,7 @@ int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, 
     return set_error(CHEM_E_WORKSPACE, "chem_step_ann: workspace smaller than chem_ann_workspace_bytes()");
   chem_ann_opts o{};
   if (opts) o = *opts;
-  if (!(o.range_margin >= 0)) o.range_margin = 0.05;
-  if (!(o.elem_tol > 0)) o.elem_tol = 1e-2;
-  if (!(o.T_min > 0)) o.T_min = 250.0;
-  if (!(o.T_max > 0)) o.T_max = 3500.0;
-  di_fill_defaults(o.di);
+  ann_fill_defaults(o);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t mc = std::min<int64_t>(n, infer_chunk(a));
   char* w = (char*)workspace;

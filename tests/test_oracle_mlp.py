@@ -222,3 +222,23 @@ def test_per_species_backward_against_finite_differences():
         e[i] = 1e-6
         fd[i] = (L(flat + e) - L(flat - e)) / 2e-6
     assert np.allclose(g, fd, rtol=1e-5, atol=1e-9)
+
+
+def test_bf16_emulated_backward_is_the_backward_within_rounding():
+    """The BF16-storage emulation changes the gradients only by storage rounding: against the
+    unemulated backward on the same (emulated) forward, each entry stays within 2^-7 of the
+    sum of its terms' magnitudes per rounded layer passed."""
+    rng = np.random.default_rng(4)
+    dims = [9, 24, 16, 5]
+    params = _tiny(rng, dims)
+    X = rng.standard_normal((64, dims[0]))
+    U, cache = mlp.forward(params, X, bf16=True)
+    dU = rng.standard_normal(U.shape)
+    g0, d0 = mlp.backward(params, cache, dU, with_deltas=True)
+    g1, d1 = mlp.backward(params, cache, dU, bf16=True, with_deltas=True)
+    acts = cache[0]
+    for l in range(len(dims) - 1):
+        depth = len(dims) - 1 - l                  # rounding stages above and at layer l
+        bound = depth * 2 ** -7 * (np.abs(d0[l]).T @ np.abs(acts[l])) * 4
+        assert (np.abs(g1[l][0] - g0[l][0]) <= bound + 1e-300).all(), l
+        assert not np.array_equal(g1[l][0], g0[l][0])           # the emulation does something
