@@ -220,6 +220,32 @@ int chem_ann_hrr_coeffs(chem_ann ann, int64_t n, int64_t ld, const double* T0, c
 int chem_ann_train_step(chem_ann ann, const void* X, const float* Ut, const float* bcty,
                         const float* hrr_c, const float* hrr_r, int64_t B,
                         const chem_train_opts* opts, float* loss_out, chem_stream stream);
+/* One training epoch over n_samples rows (X [n, 64] BF16, Ut [n, n_out_pad], bcty [n, K]
+ * (NULL unless w_mass or w_hrr != 0), hrr_c [n, K] and hrr_r [n] (NULL unless w_hrr != 0),
+ * all device arrays): the rows are visited in a seeded random order -- a permutation of
+ * 0..n-1 drawn per (seed, epoch) on the device, no table -- in floor(n / batch) minibatches,
+ * each gathered into library-owned buffers and taken through chem_ann_train_step's
+ * optimisation step, with the learning rate on a cosine schedule
+ *   lr(t) = lr_min + (lr - lr_min) (1 + cos(pi t / (total_steps - 1))) / 2,
+ * t = step0 + the step's index in the epoch (clamped to total_steps - 1).  The paper trains
+ * its networks with Adam on the loss of Eqs. 8-11 over 1600 epochs (Sec. 2.2, Sec. 4).
+ * loss_out (device, nullable) receives the epoch means of {L_tot, L_data, L_mass, L_HRR}.
+ * Rows beyond the last full minibatch are not visited in this epoch (they are in others, the
+ * order changing per epoch). */
+typedef struct {
+  chem_train_opts step;   /* Adam and loss weights; step.lr is the schedule's peak */
+  int64_t batch;          /* minibatch rows, a multiple of 8 in [8, 2^20], <= n_samples */
+  float lr_min;           /* end of the cosine schedule */
+  int64_t total_steps;    /* schedule length over all epochs (<= 0: this epoch's steps) */
+  int64_t step0;          /* schedule position of this epoch's first step */
+  uint64_t seed;          /* minibatch order: one permutation per (seed, epoch) */
+  int epoch;
+  int reserved;
+} chem_train_epoch_opts;
+int chem_ann_train_epoch(chem_ann ann, const void* X, const float* Ut, const float* bcty,
+                         const float* hrr_c, const float* hrr_r, int64_t n_samples,
+                         const chem_train_epoch_opts* opts, float* loss_out, chem_stream stream);
+
 /* Flat FP32 parameters (which = 0) or last gradients (which = 1), per layer W [out, in] then b
  * (per-species networks: W [K out, in] and b [K out], stacked by species). */
 int chem_ann_get_params(chem_ann ann, int which, float* host, int64_t count);
@@ -417,6 +443,10 @@ int chem_selftest_gemm_grouped(int epi, int G, int M, int N, int K, const void* 
                                const float* bias, int bias_goff, const void* z, int64_t ldz,
                                int64_t z_goff, void* out, int64_t ldo, int64_t out_goff, int* err,
                                chem_stream stream);
+
+/* Testing hook: order[i] = the row chem_ann_train_epoch visits at position i of the epoch
+ * (seed, epoch) over n rows, a permutation of 0..n-1.  Device pointer, 1 <= n <= 2^31 - 1. */
+int chem_selftest_epoch_order(int64_t n, uint64_t seed, int epoch, int32_t* order, chem_stream stream);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* chem_last_error(void);

@@ -285,6 +285,11 @@ class AnnOpts(C.Structure):
                 ("reserved", C.c_int), ("di", DiOpts)]
 
 
+class TrainEpochOpts(C.Structure):
+    _fields_ = [("step", TrainOpts), ("batch", C.c_int64), ("lr_min", C.c_float), ("total_steps", C.c_int64),
+                ("step0", C.c_int64), ("seed", C.c_uint64), ("epoch", C.c_int), ("reserved", C.c_int)]
+
+
 _ann_sigs_done = False
 
 
@@ -309,6 +314,8 @@ def _ann_sigs():
     L.chem_ann_targets.argtypes = [vp, i64, i64, vp, vp, vp, vp]
     L.chem_ann_forward.argtypes = [vp, vp, i64, vp, vp, C.c_size_t, vp]
     L.chem_ann_train_step.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(TrainOpts), vp, vp]
+    L.chem_ann_train_epoch.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(TrainEpochOpts), vp, vp]
+    L.chem_selftest_epoch_order.argtypes = [i64, C.c_uint64, i32, vp, vp]
     L.chem_ann_hrr_coeffs.argtypes = [vp, i64, i64, vp, vp, vp, vp, C.c_double, C.c_double, vp, vp, vp]
     L.chem_ann_get_params.argtypes = [vp, i32, fp, i64]
     L.chem_ann_set_params.argtypes = [vp, fp, i64]
@@ -460,6 +467,28 @@ def chem_ann_train_step(a: Ann, X, Ut, bcty=None, lr=1e-3, beta1=0.9, beta2=0.99
                                      _ptr(bcty, torch.float32), _ptr(hrr_c, torch.float32),
                                      _ptr(hrr_r, torch.float32), X.shape[0], C.byref(o),
                                      _ptr(loss_out, torch.float32), _stream(stream)))
+
+
+def chem_ann_train_epoch(a: Ann, X, Ut, bcty=None, batch=8192, lr=1e-3, lr_min=2e-5, total_steps=0, step0=0,
+                         seed=0, epoch=0, beta1=0.9, beta2=0.999, eps=1e-8, w_data=1.0, w_mass=0.1,
+                         hrr_c=None, hrr_r=None, w_hrr=0.0, loss_out=None, n: Optional[int] = None,
+                         stream=None) -> None:
+    """One epoch in a seeded minibatch order with the cosine schedule; loss_out gets the epoch means."""
+    if loss_out is not None and loss_out.numel() < 4:
+        raise ValueError("loss_out needs 4 floats")
+    n = X.shape[0] if n is None else n
+    step = TrainOpts(lr, beta1, beta2, eps, w_data, w_mass if bcty is not None else 0.0, 1, float(w_hrr))
+    o = TrainEpochOpts(step, int(batch), float(lr_min), int(total_steps), int(step0), int(seed), int(epoch), 0)
+    _check(lib().chem_ann_train_epoch(a.handle, _ptr(X, torch.bfloat16), _ptr(Ut, torch.float32),
+                                      _ptr(bcty, torch.float32), _ptr(hrr_c, torch.float32),
+                                      _ptr(hrr_r, torch.float32), int(n), C.byref(o),
+                                      _ptr(loss_out, torch.float32), _stream(stream)))
+
+
+def chem_selftest_epoch_order(n: int, seed: int, epoch: int, order, stream=None) -> None:
+    _ann_sigs()
+    _check(lib().chem_selftest_epoch_order(int(n), int(seed), int(epoch), _ptr(order, torch.int32),
+                                           _stream(stream)))
 
 
 def chem_ann_hrr_coeffs(a: Ann, dt: float, scale: float, T0, p, Y0, Y1, hrr_c, hrr_r, n: Optional[int] = None,

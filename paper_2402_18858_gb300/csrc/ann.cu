@@ -210,9 +210,14 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
     const int64_t i = idx ? (int64_t)idx[slot] : slot;   // cell column; U, flags, status by slot
     int flag = flags[slot];
     if (flag == 0) {
-      float yn[CHEM_MAX_SPECIES];
+      float yn[CHEM_MAX_SPECIES];    // prediction (inverse Box-Cox, renormalised)
+      float yp[CHEM_MAX_SPECIES];    // the state T' is solved for: projected, or yn when flagged
       float eo[kMaxElem], en[kMaxElem];
-      for (int e = 0; e < E; ++e) eo[e] = en[e] = 0.0f;
+      double eod[kMaxElem], lam[kMaxElem];
+      for (int e = 0; e < E; ++e) {
+        eo[e] = en[e] = 0.0f;
+        eod[e] = lam[e] = 0.0;
+      }
       const float T0 = (float)T[i];
       // enthalpy of the old state (FP32 NASA-7 sums) and old element moles
       float h0 = 0.0f, ysum = 0.0f;
@@ -224,7 +229,11 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
         const float hRT = (float)a[5] + T0 * ((float)a[6] + T0 * ((float)a[7] + T0 * ((float)a[8] + T0 * (float)a[9])))
                           + (float)a[10] / T0;
         h0 += (float)(y * m.invW[k]) * hRT;
-        for (int e = 0; e < E; ++e) eo[e] += (float)(y * m.compW[(size_t)k * E + e]);
+        for (int e = 0; e < E; ++e) {
+          const double c = y * m.compW[(size_t)k * E + e];
+          eod[e] += c;
+          eo[e] += (float)c;
+        }
         const float z = bct_f(y) + U[(size_t)slot * n_out_pad + k] * out_sd[k] + out_mean[k];
         finite = finite && isfinite(z);   // ibct_f would map a NaN to 0 (fmaxf)
         const float v = ibct_f(z);
@@ -246,43 +255,50 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
         if (!flag) {
           // accepted: project onto exact element conservation, min sum_k dY_k^2 / w_k with
           // w_k = Y_k subject to sum_k c_ke (Y_k + dY_k) = E_old_e (c = composition / W):
-          // dY = diag(w) C^T lam, (C diag(w) C^T) lam = E_old - C Y
-          float Mx[kMaxElem][kMaxElem + 1];
+          // dY = diag(w) C^T lam, (C diag(w) C^T) lam = E_old - C Y.  In FP64: the E x E system
+          // can be ill-conditioned (an element carried mostly by one abundant species), and
+          // the projected state conserves the elements to FP64 rounding.
+          double Mx[kMaxElem][kMaxElem + 1];
           for (int a1 = 0; a1 < E; ++a1) {
-            for (int a2 = 0; a2 < E; ++a2) Mx[a1][a2] = 0.0f;
-            Mx[a1][E] = eo[a1] - en[a1];
+            for (int a2 = 0; a2 <= E; ++a2) Mx[a1][a2] = 0.0;
+            Mx[a1][E] = eod[a1];
           }
           for (int k = 0; k < K; ++k) {
-            const float wk = yn[k];
+            const double wk = (double)yn[k];
             for (int a1 = 0; a1 < E; ++a1) {
-              const float c1 = (float)m.compW[(size_t)k * E + a1] * wk;
-              for (int a2 = 0; a2 < E; ++a2) Mx[a1][a2] += c1 * (float)m.compW[(size_t)k * E + a2];
+              const double c1 = m.compW[(size_t)k * E + a1] * wk;
+              Mx[a1][E] -= c1;
+              for (int a2 = 0; a2 < E; ++a2) Mx[a1][a2] += c1 * m.compW[(size_t)k * E + a2];
             }
           }
-          // Gauss-Jordan on the E x E system; elements absent from the cell are left alone
-          float lam[kMaxElem];
-          for (int a1 = 0; a1 < E; ++a1) lam[a1] = 0.0f;
+          // Gauss-Jordan with partial pivoting; elements absent from both states have a zero
+          // row and column and keep lam = 0
+          bool live[kMaxElem];
+          for (int c = 0; c < E; ++c) live[c] = Mx[c][c] > 0.0;
           for (int c = 0; c < E; ++c) {
+            if (!live[c]) continue;
             int piv = c;
             for (int r = c + 1; r < E; ++r)
-              if (fabsf(Mx[r][c]) > fabsf(Mx[piv][c])) piv = r;
-            if (!(fabsf(Mx[piv][c]) > 1e-30f)) continue;   // element absent from the cell
+              if (live[r] && fabs(Mx[r][c]) > fabs(Mx[piv][c])) piv = r;
+            if (!(fabs(Mx[piv][c]) > 0.0)) continue;
             if (piv != c)
-              for (int j = 0; j <= E; ++j) { const float t = Mx[c][j]; Mx[c][j] = Mx[piv][j]; Mx[piv][j] = t; }
-            const float d = 1.0f / Mx[c][c];
+              for (int j = 0; j <= E; ++j) { const double t = Mx[c][j]; Mx[c][j] = Mx[piv][j]; Mx[piv][j] = t; }
+            const double d = 1.0 / Mx[c][c];
             for (int j = 0; j <= E; ++j) Mx[c][j] *= d;
             for (int r = 0; r < E; ++r) {
               if (r == c) continue;
-              const float f = Mx[r][c];
+              const double f = Mx[r][c];
               for (int j = 0; j <= E; ++j) Mx[r][j] -= f * Mx[c][j];
             }
           }
-          for (int c = 0; c < E; ++c) lam[c] = (fabsf(Mx[c][c] - 1.0f) < 1e-3f) ? Mx[c][E] : 0.0f;
+          for (int c = 0; c < E; ++c) lam[c] = (live[c] && fabs(Mx[c][c] - 1.0) < 1e-9) ? Mx[c][E] : 0.0;
           for (int k = 0; k < K; ++k) {
-            float cl = 0.0f;
-            for (int e = 0; e < E; ++e) cl += (float)m.compW[(size_t)k * E + e] * lam[e];
-            yn[k] = fmaxf(yn[k] * (1.0f + cl), 0.0f);
+            double cl = 0.0;
+            for (int e = 0; e < E; ++e) cl += m.compW[(size_t)k * E + e] * lam[e];
+            yp[k] = (float)fmax((double)yn[k] * (1.0 + cl), 0.0);
           }
+        } else {
+          for (int k = 0; k < K; ++k) yp[k] = yn[k];
         }
         // T from h(T, Y_new) = h0 by Newton's method
         float Tn = T0;
@@ -291,7 +307,7 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
           float h = 0.0f, cp = 0.0f;
           for (int k = 0; k < K; ++k) {
             const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
-            const float yw = yn[k] * (float)m.invW[k];
+            const float yw = yp[k] * (float)m.invW[k];
             const float cpR = (float)a[0] + Tn * ((float)a[1] + Tn * ((float)a[2] + Tn * ((float)a[3] + Tn * (float)a[4])));
             const float hRT = (float)a[5] + Tn * ((float)a[6] + Tn * ((float)a[7] + Tn * ((float)a[8] + Tn * (float)a[9])))
                               + (float)a[10] / Tn;
@@ -306,7 +322,12 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
         else if (Tn < Tmin || Tn > Tmax) flag |= 8;
         else if (dTmax > 0.0f && fabsf(Tn - T0) > dTmax) flag |= 16;
         if (!flag) {
-          for (int k = 0; k < K; ++k) Y[(size_t)k * ld + i] = (double)yn[k];
+          // the projected state in FP64 (accepted cells were projected)
+          for (int k = 0; k < K; ++k) {
+            double cl = 0.0;
+            for (int e = 0; e < E; ++e) cl += m.compW[(size_t)k * E + e] * lam[e];
+            Y[(size_t)k * ld + i] = fmax((double)yn[k] * (1.0 + cl), 0.0);
+          }
           T[i] = (double)Tn;
         }
       }
@@ -524,6 +545,68 @@ __global__ void to_bf16_kernel(int64_t n, int gh, int ldt, int cols, const float
   }
 }
 
+// Seeded permutation of 0..n-1 for the epoch's minibatch order, without a table: a 4-round
+// Feistel network (a bijection) on the smallest domain 2^(2 hb) >= n, with cycle walking (apply
+// it again until the value falls below n; the walk stays on the cycle through the start, so it
+// ends, on average after fewer than 4 rounds since the domain is below 4 n; the bound only keeps
+// the loop finite).  Round function: a 64-bit finaliser (splitmix64's) of (half, key, round).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int64_t epoch_perm(int64_t i, int64_t n, int hb, uint64_t key) {
+  const uint64_t mask = (1ull << hb) - 1ull;
+  uint64_t x = (uint64_t)i;
+  for (int walk = 0; walk < 4096; ++walk) {
+    uint64_t L = x >> hb, R = x & mask;
+    for (int r = 0; r < 4; ++r) {
+      const uint64_t F = mix64(R ^ (key + 0x9E3779B97F4A7C15ull * (uint64_t)(r + 1))) & mask;
+      const uint64_t t = R;
+      R = L ^ F;
+      L = t;
+    }
+    x = (L << hb) | R;
+    if (x < (uint64_t)n) return (int64_t)x;
+  }
+  return i;   // not reached for a domain below 4 n (probability < (3/4)^4096)
+}
+
+__global__ void epoch_order_kernel(int64_t n, int hb, uint64_t key, int32_t* order) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    order[i] = (int32_t)epoch_perm(i, n, hb, key);
+}
+
+// rows r0 .. r0 + B - 1 of the epoch's order gathered into contiguous minibatch buffers
+__global__ void gather_batch_kernel(int64_t n, int hb, uint64_t key, int64_t r0, int64_t B, const bf16* X,
+                                    const float* Ut, int n_out_pad, const float* bcty, const float* hc, const float* hr,
+                                    int K, bf16* Xb, float* Utb, float* bctyb, float* hcb, float* hrb) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t src = epoch_perm(r0 + b, n, hb, key);
+    const uint4* xs = (const uint4*)(X + (size_t)src * kInPad);
+    uint4* xd = (uint4*)(Xb + (size_t)b * kInPad);
+#pragma unroll
+    for (int q = 0; q < kInPad / 8; ++q) xd[q] = xs[q];
+    for (int k = 0; k < n_out_pad; ++k) Utb[(size_t)b * n_out_pad + k] = Ut[(size_t)src * n_out_pad + k];
+    if (bcty)
+      for (int k = 0; k < K; ++k) bctyb[(size_t)b * K + k] = bcty[(size_t)src * K + k];
+    if (hc) {
+      for (int k = 0; k < K; ++k) hcb[(size_t)b * K + k] = hc[(size_t)src * K + k];
+      hrb[b] = hr[src];
+    }
+  }
+}
+
+// epoch mean of the per-step losses: acc[0..3] += step[0..3] (acc zeroed first); scale at the end
+__global__ void loss_accumulate_kernel(const float* step, float* acc, float scale, int finish, float* out) {
+  if (threadIdx.x < 4 && blockIdx.x == 0) {
+    const float v = acc[threadIdx.x] + step[threadIdx.x];
+    acc[threadIdx.x] = v;
+    if (finish && out) out[threadIdx.x] = v * scale;
+  }
+}
+
 int grid_for(int64_t n, int threads) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
@@ -585,7 +668,31 @@ size_t train_bytes(const chem_ann_s* a, int64_t B) {
   }
   s += (size_t)B * kInPad * 2 + 256;   // XT
   s += (size_t)B * a->n_out_pad * 4 + 256;
+  // minibatch staging of chem_ann_train_epoch: X, Ut, bcty, hrr_c, hrr_r, loss sums
+  s += (size_t)B * kInPad * 2 + (size_t)B * a->n_out_pad * 4 + 2 * (size_t)B * a->K * 4 + (size_t)B * 4 + 6 * 256;
   return s;
+}
+
+// the staging block of chem_ann_train_epoch at the end of the training buffers
+struct EpochBufs {
+  bf16* X;
+  float *Ut, *bcty, *hc, *hr, *acc;
+};
+
+EpochBufs epoch_bufs(const chem_ann_s* a, int64_t B) {
+  const size_t stage = (size_t)B * kInPad * 2 + (size_t)B * a->n_out_pad * 4 + 2 * (size_t)B * a->K * 4 +
+                       (size_t)B * 4 + 6 * 256;
+  char* w = (char*)a->tmem_ + train_bytes(a, a->tcap) - stage;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { void* p = w + off; off = (off + bytes + 255) & ~size_t(255); return p; };
+  EpochBufs e;
+  e.X = (bf16*)take((size_t)B * kInPad * 2);
+  e.Ut = (float*)take((size_t)B * a->n_out_pad * 4);
+  e.bcty = (float*)take((size_t)B * a->K * 4);
+  e.hc = (float*)take((size_t)B * a->K * 4);
+  e.hr = (float*)take((size_t)B * 4);
+  e.acc = (float*)take(8 * sizeof(float));   // epoch sums [4], last step [4]
+  return e;
 }
 
 }  // namespace
@@ -1011,25 +1118,23 @@ int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, 
   return CHEM_OK;
 }
 
-int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float* bcty, const float* hrr_c,
-                        const float* hrr_r, int64_t B, const chem_train_opts* opts, float* loss_out,
-                        chem_stream stream) {
-  int rc = check_ann(a);
-  if (rc) return rc;
-  if (B < 8 || B > (1 << 20) || B % 8 != 0 || !Xv || !Ut || !opts)
-    return set_error(CHEM_E_ARG, "chem_ann_train_step: bad arguments (B must be a multiple of 8)");
-  if (opts->w_hrr != 0.0f && (!bcty || !hrr_c || !hrr_r))
-    return set_error(CHEM_E_ARG, "chem_ann_train_step: w_hrr != 0 needs bcty, hrr_c and hrr_r");
-  cudaStream_t s = (cudaStream_t)stream;
-  const bf16* X = (const bf16*)Xv;
-  if (B > a->tcap) {
-    if (a->tmem_) { cudaStreamSynchronize(s); cudaFree(a->tmem_); a->tmem_ = nullptr; a->tcap = 0; }
-    if (cudaMalloc(&a->tmem_, train_bytes(a, B)) != cudaSuccess) {
-      cudaGetLastError();
-      return set_error(CHEM_E_NOMEM, "chem_ann_train_step: cudaMalloc of training buffers failed");
-    }
-    a->tcap = B;
+// training buffers for minibatches of up to B rows (library-owned, grown on demand)
+static int ensure_train_bufs(chem_ann a, int64_t B, cudaStream_t s) {
+  if (B <= a->tcap) return CHEM_OK;
+  if (a->tmem_) { cudaStreamSynchronize(s); cudaFree(a->tmem_); a->tmem_ = nullptr; a->tcap = 0; }
+  if (cudaMalloc(&a->tmem_, train_bytes(a, B)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(CHEM_E_NOMEM, "chem_ann_train: cudaMalloc of training buffers failed");
   }
+  a->tcap = B;
+  return CHEM_OK;
+}
+
+// one optimisation step on a contiguous minibatch (buffers already sized for B)
+static int train_step_impl(chem_ann a, const bf16* X, const float* Ut, const float* bcty, const float* hrr_c,
+                           const float* hrr_r, int64_t B, const chem_train_opts* opts, float* loss_out,
+                           cudaStream_t s) {
+  int rc;
   // carve training buffers
   TrainBufs t{};
   char* w = (char*)a->tmem_;
@@ -1123,7 +1228,10 @@ int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float
   if (!opts->apply) return CHEM_OK;
   // Adam
   a->step++;
-  const float bc1 = 1.0f - std::pow(opts->beta1, (float)a->step), bc2 = 1.0f - std::pow(opts->beta2, (float)a->step);
+  // bias corrections 1 - beta^t in FP64: in FP32, 1 - 0.999^t loses most of its digits to
+  // cancellation for small t
+  const float bc1 = (float)(1.0 - std::pow((double)opts->beta1, (double)a->step));
+  const float bc2 = (float)(1.0 - std::pow((double)opts->beta2, (double)a->step));
   for (int l = 0; l < a->L; ++l) {
     const int rows = rows_of(a, l), cols = a->dims[l];
     const int64_t nw = (int64_t)rows * cols;
@@ -1134,6 +1242,80 @@ int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float
                                                     opts->beta1, opts->beta2, opts->eps, bc1, bc2, nullptr, nullptr);
   }
   return cuda_check(cudaGetLastError(), "adam launch");
+}
+
+int chem_ann_train_step(chem_ann a, const void* Xv, const float* Ut, const float* bcty, const float* hrr_c,
+                        const float* hrr_r, int64_t B, const chem_train_opts* opts, float* loss_out,
+                        chem_stream stream) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (B < 8 || B > (1 << 20) || B % 8 != 0 || !Xv || !Ut || !opts)
+    return set_error(CHEM_E_ARG, "chem_ann_train_step: bad arguments (B must be a multiple of 8)");
+  if (opts->w_hrr != 0.0f && (!bcty || !hrr_c || !hrr_r))
+    return set_error(CHEM_E_ARG, "chem_ann_train_step: w_hrr != 0 needs bcty, hrr_c and hrr_r");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = ensure_train_bufs(a, B, s))) return rc;
+  return train_step_impl(a, (const bf16*)Xv, Ut, bcty, hrr_c, hrr_r, B, opts, loss_out, s);
+}
+
+// key of the minibatch order of (seed, epoch)
+static uint64_t epoch_key(uint64_t seed, int epoch) {
+  uint64_t st = seed * 0x9E3779B97F4A7C15ull ^ ((uint64_t)(uint32_t)epoch << 32);
+  return splitmix64(st);
+}
+
+// half-width of the permutation domain: the smallest hb with 2^(2 hb) >= n
+static int epoch_half_bits(int64_t n) {
+  int hb = 1;
+  while ((1ll << (2 * hb)) < n) ++hb;
+  return hb;
+}
+
+int chem_ann_train_epoch(chem_ann a, const void* Xv, const float* Ut, const float* bcty, const float* hrr_c,
+                         const float* hrr_r, int64_t n, const chem_train_epoch_opts* opts, float* loss_out,
+                         chem_stream stream) {
+  int rc = check_ann(a);
+  if (rc) return rc;
+  if (!opts || !Xv || !Ut) return set_error(CHEM_E_ARG, "chem_ann_train_epoch: null argument");
+  const int64_t B = opts->batch;
+  if (B < 8 || B > (1 << 20) || B % 8 != 0 || n < B || n > (int64_t)0x7fffffff)
+    return set_error(CHEM_E_ARG, "chem_ann_train_epoch: need a batch that is a multiple of 8 in [8, 2^20] and "
+                                 "batch <= n_samples <= 2^31 - 1");
+  if (opts->step.w_hrr != 0.0f && (!bcty || !hrr_c || !hrr_r))
+    return set_error(CHEM_E_ARG, "chem_ann_train_epoch: w_hrr != 0 needs bcty, hrr_c and hrr_r");
+  if (opts->step.w_mass != 0.0f && !bcty)
+    return set_error(CHEM_E_ARG, "chem_ann_train_epoch: w_mass != 0 needs bcty");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = ensure_train_bufs(a, B, s))) return rc;
+  const EpochBufs eb = epoch_bufs(a, B);
+  const int64_t steps = n / B;
+  const int64_t total = opts->total_steps > 0 ? opts->total_steps : steps;
+  const int hb = epoch_half_bits(n);
+  const uint64_t key = epoch_key(opts->seed, opts->epoch);
+  const bool with_hrr = opts->step.w_hrr != 0.0f;
+  if ((rc = cuda_check(cudaMemsetAsync(eb.acc, 0, 4 * sizeof(float), s), "chem_ann_train_epoch: loss sums"))) return rc;
+  float* step_loss = eb.acc + 4;
+  for (int64_t q = 0; q < steps; ++q) {
+    gather_batch_kernel<<<grid_for(B, 128), 128, 0, s>>>(n, hb, key, q * B, B, (const bf16*)Xv, Ut, a->n_out_pad, bcty,
+                                                        with_hrr ? hrr_c : nullptr, with_hrr ? hrr_r : nullptr, a->K,
+                                                        eb.X, eb.Ut, eb.bcty, eb.hc, eb.hr);
+    // cosine learning rate over the whole schedule
+    chem_train_opts o = opts->step;
+    const double t = std::min(1.0, (double)(opts->step0 + q) / (double)std::max<int64_t>(total - 1, 1));
+    o.lr = (float)(opts->lr_min + 0.5 * ((double)opts->step.lr - opts->lr_min) * (1.0 + std::cos(M_PI * t)));
+    if ((rc = train_step_impl(a, eb.X, eb.Ut, bcty ? eb.bcty : nullptr, with_hrr ? eb.hc : nullptr,
+                              with_hrr ? eb.hr : nullptr, B, &o, step_loss, s)))
+      return rc;
+    loss_accumulate_kernel<<<1, 32, 0, s>>>(step_loss, eb.acc, 1.0f / (float)steps, q == steps - 1 ? 1 : 0, loss_out);
+  }
+  return cuda_check(cudaGetLastError(), "chem_ann_train_epoch launches");
+}
+
+int chem_selftest_epoch_order(int64_t n, uint64_t seed, int epoch, int32_t* order, chem_stream stream) {
+  if (n < 1 || n > (int64_t)0x7fffffff || !order) return set_error(CHEM_E_ARG, "chem_selftest_epoch_order: bad arguments");
+  epoch_order_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, epoch_half_bits(n), epoch_key(seed, epoch),
+                                                                        order);
+  return cuda_check(cudaGetLastError(), "epoch_order_kernel launch");
 }
 
 // parameters/gradients as one flat FP32 host array: per layer W [rows, dims[l]] then b [rows]

@@ -111,35 +111,28 @@ def prepare(ann, data, fit: bool = True, dt: Optional[float] = None):
 
 
 def train(ann, X, bcty, U, epochs: int = 20, batch: int = 8192, lr: float = 1e-3, lr_min: float = 2e-5,
-          w_data: float = 1.0, w_mass: float = 0.1, log_every: int = 0, hrr=None, w_hrr: float = 0.0) -> Dict:
-    """Adam over minibatches (contiguous slices, offset each epoch), cosine learning rate."""
-    n = X.shape[0] - X.shape[0] % 8
+          w_data: float = 1.0, w_mass: float = 0.1, hrr=None, w_hrr: float = 0.0, seed: int = 0) -> Dict:
+    """Adam over `epochs` calls of chem_ann_train_epoch (a seeded minibatch order per epoch,
+    cosine learning rate over the whole run); the loss history holds each epoch's mean L_data."""
+    n = X.shape[0]
     batch = min(batch, n) - min(batch, n) % 8
-    steps_per_epoch = max(1, n // batch)
+    steps_per_epoch = n // batch
     total = epochs * steps_per_epoch
     loss = torch.zeros(4, dtype=torch.float32, device=X.device)
+    use_hrr = hrr is not None and w_hrr != 0.0
     hist = []
     t0 = time.perf_counter()
-    step = 0
     for e in range(epochs):
-        off = (e * 7919 * 8) % max(n - batch * steps_per_epoch + 1, 1)
-        for s in range(steps_per_epoch):
-            a = off + s * batch
-            cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / max(total - 1, 1)))
-            hc = hrr[0][a:a + batch] if hrr is not None and w_hrr != 0.0 else None
-            hr = hrr[1][a:a + batch] if hrr is not None and w_hrr != 0.0 else None
-            chem.chem_ann_train_step(ann, X[a:a + batch], U[a:a + batch], bcty[a:a + batch], lr=cur,
-                                     w_data=w_data, w_mass=w_mass, loss_out=loss, hrr_c=hc, hrr_r=hr,
-                                     w_hrr=w_hrr if hrr is not None else 0.0)
-            step += 1
-            if log_every and step % log_every == 0:
-                hist.append((step, float(loss[1].item())))
-        hist.append((step, float(loss[1].item())))
+        chem.chem_ann_train_epoch(ann, X, U, bcty, batch=batch, lr=lr, lr_min=lr_min, total_steps=total,
+                                  step0=e * steps_per_epoch, seed=seed, epoch=e, w_data=w_data, w_mass=w_mass,
+                                  hrr_c=hrr[0] if use_hrr else None, hrr_r=hrr[1] if use_hrr else None,
+                                  w_hrr=w_hrr if use_hrr else 0.0, loss_out=loss)
+        hist.append(((e + 1) * steps_per_epoch, float(loss[1].item())))
     torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
     if chem.chem_ann_error(ann) != 0:
         raise RuntimeError("tensor-core pipeline timed out during training")
-    return dict(steps=step, seconds=time.perf_counter() - t0, loss_history=hist,
-                samples_per_s=step * batch / (time.perf_counter() - t0))
+    return dict(steps=total, seconds=secs, loss_history=hist, samples_per_s=total * batch / secs)
 
 
 def errors(T, Y, Tref, Yref, ok=None) -> Dict:
@@ -245,7 +238,7 @@ def main():
     else:
         X, bcty, U = prepare(ann, data)
     del data
-    tr = train(ann, X, bcty, U, epochs=args.epochs, batch=args.batch, lr=args.lr, log_every=500,
+    tr = train(ann, X, bcty, U, epochs=args.epochs, batch=args.batch, lr=args.lr,
                hrr=hrr, w_hrr=args.w_hrr)
     if args.out:
         chem.chem_ann_save(ann, args.out, with_moments=args.with_moments)

@@ -108,9 +108,10 @@ def test_gradient_parity(lc, setup):
 
 def test_adam_steps_against_oracle(lc, setup):
     """Two Adam steps of the GPU (FP32 masters and moments) against oracle.mlp.adam_step fed
-    the GPU's own gradients and the same FP32 hyper-parameters: equal to FP32 rounding
-    (a few units in the last place of the weight and of its change); the BF16 weight copies
-    the next forward reads follow the masters."""
+    the GPU's own gradients and the same FP32 hyper-parameters: equal to FP32 rounding (a few
+    units in the last place of the weight and of its change, plus the rounding of the moments'
+    sums carried through m / sqrt(v)); the BF16 weight copies the next forward reads follow
+    the masters."""
     gm, ann0, st, X, bcty, U = setup
     ann = lc.chem_ann_create(gm, HIDDEN, seed=21)
     lc.chem_ann_set_norm(ann, lc.chem_ann_get_norm(ann0))
@@ -127,9 +128,17 @@ def test_adam_steps_against_oracle(lc, setup):
         torch.cuda.synchronize()
         g = lc.chem_ann_get_params(ann, which=1).astype(np.float64)
         p_gpu = lc.chem_ann_get_params(ann).astype(np.float64)
+        # FP32 error of the update: the moments' sums can cancel (m = b1 m + (1 - b1) g with
+        # g of the opposite sign), so their error is eps32 times the terms' magnitudes
+        e32 = float(np.finfo(np.float32).eps)
+        bc1, bc2 = 1 - b1 ** t, 1 - b2 ** t
+        Em = 4 * e32 * (np.abs(b1 * m) + np.abs((1 - b1) * g)) / bc1
+        Ev = 4 * e32 * (b2 * v + (1 - b2) * g * g) / bc2
         p_or, m, v = mlp.adam_step(p, g, m, v, t, lr, b1, b2, eps)
+        sv = np.sqrt(v / bc2)
+        dupd = lr * (Em / (sv + eps) + np.abs(m / bc1) * Ev / (2 * np.maximum(sv, 1e-300) * (sv + eps) ** 2))
         ulp = np.spacing(np.abs(p_or).astype(np.float32)).astype(np.float64)
-        bound = 4 * ulp + 16 * float(np.finfo(np.float32).eps) * np.abs(p_or - p)
+        bound = 4 * ulp + 8 * e32 * np.abs(p_or - p) + dupd
         assert (np.abs(p_gpu - p_or) <= bound).all(), (t, np.abs(p_gpu - p_or).max())
         assert (np.abs(p_or - p) > 0.5 * lr).mean() > 0.5          # the step moved the weights
         p = p_gpu
@@ -279,3 +288,51 @@ def test_forward_full_size_sampled(lc, setup, mechs):
     d = Ug[torch.as_tensor(pick, device=dev)].cpu().numpy() - Uo
     assert np.abs(d).max() <= 2e-3 * np.abs(Uo).max() + 1e-3
     assert np.sqrt((d ** 2).mean()) <= 1e-3 * np.sqrt((Uo ** 2).mean())
+
+
+def test_train_epoch_is_the_shuffled_sequence_of_steps(lc, setup):
+    """chem_ann_train_epoch: a seeded permutation per epoch (exact integer check), and the
+    epoch equals the same minibatches taken through chem_ann_train_step with the cosine
+    learning rate, bit for bit; its loss is the mean of the steps' losses."""
+    import math
+    gm, ann0, st, X, bcty, U = setup
+    n, B = 2000, 256                     # 7 full minibatches; 208 rows not visited this epoch
+    dev = torch.device("cuda")
+    orders = {}
+    for seed, ep in ((5, 0), (5, 1), (6, 0), (5, 0)):
+        o = torch.empty(n, dtype=torch.int32, device=dev)
+        lc.chem_selftest_epoch_order(n, seed, ep, o)
+        torch.cuda.synchronize()
+        a = o.cpu().numpy()
+        assert np.array_equal(np.sort(a), np.arange(n))
+        if (seed, ep) in orders:
+            assert np.array_equal(orders[(seed, ep)], a)
+        orders[(seed, ep)] = a
+    assert not np.array_equal(orders[(5, 0)], orders[(5, 1)])
+    assert not np.array_equal(orders[(5, 0)], orders[(6, 0)])
+    assert not np.array_equal(orders[(5, 0)], np.arange(n))
+
+    f32 = lambda v: float(np.float32(v))
+    lr, lr_min, total, step0 = f32(1e-3), f32(1e-4), 20, 3
+    a1 = lc.chem_ann_create(gm, [64, 32], seed=31)
+    a2 = lc.chem_ann_create(gm, [64, 32], seed=31)
+    for a in (a1, a2):
+        lc.chem_ann_set_norm(a, lc.chem_ann_get_norm(ann0))
+    Xs, Us, bs = X[:n].contiguous(), U[:n].contiguous(), bcty[:n].contiguous()
+    loss = torch.zeros(4, dtype=torch.float32, device=dev)
+    lc.chem_ann_train_epoch(a1, Xs, Us, bs, batch=B, lr=lr, lr_min=lr_min, total_steps=total, step0=step0,
+                            seed=5, epoch=1, loss_out=loss)
+    order = torch.as_tensor(orders[(5, 1)].astype(np.int64), device=dev)
+    step_loss = torch.zeros(4, dtype=torch.float32, device=dev)
+    losses = []
+    for q in range(n // B):
+        rows = order[q * B:(q + 1) * B]
+        t = min(1.0, (step0 + q) / (total - 1))
+        cur = f32(lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * t)))
+        lc.chem_ann_train_step(a2, Xs[rows].contiguous(), Us[rows].contiguous(), bs[rows].contiguous(), lr=cur,
+                               loss_out=step_loss)
+        losses.append(step_loss.cpu().numpy().copy())
+    torch.cuda.synchronize()
+    assert lc.chem_ann_error(a1) == 0 and lc.chem_ann_error(a2) == 0
+    assert np.array_equal(lc.chem_ann_get_params(a1), lc.chem_ann_get_params(a2))
+    assert np.allclose(loss.cpu().numpy(), np.mean(losses, axis=0), rtol=1e-5, atol=0)
