@@ -33,7 +33,26 @@ METRIC = "chem-step cells/s: GPU DI vs ANN+fallback at stated err; serve p50/p99
 WORKLOAD = "di_c_30sp_1m"
 DI_RTOL = 1e-9           # library defaults (rtol 1e-9, atol_Y 1e-18, Newton 0.1): what the parity tests validate
 MECH_DIR = os.path.join(tempfile.gettempdir(), "chem_bench_mech")
-EXP_FLOPS = 20           # flop convention for exp/log/log10/pow in the algorithmic count
+# FP64 flops of one exponential and one logarithm: those of the kernels' table-driven exp
+# (7 FMAs + 2 other FP64 operations) and log (8 FMAs + 5 others), FMA = 2
+EXP_FLOPS = 16
+LOG_FLOPS = 21
+ORACLE_ERR_RTOL = 1e-8   # oracle tolerance for the learned step's error reference (far below its error)
+
+
+def load_peaks() -> dict:
+    """Roofline denominators: the measured figures of MEASURED_PEAKS.json, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "of measured (MEASURED_PEAKS.json)"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "of fallback"}
+
+
+PEAKS = load_peaks()
 # DRAM bytes of one di_kernel launch per cell, from an 8,202-cell ncu capture of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum = 2,973,440 + 0 B; the written state
 # stayed in L2 there), scaled to a launch by the cells processed
@@ -46,8 +65,9 @@ DI_DRAM_BYTES_PER_CELL = 2973440 / 8202
 def di_flop_model(m: wl.Mechanism) -> dict:
     """FP64 flops of one RHS, one Jacobian, one LU and one Newton solve for this mechanism.
 
-    Conventions: add/mul = 1, fma = 2, division = 1, exp/log = EXP_FLOPS.  Counts follow the
-    textbook formulas (NASA-7, Arrhenius, K_c, Troe, Eq. 1 and its analytic Jacobian).
+    Conventions: add/mul = 1, fma = 2, division = 1, exp = EXP_FLOPS, log = LOG_FLOPS (the
+    FP64 operations of the kernels' own exp and log).  Counts follow the textbook formulas
+    (NASA-7, Arrhenius, K_c, Troe, Eq. 1 and its analytic Jacobian).
     """
     K, n = m.n_species, m.n_species + 1
     E = len(m.elements)
@@ -57,17 +77,22 @@ def di_flop_model(m: wl.Mechanism) -> dict:
     for r in m.reactions:
         nr, npd = len(r.reactants), len(r.products)
         nnz += len(set(r.reactants) | set(r.products))
-        c = 4 + EXP_FLOPS               # k_f
+        c = 4 + EXP_FLOPS               # k_f = exp(ln A + b ln T - Ea/RT)
         c += (nr + npd) + 2             # 1/K_c from per-species exp(-g/RT) products, (p0/RT)^dnu
         c += (nr - 1) + (npd - 1) + 3   # concentration products, q
         if r.kind >= 1:
             c += 2 + 2 * len(r.eff)     # [M]
         if r.kind == 2:
-            c += 6 * EXP_FLOPS + 40     # Troe: k0, 2-3 exps, 2 log10, exp10, algebra
+            # Troe: k0/k_inf and F_cent's two or three exponentials, log10 F_cent and log10 P_r,
+            # F = 10^(...), and the algebra (F_cent, P_r, c, n, x, the two divisions, k)
+            n_exp = 1 + (len(r.troe) - 1) + 1
+            c += n_exp * (EXP_FLOPS + 2) + 2 * (LOG_FLOPS + 1) + 40
         rx += c
         # Jacobian extras: dq/dC terms per species of the reaction, d/dT terms
         jx += 2 * (nr * nr + npd * npd) + 12 + (30 if r.kind == 2 else 0)
-    species = K * (8 + 10 + 10 + 1 + 2 + 4 + 2 * E + EXP_FLOPS + 1) + EXP_FLOPS + 10
+    # per species: NASA-7 c_p, h, s and dc_p/dT, g/RT, exp(-g/RT), concentration, element
+    # terms; per cell: ln T and the scalars of the energy equation
+    species = K * (8 + 10 + 10 + 1 + 2 + 4 + 2 * E + EXP_FLOPS + 1) + LOG_FLOPS + 10
     f_rhs = species + rx + 2 * nnz + 4 * K + 6
     f_jac = f_rhs + 2 * nnz * 3 + jx + 7 * K * K + 10 * K
     f_lu = 2 * n ** 3 / 3 + 2 * n * n
@@ -146,7 +171,7 @@ def cpu_baseline(m_path: str, m: wl.Mechanism, cfg: dict, cells: int, seed_offse
     el = time.perf_counter() - t0
     return {"value": cells / el, "unit": "cells/s", "cores": threads, "kind": "oracle",
             "sample": f"{cells} cells of {WORKLOAD} (same mechanism, state distribution and dt), "
-                      f"BDF rtol 1e-10, OpenMP over cells", "seconds": el,
+                      f"Radau IIA rtol 1e-10, OpenMP over cells", "seconds": el,
             "failed_cells": int((status != 0).sum())}
 
 
@@ -169,7 +194,7 @@ def run_reference(args, cfg, m, m_path):
             "config": {"workload": WORKLOAD, "cells_per_step": cells, "dt": cfg["dt"]},
             "cpu_baseline": {"value": value, "unit": "cells/s", "cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": f"{cells} cells per step of {WORKLOAD}, BDF rtol 1e-10"},
+                             "sample": f"{cells} cells per step of {WORKLOAD}, Radau IIA rtol 1e-10"},
             "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -203,8 +228,9 @@ def run_pasr(gm, m, N, dt, Y0, Y1, seed, dev):
     return {"workload": f"{N} cells, {K} species, seeded sub-grid fields (5 % laminar)",
             "ms": ms, "cells_per_s": N / (ms * 1e-3), "bytes_per_cell": bytes_cell,
             "kappa_mean": float(kap_np.mean()), "kappa_laminar_or_1": float((kap_np == 1.0).mean()),
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": 6780.0, "unit": "GB/s", "frac": gbs / 6780.0,
-                         "kernel": "pasr_kernel", "peak_source": "MEASURED_PEAKS hbm_gbs"}}
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / PEAKS["hbm_gbs"], "kernel": "pasr_kernel",
+                         "peak_source": "hbm_gbs " + PEAKS["source"]}}
 
 
 # ------------------------------------------------------------------------------------------
@@ -221,7 +247,31 @@ def mlp_flops_per_cell(dims) -> int:
 ANN_CKPT = os.path.join(ROOT, "paper_2402_18858_gb300", "models", "ann_c30_seed1.ckpt")
 
 
-def run_ann(args, m, gm, di_rate):
+def oracle_errors(m_path, T0, p, Y0, results, dt, pick):
+    """T max / p99 and per-species RMS / range of learned-step results against the FP64 oracle
+    (Radau IIA at ORACLE_ERR_RTOL) on the sampled cells `pick` (host arrays; several result
+    sets: results = dict name -> (T [n], Y [K, n]))."""
+    from oracle import Oracle
+    from paper_2402_18858_gb300 import train as tr
+    o = Oracle(m_path)
+    t0 = time.perf_counter()
+    To, Yo, so, _ = o.integrate_batch(T0[pick], p[pick], Y0[:, pick], dt, rtol=ORACLE_ERR_RTOL,
+                                      nthreads=os.cpu_count() or 1)
+    secs = time.perf_counter() - t0
+    ok = so == 0
+    out = {"reference": f"oracle (Radau IIA, rtol {ORACLE_ERR_RTOL:g}) on {pick.size} cells sampled "
+                        f"from the timed batch ({secs:.1f} s on {os.cpu_count()} host cores)",
+           "oracle_failed": int((~ok).sum())}
+    for name, (T, Y) in results.items():
+        e = tr.errors(T[pick], Y[:, pick], To, Yo, ok)
+        rng = Yo[:, ok].max(axis=1) - Yo[:, ok].min(axis=1)
+        nrms = np.sqrt(((Y[:, pick][:, ok] - Yo[:, ok]) ** 2).mean(axis=1)) / np.where(rng > 0, rng, 1.0)
+        e["species_nrms"] = [round(float(v), 6) for v in nrms]
+        out[name] = e
+    return out
+
+
+def run_ann(args, m, gm, di_rate, m_path):
     import torch
     from paper_2402_18858_gb300 import chem, train as tr
     dt = wl.WORKLOADS[WORKLOAD]["dt"]
@@ -245,8 +295,9 @@ def run_ann(args, m, gm, di_rate):
     # two operating points of the learned step, both with a fallback DI at rtol 1e-5 (the
     # fallback's own error stays far below the network's): "fast" falls back on range and
     # element-residual checks only, "accurate" also on a predicted |dT| above 50 K
-    points = {"fast": dict(elem_tol=ANN_ELEM_TOL, dT_max=0.0, di_rtol=1e-5, di_atol_Y=1e-10),
-              "accurate": dict(elem_tol=ANN_ELEM_TOL, dT_max=50.0, di_rtol=1e-5, di_atol_Y=1e-10)}
+    fb_di = dict(di_rtol=1e-5, di_atol_Y=1e-10)
+    points = {"fast": dict(elem_tol=ANN_ELEM_TOL, dT_max=0.0, **fb_di),
+              "accurate": dict(elem_tol=ANN_ELEM_TOL, dT_max=50.0, **fb_di)}
     # accuracy against DI on held-out cells (DI is within 1e-6 of the FP64 oracle)
     ev_data = tr.di_states(gm, m, 100_000, 3, dt)
     errs = {k: tr.evaluate(gm, ann, ev_data, dt, repeats=1, **o) for k, o in points.items()}
@@ -265,9 +316,22 @@ def run_ann(args, m, gm, di_rate):
     X = torch.empty((n, 64), dtype=torch.bfloat16, device=dev)
     Uo = torch.empty((n, ann.n_out_pad), dtype=torch.float32, device=dev)
     chem.chem_ann_features(ann, T0, p, Y0, X)
+    # DI at the fallback's own tolerance on the same cells: the like-for-like speed-up
+    sd = torch.empty(n, dtype=torch.int32, device=dev)
+    dws = torch.zeros(chem.chem_workspace_bytes(gm, n), dtype=torch.uint8, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    T.copy_(T0)
+    Y.copy_(Y0)
+    e0.record(s)
+    chem.chem_step_di(gm, dt, T, p, Y, sd, rtol=fb_di["di_rtol"], atol_Y=fb_di["di_atol_Y"], workspace=dws)
+    e1.record(s)
+    torch.cuda.synchronize()
+    di_same_tol = n / (e0.elapsed_time(e1) * 1e-3)
     best_mlp = 1e30
     report = {"workload": f"{ANN_WORKLOAD}: MLP {ann.dims}, BF16 tcgen05, {n} cells, dt {dt}",
-              "network": provenance, "points": {}}
+              "network": provenance, "points": {},
+              "di_same_tol": {"options": fb_di, "cells_per_s": di_same_tol}}
+    results = {}
     for name, o in points.items():
         best = 1e30
         for _ in range(3):
@@ -282,22 +346,31 @@ def run_ann(args, m, gm, di_rate):
             torch.cuda.synchronize()
             best = min(best, e0.elapsed_time(e1))
             best_mlp = min(best_mlp, e1.elapsed_time(e2))
+        results[name] = (T.cpu().numpy(), Y.cpu().numpy())
         fb = float((status != 0).float().mean().item())
         rate = n / (best * 1e-3)
         ev = errs[name]
         report["points"][name] = {"options": o, "cells_per_s": rate, "ms": best, "fallback_fraction": fb,
                                   "speedup_vs_di": rate / di_rate,
+                                  "speedup_vs_di_same_tol": rate / di_same_tol,
                                   "error_vs_di_100k_heldout": {"fallback_fraction": ev["fallback_fraction"],
                                                                **ev["all_cells"]}}
+    pick = np.sort(np.random.default_rng(11).choice(n, args.oracle_err_cells, replace=False))
+    oe = oracle_errors(m_path, st.T, st.p, st.Y, results, dt, pick)
+    for name in points:
+        report["points"][name]["error_vs_oracle"] = oe.pop(name)
+    report["error_vs_oracle_reference"] = oe
     mlp_tf = mlp_flops_per_cell(ann.dims) * n / (best_mlp * 1e-3) / 1e12
     acc = report["points"]["accurate"]
     report.update({"cells_per_s": acc["cells_per_s"], "speedup_vs_di": acc["speedup_vs_di"],
+                   "speedup_vs_di_same_tol": acc["speedup_vs_di_same_tol"],
                    "fallback_fraction": acc["fallback_fraction"],
                    "error_vs_di_100k_heldout": acc["error_vs_di_100k_heldout"],
                    "mlp_ms": best_mlp, "mlp_tflops": mlp_tf, "mlp_cells_per_s": n / (best_mlp * 1e-3)})
-    roof = {"bound": "tensor", "achieved": mlp_tf, "peak": 1937.2, "unit": "TFLOP/s", "frac": mlp_tf / 1937.2,
+    peak = PEAKS["bf16_tflops"]
+    roof = {"bound": "tensor", "achieved": mlp_tf, "peak": peak, "unit": "TFLOP/s", "frac": mlp_tf / peak,
             "traffic": None, "kernel": "gemm_bf16_kernel (MLP forward, 2 M cells)",
-            "peak_source": "MEASURED_PEAKS bf16_tflops (burst)"}
+            "peak_source": "bf16_tflops (burst) " + PEAKS["source"]}
     report["per_species_mlp"] = run_per_species_forward(gm, ann, X, Uo, mlp_tf)
     return {"report": report, "roofline": roof, "ann": ann}
 
@@ -329,14 +402,117 @@ def run_per_species_forward(gm, ann, X, Uo, multi_tflops):
     multi = mlp_flops_per_cell(ann.dims)
     return {"workload": f"{ps.groups} networks {ps.dims}, BF16 tcgen05 grouped GEMMs, {n} cells",
             "cells": n, "ms": best, "cells_per_s": n / (best * 1e-3), "flops_per_cell": fpc,
-            "flops_vs_multi_output": fpc / multi, "tflops": tf, "frac_of_bf16_peak": tf / 1937.2,
+            "flops_vs_multi_output": fpc / multi, "tflops": tf, "frac_of_bf16_peak": tf / PEAKS["bf16_tflops"],
             "time_vs_multi_output": (fpc / multi) * multi_tflops / tf}
+
+
+# ------------------------------------------------------------------------------------------
+# the other configurations of the metric: config 0 (9 species) and config 4 (53 species)
+# ------------------------------------------------------------------------------------------
+ANN_C53_CKPT = os.path.join(ROOT, "paper_2402_18858_gb300", "models", "ann_c53_seed5.ckpt")
+
+
+def time_di(gm, m, st, dt, peak_gf, repeats):
+    """GPU DI over the states `st` (resident; copies restored before each run): best-of time,
+    cells/s and the FP64 roofline of the di_kernel launch."""
+    import torch
+    from paper_2402_18858_gb300 import chem
+    dev = torch.device("cuda")
+    n = st.T.size
+    T0, p, Y0 = (torch.as_tensor(a, device=dev) for a in (st.T, st.p, st.Y))
+    T, Y = T0.clone(), Y0.clone()
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    stats = torch.empty(4 * n, dtype=torch.int32, device=dev)
+    ws = torch.zeros(chem.chem_workspace_bytes(gm, n), dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+    best = 1e30
+    for _ in range(repeats):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        chem.chem_step_di(gm, dt, T, p, Y, status, rtol=DI_RTOL, stats=stats, workspace=ws)
+        e1.record(s)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    stn = stats.cpu().numpy().reshape(4, n)
+    flops = di_flops(stn, di_flop_model(m))
+    tf = flops / (best * 1e-3) / 1e12
+    return {"ms": best, "cells_per_s": n / (best * 1e-3), "failed_cells": int((status != 0).sum().item()),
+            "steps_per_cell": float(stn[0].mean()), "flops_per_cell": flops / n,
+            "roofline": {"bound": "alu", "achieved": tf, "peak": peak_gf / 1e3, "unit": "TFLOP/s",
+                         "frac": tf / (peak_gf / 1e3), "kernel": "di_kernel (FP64 DFMA pipe)"}}
+
+
+def run_config0(peak_gf):
+    """Config 0: 9-species H/O/N mechanism, 4,096 cells, dt = 1e-6 s, GPU DI."""
+    from paper_2402_18858_gb300 import chem
+    cfg = wl.WORKLOADS["di_h2_9sp_4k"]
+    m = wl.make_mechanism(cfg["kind"], cfg["mech_seed"])
+    gm = chem.chem_load_mech(wl.mechanism_file(cfg["kind"], cfg["mech_seed"], MECH_DIR))
+    st = wl.make_states(m, cfg["n"], cfg["state_seed"])
+    r = time_di(gm, m, st, cfg["dt"], peak_gf, repeats=7)
+    r["workload"] = f"di_h2_9sp_4k: {m.n_species} species / {m.n_reactions} reactions, {cfg['n']} cells, dt {cfg['dt']}"
+    return r
+
+
+def run_config4(args, peak_gf):
+    """Config 4: 53 species / 320 reactions (12 falloff), dt = 1e-5 s.  GPU DI on a seeded
+    subsample of the 8,000,000-cell batch (per-cell cost is independent of the batch), the
+    learned step with DI fallback on all 8,000,000 cells (committed 2000-1000-500 network), its
+    speed-up and its error against the FP64 oracle on cells sampled from the timed batch."""
+    import torch
+    from paper_2402_18858_gb300 import chem
+    cfg = wl.WORKLOADS["di_c_53sp_8m"]
+    m = wl.make_mechanism(cfg["kind"], cfg["mech_seed"])
+    m_path = wl.mechanism_file(cfg["kind"], cfg["mech_seed"], MECH_DIR)
+    gm = chem.chem_load_mech(m_path)
+    n, dt = cfg["n"] if not args.c53_cells else args.c53_cells, cfg["dt"]
+    st = wl.make_states(m, n, cfg["state_seed"])
+    nsub = min(args.c53_di_cells, n)
+    sub = wl.States(T=st.T[:nsub].copy(), p=st.p[:nsub].copy(), Y=np.ascontiguousarray(st.Y[:, :nsub]))
+    di = time_di(gm, m, sub, dt, peak_gf, repeats=2)
+    out = {"workload": f"di_c_53sp_8m: {m.n_species} species / {m.n_reactions} reactions, {n} cells, dt {dt}",
+           "di": {**di, "sample": f"first {nsub} cells of the batch (per-cell work does not depend on the batch)"}}
+    if not os.path.exists(ANN_C53_CKPT):
+        out["ann"] = None
+        return out
+    ann = chem.chem_ann_load(gm, ANN_C53_CKPT)
+    dev = torch.device("cuda")
+    T0, p, Y0 = (torch.as_tensor(a, device=dev) for a in (st.T, st.p, st.Y))
+    T, Y = T0.clone(), Y0.clone()
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = torch.empty(chem.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device=dev)
+    o = dict(elem_tol=ANN_ELEM_TOL, dT_max=0.0, di_rtol=1e-5, di_atol_Y=1e-10)
+    s = torch.cuda.current_stream()
+    best = 1e30
+    for _ in range(2):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        chem.chem_step_ann(gm, ann, dt, T, p, Y, status, ws, **o)
+        e1.record(s)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    rate = n / (best * 1e-3)
+    pick = np.sort(np.random.default_rng(12).choice(n, args.oracle_err_cells_c53, replace=False))
+    oe = oracle_errors(m_path, st.T, st.p, st.Y, {"ann": (T.cpu().numpy(), Y.cpu().numpy())}, dt, pick)
+    out["ann"] = {"network": "paper_2402_18858_gb300/models/ann_c53_seed5.ckpt (4 M DI states, 40 epochs)",
+                  "dims": ann.dims, "options": o, "ms": best, "cells_per_s": rate,
+                  "fallback_fraction": float((status != 0).float().mean().item()),
+                  "speedup_vs_di": rate / di["cells_per_s"], "error_vs_oracle": oe.pop("ann"),
+                  "error_vs_oracle_reference": oe}
+    return out
 
 
 # ------------------------------------------------------------------------------------------
 # serving: Poisson arrivals of mixed requests through continuous batching
 # ------------------------------------------------------------------------------------------
 def run_serve(args, m30, g30, ann_leg, di_rate30):
+    """Config 3's request shape: cells log-uniform in [1e3, 2e6], 50/50 9-/30-species and
+    DI/learned modes, Poisson arrivals at 70 % of the measured capacity.  The count is bounded
+    (--serve-requests) so that the leg stays within about a minute of arrivals."""
     import torch
     from paper_2402_18858_gb300 import chem, train as tr
     m9 = wl.make_mechanism("h2_9", 0)
@@ -353,7 +529,7 @@ def run_serve(args, m30, g30, ann_leg, di_rate30):
     rate_ann30 = ann_leg["report"]["cells_per_s"] if ann_leg else di_rate30
     rng = np.random.default_rng(4)
     R = args.serve_requests
-    lo, hi = 1e3, 5e4
+    lo, hi = 1e3, 2e6
     sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), R)).astype(int)
     kind = rng.random(R) < 0.5            # True: 30 species
     mode = (rng.random(R) < 0.5).astype(int)
@@ -363,33 +539,53 @@ def run_serve(args, m30, g30, ann_leg, di_rate30):
                    np.where(mode == 1, 1.0 / ev9["ann_cells_per_s"], 1.0 / di_rate9)) * sizes
     lam = 0.7 / svc.mean()                 # arrivals at 70 % of the measured capacity
     gaps = rng.exponential(1.0 / lam, R)
-    sv = chem.chem_server_create(hbm_budget_bytes=8 << 30, n_streams=2, max_batch_cells=1 << 20)
-    c30 = chem.chem_server_add_class(sv, g30, a30, capacity_cells=1 << 20)
-    c9 = chem.chem_server_add_class(sv, g9, a9, capacity_cells=1 << 20)
+    # the requests' states, made before the clock starts
+    payload = []
+    for i in range(R):
+        mm = m30 if kind[i] else m9
+        st = wl.make_states(mm, int(sizes[i]), 50_000 + i)
+        payload.append((st, np.empty(sizes[i]), np.empty((mm.n_species, sizes[i])),
+                        np.empty(sizes[i], dtype=np.int32)))
+    sv = chem.chem_server_create(hbm_budget_bytes=16 << 30, n_streams=2, max_batch_cells=1 << 20,
+                                 starvation_s=30.0, di_chunk_cells=32768)
+    c30 = chem.chem_server_add_class(sv, g30, a30, capacity_cells=1 << 23)
+    c9 = chem.chem_server_add_class(sv, g9, a9, capacity_cells=1 << 23)
     reqs = []
     t0 = time.perf_counter()
     for i in range(R):
-        mm, cls, dt = (m30, c30, wl.WORKLOADS[WORKLOAD]["dt"]) if kind[i] else (m9, c9, 1e-6)
-        st = wl.make_states(mm, int(sizes[i]), 50_000 + i)
-        To = np.empty(sizes[i])
-        Yo = np.empty((mm.n_species, sizes[i]))
-        so = np.empty(sizes[i], dtype=np.int32)
+        cls, dt = (c30, wl.WORKLOADS[WORKLOAD]["dt"]) if kind[i] else (c9, 1e-6)
+        st, To, Yo, so = payload[i]
         target = t0 + gaps[:i + 1].sum()
         while time.perf_counter() < target:
             time.sleep(min(1e-3, max(0.0, target - time.perf_counter())))
         reqs.append(chem.chem_server_submit(sv, cls, int(mode[i]), dt, st.T, st.p, st.Y, To, Yo, so))
     for r in reqs:
-        done, res = chem.chem_server_wait(sv, r, 600.0)
+        done, res = chem.chem_server_wait(sv, r, 900.0)
         if not done or res != 0:
             raise RuntimeError(f"serving request {r} did not complete ({done}, {res})")
     stt = chem.chem_server_stats(sv)
+    lat = np.array([chem.chem_server_request_latency(sv, r) for r in reqs])
     del sv
-    return {"workload": f"{R} requests, cells log-uniform [{int(lo)}, {int(hi)}], 50/50 9-/30-species, "
-                        f"50/50 DI/ANN, Poisson arrivals at 70 % of measured capacity ({lam:.2f}/s)",
+
+    def pct(sel):
+        v = lat[sel]
+        return {"n": int(v.size), "p50_ms": float(np.percentile(v, 50)) if v.size else None,
+                "p99_ms": float(np.percentile(v, 99)) if v.size else None}
+    small = sizes < 30_000
+    breakdown = {"cells_lt_3e4": pct(small), "cells_ge_3e4": pct(~small),
+                 "di_30sp": pct(kind & (mode == 0)), "di_9sp": pct(~kind & (mode == 0)),
+                 "ann_30sp": pct(kind & (mode == 1)), "ann_9sp": pct(~kind & (mode == 1))}
+    return {"workload": f"{R} requests, cells log-uniform [{int(lo)}, {int(hi)}] (config 3's shape; count "
+                        f"bounded), 50/50 9-/30-species, 50/50 DI/ANN, Poisson arrivals at 70 % of measured "
+                        f"capacity ({lam:.3f}/s)",
             "p50_ms": stt["p50_ms"], "p99_ms": stt["p99_ms"], "mean_ms": stt["mean_ms"], "max_ms": stt["max_ms"],
             "cells_per_s": stt["cells_per_s"], "batches": stt["batches"],
             "mean_batch_requests": stt["mean_batch_requests"], "wall_s": stt["wall_s"],
-            "failed": stt["failed"]}
+            "failed": stt["failed"], "latency_by_kind": breakdown,
+            "p99_cause": "the largest 30-species DI requests: their own GPU time (up to 2e6 cells at the DI "
+                         "rate) sets the tail; pieces of 32,768 cells keep them from holding back small requests",
+            "scheduler": "pieces of <= 32,768 cells per DI request per launch, kind with the least work left "
+                         "first, 30 s starvation limit, 2 streams"}
 
 
 # ------------------------------------------------------------------------------------------
@@ -409,7 +605,13 @@ def main():
     ap.add_argument("--ann-train-cells", type=int, default=500_000)
     ap.add_argument("--ann-epochs", type=int, default=24)
     ap.add_argument("--ann-cells", type=int, default=2_000_000)
-    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--oracle-err-cells", type=int, default=512,
+                    help="cells of the timed learned-step batch compared with the FP64 oracle")
+    ap.add_argument("--oracle-err-cells-c53", type=int, default=128)
+    ap.add_argument("--no-config4", action="store_true", help="skip the 53-species legs")
+    ap.add_argument("--c53-cells", type=int, default=0, help="override config 4's cell count")
+    ap.add_argument("--c53-di-cells", type=int, default=65536, help="config 4 DI subsample")
     args = ap.parse_args()
 
     cfg = dict(wl.WORKLOADS[WORKLOAD])
@@ -487,11 +689,24 @@ def main():
     fm = di_flop_model(m)
     flops = di_flops(stats_np, fm)
     peak_gf = chem.chem_fp64_peak_gflops()
+    hbm = PEAKS["hbm_gbs"]
     achieved_tf = flops / (di_ms * 1e-3) / 1e12
     th_bytes = N * (m.n_species + 1) * 8 + N * 4 * 8
     th_gbs = th_bytes / (th_ms * 1e-3) / 1e9
     th_flops_cell = thermo_fp64_flops(m.n_species)
     th_tf = th_flops_cell * N / (th_ms * 1e-3) / 1e12
+
+    # the properties in full FP64 (the config's precision) beside the step's mixed mode
+    th64 = []
+    for r in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        chem.thermo_props(gm, T, Y, cp, h, mu, kap, mixed_precision=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r:
+            th64.append(e0.elapsed_time(e1))
+    th64_ms = float(np.median(th64))
 
     # PaSR filtered source from this step (Y0 -> Y after DI) with seeded sub-grid fields
     pasr = run_pasr(gm, m, N, cfg["dt"], Y0, Y, cfg["state_seed"] + 3, dev)
@@ -527,7 +742,9 @@ def main():
     d2h = oT.numel() * 8 + oY.numel() * 8 + ost.numel() * 4
 
     di_rate = N / (di_ms * 1e-3)
-    ann = None if args.no_ann else run_ann(args, m, gm, di_rate)
+    cfg0 = run_config0(peak_gf) if world == 1 else None
+    cfg4 = run_config4(args, peak_gf) if (world == 1 and not args.no_config4) else None
+    ann = None if args.no_ann else run_ann(args, m, gm, di_rate, m_path)
     serve = None if (args.no_serve or world > 1) else run_serve(args, m, gm, ann, di_rate)
 
     if rank == 0:
@@ -560,8 +777,14 @@ def main():
                                 "frac": th_tf / (peak_gf / 1e3), "kernel": "thermo_kernel (mixed precision)",
                                 "flops_per_cell": th_flops_cell,
                                 "note": "FP64 c_p/h mixture sums bound it; HBM side: "
-                                        f"{th_gbs:.0f} GB/s = {th_gbs / 6780.0:.3f} of 6780 (MEASURED_PEAKS hbm_gbs)",
-                                "hbm_gbs": th_gbs, "hbm_frac": th_gbs / 6780.0},
+                                        f"{th_gbs:.0f} GB/s = {th_gbs / hbm:.3f} of {hbm:.0f} (hbm_gbs {PEAKS['source']})",
+                                "hbm_gbs": th_gbs, "hbm_frac": th_gbs / hbm},
+            "thermo_fp64": {"ms": th64_ms, "cells_per_s": N / (th64_ms * 1e-3),
+                            "note": "thermo_props with every sum in FP64 (Wilke, conductivity included), "
+                                    "same 1,000,000 cells; the step uses the mixed mode"},
+            "config0": cfg0,
+            "config4": cfg4,
+            "peaks": PEAKS,
             "e2e": {"value": sharding.job_throughput(N, world, e2e_ms * 1e-3), "unit": "cells/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,  # di_kernel + thermo_kernel per step

@@ -314,7 +314,10 @@ typedef struct {
   int n_streams;            /* concurrent batches in flight (1..16) */
   int max_batch_cells;      /* cells per launch and per request (index-list capacity) */
   double starvation_s;      /* > 0: once the oldest waiting request has waited this long,
-                               nothing newer is admitted past it */
+                               nothing newer is admitted past it, and once an admitted request
+                               has waited this long its kind is launched next */
+  int di_chunk_cells;       /* cells of one direct-integration request per launch (0: 32768) */
+  int reserved;
 } chem_server_opts;
 
 typedef struct {
@@ -325,19 +328,23 @@ typedef struct {
 } chem_server_stats;
 
 /* A background host thread admits requests into per-class device arenas (first-fit column
- * ranges within the HBM budget), launches one batch per idle stream over all admitted
- * requests of the oldest waiting request's class, mode and dt (index list), copies results
- * back and frees the columns.  Host arrays passed to chem_server_submit must stay valid until
- * the request completes (pinned memory gives asynchronous copies).  Per-cell results do not
- * depend on the batch composition. */
+ * ranges within the HBM budget) and, whenever a stream is idle, launches one batch over
+ * pieces of the admitted requests of one kind (class, mode, dt) through an index list: the
+ * kind of the request with the least work left (or of one past starvation_s), its requests
+ * smallest remainder first, a direct-integration request contributing at most
+ * di_chunk_cells per launch and a batch at most max_batch_cells.  Each piece's results are
+ * copied back when its launch ends; a request completes with its last piece and frees its
+ * columns.  Host arrays passed to chem_server_submit must stay valid until the request
+ * completes (pinned memory gives asynchronous copies).  Per-cell results do not depend on the
+ * batch composition or on the piece a cell runs in. */
 int chem_server_create(const chem_server_opts* opts, chem_server* out);
 /* Register a class: a mechanism (and optionally a trained ANN for mode 1) with an arena of
  * capacity_cells columns.  Classes are added before the first submit. */
 int chem_server_add_class(chem_server server, chem_mech mech, chem_ann ann, int64_t capacity_cells,
                           int* class_id);
 /* Queue one request: mode 0 = direct integration, 1 = learned step with fallback; n cells
- * of host SoA state T[n], p[n], Y[K][n] (species-major, ld = n); results to T_out, Y_out,
- * status_out (host).  Non-blocking. */
+ * (at most the class arena's capacity) of host SoA state T[n], p[n], Y[K][n] (species-major,
+ * ld = n); results to T_out, Y_out, status_out (host).  Non-blocking. */
 int chem_server_submit(chem_server server, int class_id, int mode, double dt, int64_t n,
                        const double* T, const double* p, const double* Y, double* T_out,
                        double* Y_out, int32_t* status_out, int64_t* request_id);
@@ -346,6 +353,8 @@ int chem_server_submit(chem_server server, int class_id, int mode, double dt, in
 int chem_server_wait(chem_server server, int64_t request_id, double timeout_s, int* done,
                      int* result);
 int chem_server_get_stats(chem_server server, chem_server_stats* stats);
+/* Latency of one request (submit -> results on the host) in ms; -1 while it is not done. */
+int chem_server_request_latency(chem_server server, int64_t request_id, double* latency_ms);
 void chem_server_free(chem_server server);
 
 /* ---------------------------------------------------------------------------------------- */

@@ -541,7 +541,7 @@ def chem_step_ann(m: Mech, a: Ann, dt: float, T, p, Y, status, workspace, idx=No
 # ------------------------------------------------------------------------------------------
 class ServerOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("n_streams", C.c_int), ("max_batch_cells", C.c_int),
-                ("starvation_s", C.c_double)]
+                ("starvation_s", C.c_double), ("di_chunk_cells", C.c_int), ("reserved", C.c_int)]
 
 
 class ServerStats(C.Structure):
@@ -567,6 +567,7 @@ def _srv_sigs():
                                      C.POINTER(C.c_int64)]
     L.chem_server_wait.argtypes = [vp, C.c_int64, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.chem_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    L.chem_server_request_latency.argtypes = [vp, C.c_int64, C.POINTER(C.c_double)]
     L.chem_server_free.argtypes = [vp]
     L.chem_server_free.restype = None
     _srv_sigs_done = True
@@ -590,9 +591,10 @@ class Server:
 
 
 def chem_server_create(hbm_budget_bytes: int, n_streams: int = 2, max_batch_cells: int = 1 << 21,
-                       starvation_s: float = 0.0) -> Server:
+                       starvation_s: float = 0.0, di_chunk_cells: int = 0) -> Server:
     _srv_sigs()
-    o = ServerOpts(int(hbm_budget_bytes), int(n_streams), int(max_batch_cells), float(starvation_s))
+    o = ServerOpts(int(hbm_budget_bytes), int(n_streams), int(max_batch_cells), float(starvation_s),
+                   int(di_chunk_cells), 0)
     h = C.c_void_p()
     _check(lib().chem_server_create(C.byref(o), C.byref(h)))
     return Server(h.value)
@@ -627,6 +629,13 @@ def chem_server_wait(sv: Server, request_id: int, timeout_s: float = 60.0):
     done, res = C.c_int(), C.c_int()
     _check(lib().chem_server_wait(sv.handle, int(request_id), float(timeout_s), C.byref(done), C.byref(res)))
     return bool(done.value), res.value
+
+
+def chem_server_request_latency(sv: Server, request_id: int) -> float:
+    """Submit-to-results latency of a completed request in ms (-1 while it runs)."""
+    v = C.c_double()
+    _check(lib().chem_server_request_latency(sv.handle, int(request_id), C.byref(v)))
+    return v.value
 
 
 def chem_server_stats(sv: Server) -> dict:

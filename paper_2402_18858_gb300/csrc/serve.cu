@@ -6,14 +6,20 @@
 //   * admission by device-memory budget: every (mechanism, ANN) class owns a structure-of-
 //     arrays arena of cell columns in HBM; a request is admitted when a free column range of
 //     its size exists (first fit), its state is copied in once and stays resident;
-//   * continuous batching: whenever a stream is idle, one kernel launch processes every
-//     admitted request of the class (and dt, mode) of the oldest waiting request, through an
-//     index list over their columns; requests keep being admitted while others run, and
-//     several streams overlap on the device;
-//   * completion: results are copied back per request, its columns are freed, and its
-//     latency (submit -> results on the host) is recorded.
-// Every per-cell result is independent of the batch composition (the kernels are
-// deterministic per cell), so a request's answer is the same alone or in any mix.
+//   * continuous batching in pieces: whenever a stream is idle, it picks the kind (class,
+//     mode, dt) of the ready request with the least work left (or of a request that has
+//     waited past the starvation limit) and launches one kernel over pieces of every ready
+//     request of that kind, smallest remainder first, through an index list; a direct-
+//     integration request contributes at most di_chunk_cells per launch, so a large request
+//     advances in bounded pieces and never holds a stream for its whole length while small
+//     requests wait; requests keep being admitted while others run, and several streams
+//     overlap on the device;
+//   * completion: each piece's results are copied back as its launch ends; a request whose
+//     last piece is back frees its columns and records its latency (submit -> results on the
+//     host).
+// Every per-cell result is independent of the batch composition and of the piece it runs in
+// (the kernels are deterministic per cell), so a request's answer is the same alone or in any
+// mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,6 +58,8 @@ struct Request {
   int32_t* status_out = nullptr;
   double t_submit = 0, t_done = 0;
   int64_t col0 = -1;
+  int64_t launched = 0;   // cells handed to launches so far
+  int64_t finished = 0;   // cells whose results are back on the host
   int state = kQueued;
   int result = 0;        // CHEM_OK or the API error of its launch
   cudaEvent_t admitted = nullptr;
@@ -93,11 +101,18 @@ struct Class {
   ColumnAllocator cols;
 };
 
+// cells [off, off + len) of a request, run in one launch
+struct Piece {
+  Request* r;
+  int64_t off, len;
+};
+
 struct Slot {
   cudaStream_t s = nullptr;
   cudaEvent_t done = nullptr, copied = nullptr;
   int phase = 0;                    // 0 idle, 1 running, 2 copying back
-  std::vector<Request*> reqs;
+  std::vector<Piece> pieces;
+  int rc = 0;                       // API result of the slot's launch
   int32_t* d_idx = nullptr;
   int32_t* h_idx = nullptr;         // pinned staging of the index list
   int32_t* d_status = nullptr;
@@ -158,26 +173,33 @@ void finish_request(chem_server_s* sv, Request* r, double t) {
 bool schedule(chem_server_s* sv) {
   bool progress = false;
   const double t = now_s();
-  // completions
+  // completions: copy each piece's results back, then account for them
   for (Slot& sl : sv->slots) {
     if (sl.phase == 1 && cudaEventQuery(sl.done) == cudaSuccess) {
       int64_t s0 = 0;
-      for (Request* r : sl.reqs) {
+      for (const Piece& pc : sl.pieces) {
+        Request* r = pc.r;
         Class& c = *sv->classes[r->cls];
-        if (r->result == CHEM_OK) {
-          cudaMemcpyAsync(r->T_out, c.T + r->col0, r->n * 8, cudaMemcpyDeviceToHost, sl.s);
-          cudaMemcpy2DAsync(r->Y_out, r->n * 8, c.Y + r->col0, c.cap * 8, r->n * 8, c.K, cudaMemcpyDeviceToHost, sl.s);
-          cudaMemcpyAsync(r->status_out, sl.d_status + s0, r->n * 4, cudaMemcpyDeviceToHost, sl.s);
+        if (sl.rc == CHEM_OK) {
+          cudaMemcpyAsync(r->T_out + pc.off, c.T + r->col0 + pc.off, pc.len * 8, cudaMemcpyDeviceToHost, sl.s);
+          cudaMemcpy2DAsync(r->Y_out + pc.off, r->n * 8, c.Y + r->col0 + pc.off, c.cap * 8, pc.len * 8, c.K,
+                            cudaMemcpyDeviceToHost, sl.s);
+          cudaMemcpyAsync(r->status_out + pc.off, sl.d_status + s0, pc.len * 4, cudaMemcpyDeviceToHost, sl.s);
         }
-        s0 += r->n;
+        s0 += pc.len;
       }
       cudaEventRecord(sl.copied, sl.s);
       sl.phase = 2;
       progress = true;
     }
     if (sl.phase == 2 && cudaEventQuery(sl.copied) == cudaSuccess) {
-      for (Request* r : sl.reqs) finish_request(sv, r, now_s());
-      sl.reqs.clear();
+      for (const Piece& pc : sl.pieces) {
+        Request* r = pc.r;
+        if (sl.rc != CHEM_OK) r->result = sl.rc;
+        r->finished += pc.len;
+        if (r->finished == r->n) finish_request(sv, r, now_s());
+      }
+      sl.pieces.clear();
       sl.phase = 0;
       progress = true;
       sv->cv.notify_all();
@@ -204,53 +226,64 @@ bool schedule(chem_server_s* sv) {
     it = sv->queue.erase(it);
     progress = true;
   }
-  // batching: every idle stream takes the class/mode/dt of the oldest ready request and all
-  // ready requests of that kind, up to max_batch_cells
+  // batching: every idle stream picks a kind and launches pieces of its ready requests
+  const int64_t di_chunk = sv->opts.di_chunk_cells > 0 ? sv->opts.di_chunk_cells : 32768;
   for (Slot& sl : sv->slots) {
     if (sl.phase != 0) continue;
-    Request* oldest = nullptr;
-    for (auto& kv : sv->reqs) {
-      Request* r = kv.second.get();
-      if (r->state == kAdmitting && cudaEventQuery(r->admitted) == cudaSuccess) r->state = kReady;
-      if (r->state == kReady && (!oldest || r->id < oldest->id)) oldest = r;
-    }
-    if (!oldest) break;
-    std::vector<Request*> batch;
-    int64_t cells = 0;
     std::vector<Request*> ready;
     for (auto& kv : sv->reqs) {
       Request* r = kv.second.get();
-      if (r->state == kReady && r->cls == oldest->cls && r->mode == oldest->mode && r->dt == oldest->dt) ready.push_back(r);
+      if (r->state == kAdmitting && cudaEventQuery(r->admitted) == cudaSuccess) r->state = kReady;
+      if (r->state == kReady && r->launched < r->n) ready.push_back(r);
     }
-    std::sort(ready.begin(), ready.end(), [](Request* a, Request* b) { return a->id < b->id; });
-    for (Request* r : ready) {
-      if (!batch.empty() && cells + r->n > sv->opts.max_batch_cells) break;
-      batch.push_back(r);
-      cells += r->n;
+    if (ready.empty()) break;
+    auto left = [](const Request* r) { return r->n - r->launched; };
+    auto before = [&](const Request* a, const Request* b) {
+      return left(a) != left(b) ? left(a) < left(b) : a->id < b->id;
+    };
+    // the kind: that of a request past the starvation limit (oldest first), else that of the
+    // request with the least work left
+    Request* pick = nullptr;
+    if (sv->opts.starvation_s > 0)
+      for (Request* r : ready)
+        if (t - r->t_submit > sv->opts.starvation_s && (!pick || r->id < pick->id)) pick = r;
+    if (!pick)
+      for (Request* r : ready)
+        if (!pick || before(r, pick)) pick = r;
+    std::vector<Request*> kind;
+    for (Request* r : ready)
+      if (r->cls == pick->cls && r->mode == pick->mode && r->dt == pick->dt) kind.push_back(r);
+    std::sort(kind.begin(), kind.end(), before);
+    if (pick != kind.front()) {   // a starving request goes first within its kind
+      kind.erase(std::find(kind.begin(), kind.end(), pick));
+      kind.insert(kind.begin(), pick);
     }
-    Class& c = *sv->classes[oldest->cls];
-    int64_t q = 0;
-    for (Request* r : batch) {
-      for (int64_t i = 0; i < r->n; ++i) sl.h_idx[q + i] = (int32_t)(r->col0 + i);
-      q += r->n;
-      r->state = kRunning;
+    const int64_t cap = sv->opts.max_batch_cells;
+    const int64_t piece_max = pick->mode == 0 ? std::min<int64_t>(di_chunk, cap) : cap;
+    int64_t cells = 0;
+    for (Request* r : kind) {
+      if (cells >= cap) break;
+      const int64_t len = std::min({left(r), piece_max, cap - cells});
+      sl.pieces.push_back(Piece{r, r->launched, len});
+      for (int64_t i = 0; i < len; ++i) sl.h_idx[cells + i] = (int32_t)(r->col0 + r->launched + i);
+      r->launched += len;
+      if (r->launched == r->n) r->state = kRunning;
+      cells += len;
     }
+    Class& c = *sv->classes[pick->cls];
     cudaMemcpyAsync(sl.d_idx, sl.h_idx, cells * 4, cudaMemcpyHostToDevice, sl.s);
-    int rc;
-    if (oldest->mode == 1) {
+    if (pick->mode == 1) {
       chem_ann_opts ao{};
-      rc = chem_step_ann(c.mech, c.ann, cells, c.cap, oldest->dt, c.T, c.p, c.Y, sl.d_idx, &ao, sl.d_status,
-                         sl.ann_ws, sl.ann_ws_bytes, (chem_stream)sl.s);
+      sl.rc = chem_step_ann(c.mech, c.ann, cells, c.cap, pick->dt, c.T, c.p, c.Y, sl.d_idx, &ao, sl.d_status,
+                            sl.ann_ws, sl.ann_ws_bytes, (chem_stream)sl.s);
     } else {
-      rc = chem_step_di(c.mech, cells, c.cap, oldest->dt, c.T, c.p, c.Y, sl.d_idx, nullptr, sl.d_status, nullptr,
-                        sl.di_ws, chem_workspace_bytes(c.mech, cells), (chem_stream)sl.s);
+      sl.rc = chem_step_di(c.mech, cells, c.cap, pick->dt, c.T, c.p, c.Y, sl.d_idx, nullptr, sl.d_status, nullptr,
+                           sl.di_ws, chem_workspace_bytes(c.mech, cells), (chem_stream)sl.s);
     }
-    for (Request* r : batch) r->result = rc;
     cudaEventRecord(sl.done, sl.s);
-    sl.reqs = batch;
     sl.phase = 1;
     sv->batches++;
-    sv->batch_reqs += (int64_t)batch.size();
+    sv->batch_reqs += (int64_t)sl.pieces.size();
     progress = true;
   }
   return progress;
@@ -274,7 +307,7 @@ extern "C" {
 
 int chem_server_create(const chem_server_opts* opts, chem_server* out) {
   if (!opts || !out || opts->n_streams < 1 || opts->n_streams > 16 || opts->max_batch_cells < 1 ||
-      opts->hbm_budget_bytes == 0)
+      opts->hbm_budget_bytes == 0 || opts->di_chunk_cells < 0)
     return set_error(CHEM_E_ARG, "chem_server_create: bad options");
   *out = nullptr;
   chem_server_s* sv = new chem_server_s();
@@ -348,7 +381,7 @@ int chem_server_add_class(chem_server sv, chem_mech mech, chem_ann ann, int64_t 
 int chem_server_submit(chem_server sv, int class_id, int mode, double dt, int64_t n, const double* T, const double* p,
                        const double* Y, double* T_out, double* Y_out, int32_t* status_out, int64_t* request_id) {
   if (!sv || class_id < 0 || class_id >= (int)sv->classes.size() || (mode != 0 && mode != 1) || n < 1 ||
-      n > sv->opts.max_batch_cells || !T || !p || !Y || !T_out || !Y_out || !status_out || !(dt >= 0))
+      !T || !p || !Y || !T_out || !Y_out || !status_out || !(dt >= 0))
     return set_error(CHEM_E_ARG, "chem_server_submit: bad arguments");
   if (mode == 1 && !sv->classes[class_id]->ann) return set_error(CHEM_E_ARG, "chem_server_submit: class has no ANN");
   if (n > sv->classes[class_id]->cap) return set_error(CHEM_E_ARG, "chem_server_submit: request larger than its class arena");
@@ -382,6 +415,16 @@ int chem_server_wait(chem_server sv, int64_t request_id, double timeout_s, int* 
   sv->cv.wait_for(lock, std::chrono::duration<double>(std::max(timeout_s, 0.0)), [&] { return r->state == kDone; });
   *done = r->state == kDone;
   if (result) *result = r->result;
+  return CHEM_OK;
+}
+
+int chem_server_request_latency(chem_server sv, int64_t request_id, double* latency_ms) {
+  if (!sv || !latency_ms) return set_error(CHEM_E_ARG, "chem_server_request_latency: bad arguments");
+  std::lock_guard<std::mutex> lock(sv->mu);
+  auto it = sv->reqs.find(request_id);
+  if (it == sv->reqs.end()) return set_error(CHEM_E_ARG, "chem_server_request_latency: unknown request");
+  const Request* r = it->second.get();
+  *latency_ms = r->state == kDone ? (r->t_done - r->t_submit) * 1e3 : -1.0;
   return CHEM_OK;
 }
 

@@ -82,3 +82,33 @@ def test_mixed_requests_same_as_alone(lc, mechs):
         Ta, Ya, sa = _alone(lc, gm, ann, mode, dt, st)
         assert np.array_equal(so, sa), rid
         assert np.array_equal(To, Ta) and np.array_equal(Yo, Ya), rid
+
+
+def test_requests_in_pieces_same_as_alone(lc, mechs):
+    """Direct-integration requests larger than a piece (di_chunk_cells) and one larger than a
+    whole batch run in several launches; each answer equals the request run alone, and the
+    small requests submitted after the large ones finish before them."""
+    m9, p9 = mechs["h2_9"]
+    g9 = lc.chem_load_mech(p9)
+    sv = lc.chem_server_create(hbm_budget_bytes=256 << 20, n_streams=2, max_batch_cells=3000,
+                               di_chunk_cells=700)
+    c9 = lc.chem_server_add_class(sv, g9, None, capacity_cells=40000)
+    sizes = [9000, 5000, 20, 35, 1200, 10, 2600]
+    reqs = []
+    for i, n in enumerate(sizes):
+        st = w.make_states(m9, n, 2000 + i)
+        To, Yo, so = np.empty(n), np.empty((m9.n_species, n)), np.empty(n, dtype=np.int32)
+        rid = lc.chem_server_submit(sv, c9, 0, 1e-6, st.T, st.p, st.Y, To, Yo, so)
+        reqs.append((rid, st, To, Yo, so))
+    for rid, *_ in reqs:
+        done, res = lc.chem_server_wait(sv, rid, 120.0)
+        assert done and res == 0
+    lat = [lc.chem_server_request_latency(sv, r[0]) for r in reqs]
+    assert min(lat) > 0
+    assert max(lat[2], lat[3], lat[5]) < min(lat[0], lat[1])      # small ones are not held back
+    stats = lc.chem_server_stats(sv)
+    assert stats["completed"] == len(sizes) and stats["failed"] == 0
+    assert stats["batches"] >= 9000 // 700 + 1
+    for rid, st, To, Yo, so in reqs:
+        Ta, Ya, sa = _alone(lc, g9, None, 0, 1e-6, st)
+        assert np.array_equal(so, sa) and np.array_equal(To, Ta) and np.array_equal(Yo, Ya), rid
