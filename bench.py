@@ -276,10 +276,10 @@ def run_ann(args, m, gm, di_rate, m_path):
     from paper_2402_18858_gb300 import chem, train as tr
     dt = wl.WORKLOADS[WORKLOAD]["dt"]
     if os.path.exists(ANN_CKPT) and not args.ann_retrain:
-        # trained offline by paper_2402_18858_gb300.train (8 M DI samples, 60 epochs, GPU)
+        # trained offline by paper_2402_18858_gb300.train (16 M DI samples, 100 epochs, GPU)
         ann = chem.chem_ann_load(gm, ANN_CKPT)
         provenance = {"source": "paper_2402_18858_gb300/models/ann_c30_seed1.ckpt",
-                      "train_cells": 8_000_000, "train_epochs": 60}
+                      "train_cells": 16_000_000, "train_epochs": 100}
     else:
         t0 = time.perf_counter()
         data = tr.di_states(gm, m, args.ann_train_cells, 2, dt)
@@ -292,11 +292,13 @@ def run_ann(args, m, gm, di_rate, m_path):
         provenance = {"source": "trained in this run", "train_cells": args.ann_train_cells,
                       "train_epochs": args.ann_epochs, "data_generation_s": gen_s, "train_s": trn["seconds"],
                       "train_samples_per_s": trn["samples_per_s"]}
-    # two operating points of the learned step, both with a fallback DI at rtol 1e-5 (the
+    # three operating points of the learned step, all with a fallback DI at rtol 1e-5 (the
     # fallback's own error stays far below the network's): "fast" falls back on range and
-    # element-residual checks only, "accurate" also on a predicted |dT| above 50 K
+    # element-residual checks only, "balanced" and "accurate" also on a predicted |dT| above
+    # 100 K and 50 K
     fb_di = dict(di_rtol=1e-5, di_atol_Y=1e-10)
     points = {"fast": dict(elem_tol=ANN_ELEM_TOL, dT_max=0.0, **fb_di),
+              "balanced": dict(elem_tol=ANN_ELEM_TOL, dT_max=100.0, **fb_di),
               "accurate": dict(elem_tol=ANN_ELEM_TOL, dT_max=50.0, **fb_di)}
     # accuracy against DI on held-out cells (DI is within 1e-6 of the FP64 oracle)
     ev_data = tr.di_states(gm, m, 100_000, 3, dt)

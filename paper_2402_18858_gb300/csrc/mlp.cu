@@ -58,18 +58,113 @@ __device__ __forceinline__ float dgelu_f(float x) {
 #define CHEM_GEMM_STAGES 3
 #endif
 
+// staging buffer of one epilogue warp (32 rows x 32 BF16 columns), see store_rows_bf16
+constexpr int kEpiWarpBytes = 32 * 64;
+
 template <int BN>
 struct TileCfg {
   static constexpr int STAGES = BN >= 224 ? CHEM_GEMM_STAGES_256 : CHEM_GEMM_STAGES;
   static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   static constexpr size_t A_BYTES = (size_t)tc::BM * tc::BK * 2;
   static constexpr size_t B_BYTES = (size_t)BN * tc::BK * 2;
-  static constexpr size_t SMEM = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 2) * 8 + 16;
+  static constexpr size_t SMEM = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 2) * 8 + 16 + 128 +
+                                 8 * kEpiWarpBytes;
 };
 
-// epilogue of one 32-column chunk of one accumulator row: columns col0 .. col0 + nv - 1 of row
+// Per-warp staging of a 32 x 32 BF16 block between the row-per-lane layout of the TMEM
+// epilogue and row segments: a warp's store (load) then moves 8 whole 64-byte row segments
+// (full 32-byte sectors) instead of 32 scattered 16-byte pieces.  Slot of (row r, 16-byte chunk
+// c) in the 2 KB buffer: r * 64 + 16 ((c + (r >> 1)) & 3), free of bank conflicts both for one
+// row per lane and for four lanes per row.
+__device__ __forceinline__ uint32_t stage_slot(int r, int c) { return (uint32_t)(r * 64 + 16 * ((c + (r >> 1)) & 3)); }
+
+// rows 0 .. nrows - 1 of `dst` (row stride ld elements, 32 columns) from the staging buffer,
+// which holds this lane's row (lane = row) at stage_slot(lane, 0..3)
+__device__ __forceinline__ void flush_rows_bf16(const uint8_t* wbuf, bf16* dst, int64_t ld, int nrows, int lane) {
+  __syncwarp();
+  const int c = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = (lane >> 2) + 8 * i;
+    if (r < nrows) *(uint4*)(dst + (size_t)r * ld + 8 * c) = *(const uint4*)(wbuf + stage_slot(r, c));
+  }
+  __syncwarp();
+}
+
+// the reverse: this lane's row (lane = row - row0) of src into pk; rows past nrows read zero
+__device__ __forceinline__ void load_rows_bf16(uint4 (&pk)[4], uint8_t* wbuf, const bf16* src, int64_t ld,
+                                               int nrows, int lane) {
+  const int c = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = (lane >> 2) + 8 * i;
+    const uint4 v = r < nrows ? __ldg((const uint4*)(src + (size_t)r * ld + 8 * c)) : make_uint4(0u, 0u, 0u, 0u);
+    *(uint4*)(wbuf + stage_slot(r, c)) = v;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) pk[q] = *(const uint4*)(wbuf + stage_slot(lane, q));
+  __syncwarp();
+}
+
+// epilogue of one 32-column chunk of the accumulator rows of a warp: this lane's row is
+// row = row0 + lane, columns col0 .. col0 + nv - 1; rows row0 .. row0 + nrows - 1 exist.
+// Called by the whole warp (the staged BF16 paths synchronise it).
 template <int EPI>
-__device__ __forceinline__ void epi_chunk(float (&v)[32], int row, int col0, int nv, const GemmEpi& e) {
+__device__ __forceinline__ void epi_chunk(float (&v)[32], int row, int col0, int nv, const GemmEpi& e,
+                                          uint8_t* wbuf, int row0, int nrows, int lane) {
+  if ((EPI == 0 || EPI == 2) && nv == 32) {
+    if (EPI == 0) {
+      // hidden layer forward: out = bf16(GELU(acc + b)); optional pre-activation copy.  Each
+      // group of 8 columns goes to the staging buffer as soon as it is made (few live registers)
+      if (e.bias) {
+        // the chunk's 32 biases as eight 16-byte broadcast loads (col0 is a multiple of 32)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 b4 = __ldg((const float4*)(e.bias + col0) + q);
+          v[4 * q] += b4.x;
+          v[4 * q + 1] += b4.y;
+          v[4 * q + 2] += b4.z;
+          v[4 * q + 3] += b4.w;
+        }
+      }
+      if (e.zout) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          __align__(16) bf16 u[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) u[i] = __float2bfloat16_rn(v[8 * q + i]);
+          *(uint4*)(wbuf + stage_slot(lane, q)) = *(const uint4*)u;
+        }
+        flush_rows_bf16(wbuf, e.zout + (size_t)row0 * e.ldo + col0, e.ldo, nrows, lane);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        __align__(16) bf16 t[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = __float2bfloat16_rn(gelu_f(v[8 * q + i]));
+        *(uint4*)(wbuf + stage_slot(lane, q)) = *(const uint4*)t;
+      }
+      flush_rows_bf16(wbuf, (bf16*)e.out + (size_t)row0 * e.ldo + col0, e.ldo, nrows, lane);
+    } else {
+      // hidden-layer backward: dZ = acc * GELU'(z)
+      uint4 zk[4];
+      load_rows_bf16(zk, wbuf, e.z + (size_t)row0 * e.ldz + col0, e.ldz, nrows, lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bf16* zin = (const bf16*)&zk[q];
+        __align__(16) bf16 t[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = __float2bfloat16_rn(v[8 * q + i] * dgelu_f(__bfloat162float(zin[i])));
+        *(uint4*)(wbuf + stage_slot(lane, q)) = *(const uint4*)t;
+      }
+      flush_rows_bf16(wbuf, (bf16*)e.out + (size_t)row0 * e.ldo + col0, e.ldo, nrows, lane);
+    }
+    return;
+  }
+  if (row - row0 >= nrows) return;
+  // every loop below is unrolled over the 32 columns with the ragged bound as a predicate: an
+  // index that depends on nv would put the accumulator chunk into local memory
   if (EPI == 0 || EPI == 1) {   // + bias
     if (e.bias) {
 #pragma unroll
@@ -93,9 +188,12 @@ __device__ __forceinline__ void epi_chunk(float (&v)[32], int row, int col0, int
         if (zo) *(uint4*)(zo + 8 * q) = *(const uint4*)u;
       }
     } else {
-      for (int i = 0; i < nv; ++i) {
-        o[i] = __float2bfloat16_rn(gelu_f(v[i]));
-        if (zo) zo[i] = __float2bfloat16_rn(v[i]);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        if (i < nv) {
+          o[i] = __float2bfloat16_rn(gelu_f(v[i]));
+          if (zo) zo[i] = __float2bfloat16_rn(v[i]);
+        }
       }
     }
   } else if (EPI == 1 || EPI == 3) {
@@ -105,31 +203,24 @@ __device__ __forceinline__ void epi_chunk(float (&v)[32], int row, int col0, int
 #pragma unroll
       for (int q = 0; q < 8; ++q) *(float4*)(o + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     } else {
-      for (int i = 0; i < nv; ++i) o[i] = v[i];
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (i < nv) o[i] = v[i];
     }
   } else if (EPI == 2) {
     // hidden-layer backward: dZ = acc * GELU'(z)
     const bf16* zz = e.z + (size_t)row * e.ldz + col0;
     bf16* o = (bf16*)e.out + (size_t)row * e.ldo + col0;
-    if (nv == 32) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        __align__(16) bf16 zin[8], t[8];
-        *(uint4*)zin = __ldg((const uint4*)(zz + 8 * q));
-#pragma unroll
-        for (int i = 0; i < 8; ++i) t[i] = __float2bfloat16_rn(v[8 * q + i] * dgelu_f(__bfloat162float(zin[i])));
-        *(uint4*)(o + 8 * q) = *(const uint4*)t;
-      }
-    } else {
-      for (int i = 0; i < nv; ++i) o[i] = __float2bfloat16_rn(v[i] * dgelu_f(__bfloat162float(zz[i])));
-    }
+    for (int i = 0; i < 32; ++i)
+      if (i < nv) o[i] = __float2bfloat16_rn(v[i] * dgelu_f(__bfloat162float(zz[i])));
   }
 }
 
 // S (1..STAGES, a launch argument) stages in the ring: min(STAGES, K slabs), so that a
 // short K takes less shared memory and more CTAs share an SM
 template <int BN, int EPI>
-__global__ void __launch_bounds__(256) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
+__global__ void __launch_bounds__(256, 4) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
                                                            const __grid_constant__ CUtensorMap tb,
                                                            GemmEpi e, int M, int N, int K, int S, int* err) {
   using C = TileCfg<BN>;
@@ -141,6 +232,7 @@ __global__ void __launch_bounds__(256) gemm_bf16_kernel(const __grid_constant__ 
   uint64_t* empty = full + S;
   uint64_t* done = empty + S;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint8_t* stage = (uint8_t*)(((uintptr_t)(tmem_slot + 4) + 127) & ~(uintptr_t)127);   // 8 warps x 2 KB
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // N tiles fastest: the CTAs of one row block run together and share its A rows in L2
@@ -194,14 +286,17 @@ __global__ void __launch_bounds__(256) gemm_bf16_kernel(const __grid_constant__ 
     // 8 epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (the rows it may access) and
     // every second 32-column chunk starting at chunk w / 4
     const int quarter = warp & 3;
-    const int row = m0 + quarter * 32 + lane;
+    const int row0 = m0 + quarter * 32, row = row0 + lane;
+    const int nrows = max(0, min(32, M - row0));
+    uint8_t* wbuf = stage + warp * kEpiWarpBytes;
 #pragma unroll 1
     for (int c0 = (warp >> 2) * 32; c0 < BN; c0 += 64) {
       if (n0 + c0 >= N) break;
       float v[32];
       tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
-      if (row < M)   // no early exit: the next tcgen05.ld needs the whole warp
-        epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), e);
+      // the whole warp takes part (no early exit): the next tcgen05.ld and the staged stores
+      // need every lane
+      epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), e, wbuf, row0, nrows, lane);
       __syncwarp();
     }
   }
@@ -223,12 +318,14 @@ template <int BN>
 struct PersistCfg {
   static constexpr size_t A_BYTES = (size_t)tc::BM * tc::BK * 2;
   static constexpr size_t B_BYTES = (size_t)BN * tc::BK * 2;
-  // as many stages as fit in 220 KB (at most 8): the ring must cover the L2 latency
-  static constexpr int STAGES = (int)((220 * 1024) / (A_BYTES + B_BYTES)) < 8
-                                    ? (int)((220 * 1024) / (A_BYTES + B_BYTES)) : 8;
+  // as many stages as fit in 204 KB (at most 8; the ring must cover the L2 latency), leaving
+  // 16 KB for the epilogue warps' staging buffers
+  static constexpr int STAGES = (int)((204 * 1024) / (A_BYTES + B_BYTES)) < 8
+                                    ? (int)((204 * 1024) / (A_BYTES + B_BYTES)) : 8;
   static constexpr uint32_t ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
-  static constexpr size_t SMEM = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 4) * 8 + 16;
+  static constexpr size_t SMEM = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 4) * 8 + 16 + 128 +
+                                 8 * kEpiWarpBytes;
 };
 
 __device__ __forceinline__ bool gemm_failed(const int* err) { return *(const volatile int*)err != 0; }
@@ -247,6 +344,7 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_persistent(const __grid_cons
   uint64_t* accf = empty + S;    // [2]
   uint64_t* acce = accf + 2;     // [2]
   uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+  uint8_t* stage = (uint8_t*)(((uintptr_t)(tmem_slot + 4) + 127) & ~(uintptr_t)127);   // 8 warps x 2 KB
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkb = (K + tc::BK - 1) / tc::BK;
@@ -330,7 +428,9 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_persistent(const __grid_cons
       tc::tc_fence_after();
       const int gr = t / per_group, r = t - gr * per_group;
       const int m0 = (r / n_tiles) * tc::BM, n0 = (r % n_tiles) * BN;
-      const int row = m0 + quarter * 32 + lane;
+      const int row0 = m0 + quarter * 32, row = row0 + lane;
+      const int nrows = max(0, min(32, M - row0));
+      uint8_t* wbuf = stage + (warp - 2) * kEpiWarpBytes;
       GemmEpi eg = e;
       if (gr) {
         constexpr size_t osz = (EPI == 0 || EPI == 2) ? 2 : 4;
@@ -345,8 +445,9 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_persistent(const __grid_cons
         if (n0 + c0 >= N) break;
         float v[32];
         tc::tmem_ld32(acc + (uint32_t)c0, v);
-        if (row < M)   // no early exit: the next tcgen05.ld needs the whole warp
-          epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), eg);
+        // the whole warp takes part (no early exit): the next tcgen05.ld and the staged
+        // stores need every lane
+        epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), eg, wbuf, row0, nrows, lane);
         __syncwarp();
       }
       tc::tc_fence_before();
@@ -419,7 +520,8 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
       pconfigured = true;
     }
     const int S = nkb_all < P::STAGES ? nkb_all : P::STAGES;
-    const size_t smem = 1024 + (size_t)S * (P::A_BYTES + P::B_BYTES) + (2 * (size_t)S + 4) * 8 + 16;
+    const size_t smem = 1024 + (size_t)S * (P::A_BYTES + P::B_BYTES) + (2 * (size_t)S + 4) * 8 + 16 + 128 +
+                        8 * (size_t)kEpiWarpBytes;
     const int64_t total = (int64_t)((N + BN - 1) / BN) * ((M + tc::BM - 1) / tc::BM) * G;
     if (total > 0x7fffffff) return set_error(CHEM_E_ARG, "gemm: too many tiles in one call");
     static int sms = 0;
@@ -443,7 +545,8 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
   }
   const int nkb = (K + tc::BK - 1) / tc::BK;
   const int S = nkb < Cfg::STAGES ? nkb : Cfg::STAGES;
-  const size_t smem = 1024 + (size_t)S * (Cfg::A_BYTES + Cfg::B_BYTES) + (2 * (size_t)S + 2) * 8 + 16;
+  const size_t smem = 1024 + (size_t)S * (Cfg::A_BYTES + Cfg::B_BYTES) + (2 * (size_t)S + 2) * 8 + 16 + 128 +
+                      8 * (size_t)kEpiWarpBytes;
   if ((M + tc::BM - 1) / tc::BM > 65535) return set_error(CHEM_E_ARG, "gemm: more than 65535 row blocks in one call");
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + tc::BM - 1) / tc::BM));
   gemm_bf16_kernel<BN, EPI><<<grid, 256, smem, s>>>(ta, tb, e, M, N, K, S, err);
