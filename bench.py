@@ -3,7 +3,7 @@
 
 One step = one pass of the hot path over one batch of synthetic cells resident in HBM:
 direct integration of Eq. 2 for every cell (FP64 BDF, chem_step_di) followed by the mixture
-property update (thermo_props).  Default workload: the 30-species / 180-reaction (8 Troe)
+property update (thermo_props, FP64).  Default workload: the 30-species / 180-reaction (8 Troe)
 synthetic C/H/O/N mechanism, 1,000,000 cells, dt = 5e-6 s.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--cells C]
@@ -100,10 +100,17 @@ def di_flop_model(m: wl.Mechanism) -> dict:
     return dict(rhs=f_rhs, jac=f_jac, lu=f_lu, solve=f_solve, step=30 * n)
 
 
-def thermo_fp64_flops(K: int) -> int:
-    """FP64 flops per cell of the mixed-precision property kernel: sum Y_k/W_k (K FMAs), the
-    six mixture coefficients A_i = sum_k Y_k a_ik/W_k (6K FMAs), c_p and h from them (~20)."""
-    return 2 * K + 2 * 6 * K + 20
+def thermo_fp64_flops(K: int, mixed: bool) -> int:
+    """FP64 flops per cell of the property kernel.  Both modes: sum Y_k/W_k (K FMAs), the six
+    mixture coefficients A_i = sum_k Y_k a_ik/W_k (6K FMAs), c_p and h from them (~20).  FP64
+    mode also: ln T and the reciprocals (~40); per species the mole fraction (2), the ln mu and
+    ln lambda cubics (12), four exponentials (4 (EXP + 1)), the conductivity sums (4) and
+    X/s, X/s^2 (2); Wilke's three sums (3 FMAs = 6 flops per species pair) and per species the
+    denominator, the reciprocal and the sum (17).  The mixed mode's transport runs in FP32."""
+    base = 2 * K + 2 * 6 * K + 20
+    if mixed:
+        return base
+    return base + 40 + K * (2 + 12 + 4 * (EXP_FLOPS + 1) + 4 + 2 + 17) + 6 * K * K
 
 
 def di_flops(stats: np.ndarray, fm: dict) -> float:
@@ -663,7 +670,7 @@ def main():
         chem.chem_step_di(gm, cfg["dt"], T, p, Y, status, rtol=DI_RTOL, stats=stats, workspace=ws)
         if i is not None:
             ev[i][1].record(stream)
-        chem.thermo_props(gm, T, Y, cp, h, mu, kap, mixed_precision=True)
+        chem.thermo_props(gm, T, Y, cp, h, mu, kap, mixed_precision=False)
         if i is not None:
             ev[i][2].record(stream)
 
@@ -695,20 +702,20 @@ def main():
     achieved_tf = flops / (di_ms * 1e-3) / 1e12
     th_bytes = N * (m.n_species + 1) * 8 + N * 4 * 8
     th_gbs = th_bytes / (th_ms * 1e-3) / 1e9
-    th_flops_cell = thermo_fp64_flops(m.n_species)
+    th_flops_cell = thermo_fp64_flops(m.n_species, mixed=False)
     th_tf = th_flops_cell * N / (th_ms * 1e-3) / 1e12
 
-    # the properties in full FP64 (the config's precision) beside the step's mixed mode
-    th64 = []
+    # the properties in the mixed mode (FP32 transport sums) beside the step's FP64 mode
+    thm = []
     for r in range(6):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        chem.thermo_props(gm, T, Y, cp, h, mu, kap, mixed_precision=False)
+        chem.thermo_props(gm, T, Y, cp, h, mu, kap, mixed_precision=True)
         e1.record(stream)
         torch.cuda.synchronize()
         if r:
-            th64.append(e0.elapsed_time(e1))
-    th64_ms = float(np.median(th64))
+            thm.append(e0.elapsed_time(e1))
+    thm_ms = float(np.median(thm))
 
     # PaSR filtered source from this step (Y0 -> Y after DI) with seeded sub-grid fields
     pasr = run_pasr(gm, m, N, cfg["dt"], Y0, Y, cfg["state_seed"] + 3, dev)
@@ -724,7 +731,7 @@ def main():
         T.copy_(hT, non_blocking=True)
         Y.copy_(hY, non_blocking=True)
         chem.chem_step_di(gm, cfg["dt"], T, p, Y, status, rtol=DI_RTOL, workspace=ws)
-        chem.thermo_props(gm, T, Y, cp, h, mu, kap, mixed_precision=True)
+        chem.thermo_props(gm, T, Y, cp, h, mu, kap, mixed_precision=False)
         oT.copy_(T, non_blocking=True)
         oY.copy_(Y, non_blocking=True)
         ost.copy_(status, non_blocking=True)
@@ -761,7 +768,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": N, "species": m.n_species,
                        "reactions": m.n_reactions, "dt": cfg["dt"], "di_rtol": DI_RTOL,
-                       "step": "chem_step_di (FP64 BDF) + thermo_props (mixed precision)",
+                       "step": "chem_step_di (FP64 BDF) + thermo_props (FP64)",
                        "l2": f"inputs {N * (m.n_species + 1) * 8 / 1e6:.0f} MB > 129 MB L2",
                        "parallelism": f"dp{world} (independent cells, no collective)"},
             "di_cells_per_s": N / (di_ms * 1e-3), "di_ms": di_ms, "thermo_ms": th_ms,
@@ -776,14 +783,15 @@ def main():
                          "traffic": DI_DRAM_BYTES_PER_CELL * N, "kernel": "di_kernel (FP64 DFMA pipe)",
                          "peak_source": "measured live: chem_fp64_peak_gflops DFMA probe"},
             "thermo_roofline": {"bound": "alu", "achieved": th_tf, "peak": peak_gf / 1e3, "unit": "TFLOP/s",
-                                "frac": th_tf / (peak_gf / 1e3), "kernel": "thermo_kernel (mixed precision)",
+                                "frac": th_tf / (peak_gf / 1e3), "kernel": "thermo_kernel (FP64)",
                                 "flops_per_cell": th_flops_cell,
-                                "note": "FP64 c_p/h mixture sums bound it; HBM side: "
+                                "note": "FP64 Wilke sums (3 FMAs per species pair) bound it; HBM side: "
                                         f"{th_gbs:.0f} GB/s = {th_gbs / hbm:.3f} of {hbm:.0f} (hbm_gbs {PEAKS['source']})",
                                 "hbm_gbs": th_gbs, "hbm_frac": th_gbs / hbm},
-            "thermo_fp64": {"ms": th64_ms, "cells_per_s": N / (th64_ms * 1e-3),
-                            "note": "thermo_props with every sum in FP64 (Wilke, conductivity included), "
-                                    "same 1,000,000 cells; the step uses the mixed mode"},
+            "thermo_mixed": {"ms": thm_ms, "cells_per_s": N / (thm_ms * 1e-3),
+                             "fp64_flops_per_cell": thermo_fp64_flops(m.n_species, mixed=True),
+                             "note": "thermo_props with the O(K^2) transport sums in FP32 (c_p, h in FP64), "
+                                     "same 1,000,000 cells; the step uses the FP64 mode"},
             "config0": cfg0,
             "config4": cfg4,
             "peaks": PEAKS,

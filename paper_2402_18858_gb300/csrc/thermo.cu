@@ -26,8 +26,7 @@ template <typename real>
 struct ThermoSmem {
   double* c;     // [2][6][K]  a_qk / W_k
   real* tr;      // [8][K]     ln mu (4), ln lambda (4)
-  real* wA;      // FP64 mode: [K][K] A_kj
-  real* wB;      // FP64 mode: [K][K] B_kj
+  double* w3d;   // FP64 mode: [3][K][K] A_kj, A_kj B_kj, A_kj B_kj^2
   float4* w3;    // mixed mode: [K][K] (A, A B, A B^2, 0)
   float* invW;   // mixed mode: [K]
 };
@@ -36,7 +35,7 @@ template <typename real>
 __host__ __device__ inline size_t thermo_smem_bytes(int K, bool transport) {
   size_t b = (size_t)12 * K * sizeof(double);
   if (transport) {
-    if (sizeof(real) == sizeof(double)) b += ((size_t)8 * K + 2 * (size_t)K * K) * sizeof(real);
+    if (sizeof(real) == sizeof(double)) b += ((size_t)8 * K + 3 * (size_t)K * K) * sizeof(double);
     else b += (size_t)8 * K * sizeof(float) + (size_t)K * K * sizeof(float4) + (size_t)K * sizeof(float) + 16;
   }
   return b;
@@ -76,7 +75,7 @@ __global__ void __launch_bounds__(128) thermo_kernel(DevMech m, int64_t n, int64
   ThermoSmem<real> S;
   S.c = tsm;
   S.tr = (real*)(tsm + 12 * K);
-  S.wA = S.wB = nullptr;
+  S.w3d = nullptr;
   S.w3 = nullptr;
   S.invW = nullptr;
   if (MIXED) {
@@ -84,8 +83,7 @@ __global__ void __launch_bounds__(128) thermo_kernel(DevMech m, int64_t n, int64
     S.w3 = (float4*)(((uintptr_t)(S.tr + 8 * K) + 15) & ~(uintptr_t)15);
     S.invW = (float*)(S.w3 + K * K);
   } else {
-    S.wA = S.tr + 8 * K;
-    S.wB = S.wA + K * K;
+    S.w3d = (double*)(S.tr + 8 * K);
   }
   for (int i = threadIdx.x; i < 12 * K; i += blockDim.x) {
     const int rg = i / (6 * K), q = (i / K) % 6, k = i % K;
@@ -95,12 +93,13 @@ __global__ void __launch_bounds__(128) thermo_kernel(DevMech m, int64_t n, int64
   if (transport) {
     for (int i = threadIdx.x; i < 8 * K; i += blockDim.x) S.tr[i] = (real)__ldg(m.tr + (size_t)(i % K) * 8 + i / K);
     for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
+      const double A = __ldg(m.wA + i), B = __ldg(m.wB + i);
       if (MIXED) {
-        const double A = __ldg(m.wA + i), B = __ldg(m.wB + i);
         S.w3[i] = make_float4((float)A, (float)(A * B), (float)(A * B * B), 0.0f);
       } else {
-        S.wA[i] = (real)__ldg(m.wA + i);
-        S.wB[i] = (real)__ldg(m.wB + i);
+        S.w3d[i] = A;
+        S.w3d[K * K + i] = A * B;
+        S.w3d[2 * K * K + i] = A * B * B;
       }
     }
     if (MIXED)
@@ -176,41 +175,50 @@ __global__ void __launch_bounds__(128) thermo_kernel(DevMech m, int64_t n, int64
         mu_out[i] = (double)mu;
       }
     } else {
-      // FP64 reference form: Wilke mu = sum_k X_k mu_k / sum_j X_j Phi_kj,
-      // Phi_kj = (1 + sqrt(mu_k/mu_j) (W_j/W_k)^(1/4))^2 / sqrt(8 (1 + W_k/W_j)),
-      // mixture-averaged conductivity 0.5 (sum X lambda + 1 / sum X / lambda)
-      real X[KC ? KC : CHEM_MAX_SPECIES], smu[KC ? KC : CHEM_MAX_SPECIES], ismu[KC ? KC : CHEM_MAX_SPECIES];
-      const real isYW = (real)(1.0 / sYW);
-      const real L = (real)log(Tc);
-      real l1 = 0, l2 = 0;
+      // FP64: Wilke mu = sum_k X_k mu_k / sum_j X_j Phi_kj with
+      // Phi_kj = (1 + sqrt(mu_k/mu_j) (W_j/W_k)^(1/4))^2 / sqrt(8 (1 + W_k/W_j)) = A_kj (1 + s_k B_kj / s_j)^2,
+      // s = sqrt(mu), in the expanded form of the mixed mode (three sums of positive terms per
+      // species pair, no cancellation); mixture-averaged conductivity 0.5 (sum X lambda +
+      // 1 / sum X / lambda).  Exponentials by the table-driven exp, reciprocals by Newton's
+      // iteration (both within about 2 ulp).
+      const double* __restrict__ et = m.exptab;
+      double X[KC ? KC : CHEM_MAX_SPECIES], sm[KC ? KC : CHEM_MAX_SPECIES];
+      double vx[KC ? KC : CHEM_MAX_SPECIES], wx[KC ? KC : CHEM_MAX_SPECIES];
+      const double isYW = rcp_nr(sYW);
+      const double L = log_t(Tc, m.logtab);
+      double l1 = 0.0, l2 = 0.0;
 #pragma unroll
       for (int k = 0; k < (KC ? KC : K); ++k) {
-        X[k] = (real)(yv[k] * __ldg(m.invW + k)) * isYW;
-        const real lnmu = S.tr[k] + L * (S.tr[K + k] + L * (S.tr[2 * K + k] + L * S.tr[3 * K + k]));
-        const real lnlam = S.tr[4 * K + k] + L * (S.tr[5 * K + k] + L * (S.tr[6 * K + k] + L * S.tr[7 * K + k]));
-        smu[k] = exp(lnmu * (real)0.5);
-        ismu[k] = (real)1 / smu[k];
-        const real lam = exp(lnlam);
-        l1 += X[k] * lam;
-        l2 += X[k] / lam;
+        X[k] = yv[k] * __ldg(m.invW + k) * isYW;
+        const double lnmu = S.tr[k] + L * (S.tr[K + k] + L * (S.tr[2 * K + k] + L * S.tr[3 * K + k]));
+        const double lnlam = S.tr[4 * K + k] + L * (S.tr[5 * K + k] + L * (S.tr[6 * K + k] + L * S.tr[7 * K + k]));
+        sm[k] = exp_t(0.5 * lnmu, et);
+        const double ism = exp_t(-0.5 * lnmu, et);
+        l1 = fma(X[k], exp_t(lnlam, et), l1);
+        l2 = fma(X[k], exp_t(-lnlam, et), l2);
+        vx[k] = X[k] * ism;
+        wx[k] = vx[k] * ism;
       }
-      if (kappa_out) kappa_out[i] = 0.5 * ((double)l1 + 1.0 / (double)l2);
+      if (kappa_out) kappa_out[i] = 0.5 * (l1 + rcp_nr(l2));
       if (mu_out) {
-        real mu = 0;
+        double mu = 0.0;
 #pragma unroll 2
         for (int k = 0; k < (KC ? KC : K); ++k) {
-          real den = 0;
-          const real sk = smu[k];
-          const real* A = S.wA + k * K;
-          const real* B = S.wB + k * K;
+          const double* W0 = S.w3d + k * K;
+          const double* W1 = W0 + K * K;
+          const double* W2 = W1 + K * K;
+          double d0 = 0.0, d1 = 0.0, d2 = 0.0;
 #pragma unroll
           for (int j = 0; j < (KC ? KC : K); ++j) {
-            const real t = (real)1 + sk * ismu[j] * B[j];
-            den += X[j] * A[j] * t * t;
+            d0 = fma(W0[j], X[j], d0);
+            d1 = fma(W1[j], vx[j], d1);
+            d2 = fma(W2[j], wx[j], d2);
           }
-          mu += X[k] * sk * sk / den;
+          const double sk = sm[k];
+          const double den = fma(sk, fma(sk, d2, 2.0 * d1), d0);
+          mu = fma(X[k] * sk * sk, rcp_nr(den), mu);
         }
-        mu_out[i] = (double)mu;
+        mu_out[i] = mu;
       }
     }
   }

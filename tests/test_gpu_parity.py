@@ -128,25 +128,27 @@ def test_thermo_T_from_h(lc, gmech, mechs, oracles):
 
 
 def test_thermo_props_full_size_sampled(lc, gmech, mechs, oracles):
-    """The benchmark's launch: mixed-precision properties of 1,000,000 cells of the 30-species
-    workload in one call; 400 sampled cells (and the ragged last one) against the oracle."""
+    """The benchmark's launches: FP64 properties of 1,000,000 cells of the 30-species workload in
+    one call (the step's mode) and the mixed mode beside it; 400 sampled cells (and the ragged
+    last one) against the oracle."""
     m, _ = mechs["c_30"]
     o = oracles["c_30"]
     cfg = w.WORKLOADS["di_c_30sp_1m"]
     st = w.make_states(m, cfg["n"], cfg["state_seed"])
     T, Y = _dev(st.T), _dev(st.Y)
-    cp, h, mu, kap = (torch.empty_like(T) for _ in range(4))
-    lc.thermo_props(gmech["c_30"], T, Y, cp, h, mu, kap, mixed_precision=True)
-    torch.cuda.synchronize()
-    got = [x.cpu().numpy() for x in (cp, h, mu, kap)]
     pick = np.sort(np.random.default_rng(1).choice(cfg["n"], 400, replace=False))
     pick[-1] = cfg["n"] - 1
-    for i in pick:
-        ref = o.thermo_props(st.T[i], st.Y[:, i])
-        assert got[0][i] == pytest.approx(ref[0], rel=1e-12)
-        assert got[1][i] == pytest.approx(ref[1], rel=1e-12, abs=1e-6 * abs(ref[0]))
-        assert got[2][i] == pytest.approx(ref[2], rel=2e-5)
-        assert got[3][i] == pytest.approx(ref[3], rel=2e-5)
+    for mixed, tol in ((False, 1e-12), (True, 2e-5)):
+        cp, h, mu, kap = (torch.empty_like(T) for _ in range(4))
+        lc.thermo_props(gmech["c_30"], T, Y, cp, h, mu, kap, mixed_precision=mixed)
+        torch.cuda.synchronize()
+        got = [x.cpu().numpy() for x in (cp, h, mu, kap)]
+        for i in pick:
+            ref = o.thermo_props(st.T[i], st.Y[:, i])
+            assert got[0][i] == pytest.approx(ref[0], rel=1e-12)
+            assert got[1][i] == pytest.approx(ref[1], rel=1e-12, abs=1e-6 * abs(ref[0]))
+            assert got[2][i] == pytest.approx(ref[2], rel=tol)
+            assert got[3][i] == pytest.approx(ref[3], rel=tol)
 
 
 # ------------------------------------------------------------------------------------------
