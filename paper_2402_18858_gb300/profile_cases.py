@@ -3,6 +3,7 @@
     python -m paper_2402_18858_gb300.profile_cases di --cells 8192
     python -m paper_2402_18858_gb300.profile_cases di --kind c_53 --mech-seed 5 --dt 1e-5 --cells 16384
     python -m paper_2402_18858_gb300.profile_cases thermo --cells 1048576
+    python -m paper_2402_18858_gb300.profile_cases thermo64 --cells 1048576
     python -m paper_2402_18858_gb300.profile_cases mlp --cells 65536
     python -m paper_2402_18858_gb300.profile_cases mlp_ps --cells 65536
     python -m paper_2402_18858_gb300.profile_cases rates --cells 65536
@@ -30,7 +31,7 @@ CKPT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models", "ann_c
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["di", "thermo", "mlp", "mlp_ps", "rates", "jacobian", "pasr"])
+    ap.add_argument("case", choices=["di", "thermo", "thermo64", "mlp", "mlp_ps", "rates", "jacobian", "pasr"])
     ap.add_argument("--cells", type=int, default=8192)
     ap.add_argument("--repeats", type=int, default=2)
     ap.add_argument("--kind", default=MECH[0], help="mechanism kind (the DI case only; default c_30)")
@@ -81,11 +82,12 @@ def main():
 
         def run():
             chem.chem_pasr_source(gm, 5e-6, rho, Y0, Y1, k, eps, nu, omega, kap)
-    elif a.case == "thermo":
+    elif a.case in ("thermo", "thermo64"):
         outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4)]
+        mixed = a.case == "thermo"
 
         def run():
-            chem.thermo_props(gm, T0, Y0, *outs, mixed_precision=True)
+            chem.thermo_props(gm, T0, Y0, *outs, mixed_precision=mixed)
     elif a.case == "mlp_ps":
         # one 1600-800-400 network per species (grouped GEMMs), random weights
         ann0 = chem.chem_ann_load(gm, CKPT)
