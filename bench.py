@@ -560,8 +560,8 @@ def run_serve(args, m30, g30, ann_leg, di_rate30):
         st = wl.make_states(mm, int(sizes[i]), 50_000 + i)
         payload.append((st, np.empty(sizes[i]), np.empty((mm.n_species, sizes[i])),
                         np.empty(sizes[i], dtype=np.int32)))
-    sv = chem.chem_server_create(hbm_budget_bytes=16 << 30, n_streams=2, max_batch_cells=1 << 20,
-                                 starvation_s=30.0, di_chunk_cells=32768)
+    sv = chem.chem_server_create(hbm_budget_bytes=16 << 30, n_streams=args.serve_streams, max_batch_cells=1 << 20,
+                                 starvation_s=30.0, di_chunk_cells=args.serve_chunk)
     c30 = chem.chem_server_add_class(sv, g30, a30, capacity_cells=1 << 23)
     c9 = chem.chem_server_add_class(sv, g9, a9, capacity_cells=1 << 23)
     reqs = []
@@ -598,8 +598,8 @@ def run_serve(args, m30, g30, ann_leg, di_rate30):
             "failed": stt["failed"], "latency_by_kind": breakdown,
             "p99_cause": "the largest 30-species DI requests: their own GPU time (up to 2e6 cells at the DI "
                          "rate) sets the tail; pieces of 32,768 cells keep them from holding back small requests",
-            "scheduler": "pieces of <= 32,768 cells per DI request per launch, kind with the least work left "
-                         "first, 30 s starvation limit, 2 streams"}
+            "scheduler": f"pieces of <= {args.serve_chunk} cells per DI request per launch, kind with the least "
+                         f"work left first, 30 s starvation limit, {args.serve_streams} streams"}
 
 
 # ------------------------------------------------------------------------------------------
@@ -620,6 +620,8 @@ def main():
     ap.add_argument("--ann-epochs", type=int, default=24)
     ap.add_argument("--ann-cells", type=int, default=2_000_000)
     ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-streams", type=int, default=2)
+    ap.add_argument("--serve-chunk", type=int, default=32768, help="cells of a DI request per launch")
     ap.add_argument("--oracle-err-cells", type=int, default=512,
                     help="cells of the timed learned-step batch compared with the FP64 oracle")
     ap.add_argument("--oracle-err-cells-c53", type=int, default=128)
