@@ -553,13 +553,26 @@ def run_serve(args, m30, g30, ann_leg, di_rate30):
                    np.where(mode == 1, 1.0 / ev9["ann_cells_per_s"], 1.0 / di_rate9)) * sizes
     lam = 0.7 / svc.mean()                 # arrivals at 70 % of the measured capacity
     gaps = rng.exponential(1.0 / lam, R)
-    # the requests' states, made before the clock starts
+    # the requests' states, made before the clock starts, in pinned host memory: copies from
+    # and to pageable memory would block the server's scheduler thread until they complete
+    keep = []
+
+    def pinned(a=None, shape=None, dtype=np.float64):
+        if a is not None:
+            shape, dtype = a.shape, a.dtype
+        t = torch.empty(shape, dtype={np.float64: torch.float64, np.int32: torch.int32}[np.dtype(dtype).type],
+                        pin_memory=True)
+        keep.append(t)
+        v = t.numpy()
+        if a is not None:
+            v[...] = a
+        return v
     payload = []
     for i in range(R):
         mm = m30 if kind[i] else m9
         st = wl.make_states(mm, int(sizes[i]), 50_000 + i)
-        payload.append((st, np.empty(sizes[i]), np.empty((mm.n_species, sizes[i])),
-                        np.empty(sizes[i], dtype=np.int32)))
+        payload.append(((pinned(st.T), pinned(st.p), pinned(st.Y)), pinned(shape=(sizes[i],)),
+                        pinned(shape=(mm.n_species, sizes[i])), pinned(shape=(sizes[i],), dtype=np.int32)))
     sv = chem.chem_server_create(hbm_budget_bytes=16 << 30, n_streams=args.serve_streams, max_batch_cells=1 << 20,
                                  starvation_s=30.0, di_chunk_cells=args.serve_chunk)
     c30 = chem.chem_server_add_class(sv, g30, a30, capacity_cells=1 << 23)
@@ -568,18 +581,18 @@ def run_serve(args, m30, g30, ann_leg, di_rate30):
     t0 = time.perf_counter()
     for i in range(R):
         cls, dt = (c30, wl.WORKLOADS[WORKLOAD]["dt"]) if kind[i] else (c9, 1e-6)
-        st, To, Yo, so = payload[i]
+        (T_in, p_in, Y_in), To, Yo, so = payload[i]
         target = t0 + gaps[:i + 1].sum()
         while time.perf_counter() < target:
             time.sleep(min(1e-3, max(0.0, target - time.perf_counter())))
-        reqs.append(chem.chem_server_submit(sv, cls, int(mode[i]), dt, st.T, st.p, st.Y, To, Yo, so))
+        reqs.append(chem.chem_server_submit(sv, cls, int(mode[i]), dt, T_in, p_in, Y_in, To, Yo, so))
     for r in reqs:
         done, res = chem.chem_server_wait(sv, r, 900.0)
         if not done or res != 0:
             raise RuntimeError(f"serving request {r} did not complete ({done}, {res})")
     stt = chem.chem_server_stats(sv)
     lat = np.array([chem.chem_server_request_latency(sv, r) for r in reqs])
-    del sv
+    del sv, payload, keep
 
     def pct(sel):
         v = lat[sel]
@@ -597,7 +610,9 @@ def run_serve(args, m30, g30, ann_leg, di_rate30):
             "mean_batch_requests": stt["mean_batch_requests"], "wall_s": stt["wall_s"],
             "failed": stt["failed"], "latency_by_kind": breakdown,
             "p99_cause": "the largest 30-species DI requests: their own GPU time (up to 2e6 cells at the DI "
-                         "rate) sets the tail; pieces of 32,768 cells keep them from holding back small requests",
+                         f"rate) sets the tail; pieces of {args.serve_chunk} cells keep them from holding back "
+                         "small requests",
+            "host_buffers": "pinned",
             "scheduler": f"pieces of <= {args.serve_chunk} cells per DI request per launch, kind with the least "
                          f"work left first, 30 s starvation limit, {args.serve_streams} streams"}
 

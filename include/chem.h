@@ -335,8 +335,9 @@ typedef struct {
  * di_chunk_cells per launch and a batch at most max_batch_cells.  Each piece's results are
  * copied back when its launch ends; a request completes with its last piece and frees its
  * columns.  Host arrays passed to chem_server_submit must stay valid until the request
- * completes (pinned memory gives asynchronous copies).  Per-cell results do not depend on the
- * batch composition or on the piece a cell runs in. */
+ * completes.  Pass pinned (page-locked) host memory: a copy from or to pageable memory blocks
+ * the scheduler thread until it ends, which serialises the streams.  Per-cell results do not
+ * depend on the batch composition or on the piece a cell runs in. */
 int chem_server_create(const chem_server_opts* opts, chem_server* out);
 /* Register a class: a mechanism (and optionally a trained ANN for mode 1) with an arena of
  * capacity_cells columns.  Classes are added before the first submit. */
