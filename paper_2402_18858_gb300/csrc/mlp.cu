@@ -24,28 +24,41 @@ using bf16 = __nv_bfloat16;
 // approximation of Abramowitz & Stegun, Handbook of Mathematical Functions, eq. 7.1.26
 // (Hastings): erf z = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-z^2}, t = 1 / (1 + p z),
 // z >= 0, |error| <= 1.5e-7 (6e-7 in FP32 arithmetic); GELU within 2.1e-7 max(1, |x|), far below
-// the BF16 rounding of the outputs.  One reciprocal and one exponential on the special-function
-// unit, shared by GELU' through e^{-z^2} = e^{-x^2/2}.
+// the BF16 rounding of the outputs.  Arranged for few instructions: with a = |x| and z = a/sqrt2,
+// w = (1 - erf z)/2 = t q(t) e^{-x^2/2} with the a_i halved and p/sqrt2 folded into t, and then
+// Phi(x) = x >= 0 ? 1 - w : w, GELU x = x Phi(x), GELU' x = Phi(x) + x e^{-x^2/2} / sqrt(2 pi).
+// One reciprocal and one base-2 exponential on the special-function unit.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ float erf_as(float z, float& ez2) {
-  const float az = fabsf(z);
-  const float t = __fdividef(1.0f, fmaf(0.3275911f, az, 1.0f));
-  float q = fmaf(t, 1.061405429f, -1.453152027f);
-  q = fmaf(q, t, 1.421413741f);
-  q = fmaf(q, t, -0.284496736f);
-  q = fmaf(q, t, 0.254829592f);
-  ez2 = __expf(-az * az);
-  return copysignf(fmaf(-q * t, ez2, 1.0f), z);
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// w = (1 - erf(|x| / sqrt2)) / 2 and e = e^{-x^2/2}
+__device__ __forceinline__ float half_erfc_as(float x, float& e) {
+  const float t = rcp_approx(fmaf(0.3275911f * 0.70710678118654752f, fabsf(x), 1.0f));
+  float q = fmaf(t, 0.5f * 1.061405429f, 0.5f * -1.453152027f);
+  q = fmaf(q, t, 0.5f * 1.421413741f);
+  q = fmaf(q, t, 0.5f * -0.284496736f);
+  q = fmaf(q, t, 0.5f * 0.254829592f);
+  e = ex2_approx((x * -0.72134752044448170f) * x);   // -log2(e) / 2
+  return (q * t) * e;
 }
 __device__ __forceinline__ float gelu_f(float x) {
-  float ez2;
-  const float e = erf_as(x * 0.70710678118654752f, ez2);
-  return 0.5f * x * (1.0f + e);
+  float e;
+  const float w = half_erfc_as(x, e);
+  const float r = x * w;
+  return x >= 0.0f ? x - r : r;
 }
 __device__ __forceinline__ float dgelu_f(float x) {
-  float ez2;
-  const float e = erf_as(x * 0.70710678118654752f, ez2);
-  return fmaf(x * 0.39894228040143268f, ez2, 0.5f * (1.0f + e));
+  float e;
+  const float w = half_erfc_as(x, e);
+  return fmaf(x * 0.39894228040143268f, e, x >= 0.0f ? 1.0f - w : w);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -217,6 +230,34 @@ __device__ __forceinline__ void epi_chunk(float (&v)[32], int row, int col0, int
   }
 }
 
+// Epilogue 4 (short-K kernel only): the hidden-layer forward of epilogue 0 without the
+// pre-activation copy, N a multiple of 32.  Each 32-column chunk is read from TMEM in four
+// 8-column pieces: with a whole 32-float chunk plus the GELU temporaries live, the short-K
+// kernel's 64 registers per thread spill.
+__device__ __forceinline__ void epi_gelu_x8(uint32_t taddr, int col0, const GemmEpi& e, uint8_t* wbuf,
+                                            int row0, int nrows, int lane) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    float v[8];
+    tc::tmem_ld8(taddr + 8 * h, v);
+    if (e.bias) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float4 b4 = __ldg((const float4*)(e.bias + col0 + 8 * h) + q);
+        v[4 * q] += b4.x;
+        v[4 * q + 1] += b4.y;
+        v[4 * q + 2] += b4.z;
+        v[4 * q + 3] += b4.w;
+      }
+    }
+    __align__(16) bf16 t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t[i] = __float2bfloat16_rn(gelu_f(v[i]));
+    *(uint4*)(wbuf + stage_slot(lane, h)) = *(const uint4*)t;
+  }
+  flush_rows_bf16(wbuf, (bf16*)e.out + (size_t)row0 * e.ldo + col0, e.ldo, nrows, lane);
+}
+
 // S (1..STAGES, a launch argument) stages in the ring: min(STAGES, K slabs), so that a
 // short K takes less shared memory and more CTAs share an SM
 template <int BN, int EPI>
@@ -292,11 +333,16 @@ __global__ void __launch_bounds__(256, 4) gemm_bf16_kernel(const __grid_constant
 #pragma unroll 1
     for (int c0 = (warp >> 2) * 32; c0 < BN; c0 += 64) {
       if (n0 + c0 >= N) break;
-      float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
       // the whole warp takes part (no early exit): the next tcgen05.ld and the staged stores
       // need every lane
-      epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), e, wbuf, row0, nrows, lane);
+      if constexpr (EPI == 4) {
+        epi_gelu_x8(taddr, n0 + c0, e, wbuf, row0, nrows, lane);
+      } else {
+        float v[32];
+        tc::tmem_ld32(taddr, v);
+        epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), e, wbuf, row0, nrows, lane);
+      }
       __syncwarp();
     }
   }
@@ -508,7 +554,9 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
   if ((rc = make_map(&ta, A, M + (int64_t)(G - 1) * e.a_row, K + (int64_t)(G - 1) * e.a_col, lda, tc::BM))) return rc;
   if ((rc = make_map(&tb, B, N + (int64_t)(G - 1) * e.b_row, K + (int64_t)(G - 1) * e.b_col, ldb, BN))) return rc;
   const int nkb_all = (K + tc::BK - 1) / tc::BK;
-  if (nkb_all > 2 || G > 1) {
+  if constexpr (EPI == 4) {
+    if (nkb_all > 2 || G > 1 || N % 32) return set_error(CHEM_E_ARG, "gemm: epilogue 4 needs K <= 128, N % 32 == 0");
+  } else if (nkb_all > 2 || G > 1) {
     // long K: persistent warp-specialised kernel, one CTA per SM
     using P = PersistCfg<BN>;
     static bool pconfigured = false;
@@ -582,10 +630,14 @@ int gemm_bf16(int epi, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, i
       if (padded < best) { best = padded; bn = c; }
     }
   }
+  // the first layer's forward without a pre-activation copy: the short-K kernel's lean GELU epilogue
+  const bool gelu_x8 = epi == 0 && !e.zout && e.groups <= 1 && K <= 2 * tc::BK && N % 32 == 0;
 #define CHEM_GEMM_CASE(BNV)                                                                    \
   if (bn == BNV) {                                                                             \
     switch (epi) {                                                                             \
-      case 0: return launch_gemm_t<BNV, 0>(A, lda, B, ldb, M, N, K, e, err, s);                \
+      case 0:                                                                                  \
+        if (gelu_x8) return launch_gemm_t<BNV, 4>(A, lda, B, ldb, M, N, K, e, err, s);         \
+        return launch_gemm_t<BNV, 0>(A, lda, B, ldb, M, N, K, e, err, s);                      \
       case 1: return launch_gemm_t<BNV, 1>(A, lda, B, ldb, M, N, K, e, err, s);                \
       case 2: return launch_gemm_t<BNV, 2>(A, lda, B, ldb, M, N, K, e, err, s);                \
       default: return launch_gemm_t<BNV, 3>(A, lda, B, ldb, M, N, K, e, err, s);               \
