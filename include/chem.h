@@ -432,6 +432,12 @@ int chem_selftest_exp(chem_mech mech, int64_t n, const double* x, double* y, che
  * pointers, n >= 0. */
 int chem_selftest_log(chem_mech mech, int64_t n, const double* x, double* y, chem_stream stream);
 
+/* Testing hook: y[i] = 1/x[i] by the library's own FP64 reciprocal (hardware estimate plus one
+ * third-order refinement step, used for every reciprocal of the integration and property
+ * kernels), for comparison with IEEE division.  Within 1 ulp for normal x whose reciprocal is
+ * normal; zero and infinite x give NaN.  Device pointers, n >= 0. */
+int chem_selftest_rcp(int64_t n, const double* x, double* y, chem_stream stream);
+
 /* Testing hook: one tensor-core GEMM of the MLP, out = epi(A B^T) with A [M, K] and B [N, K]
  * BF16 row-major (K a multiple of 8, 16-byte aligned), FP32 accumulation.  epi 0: GELU(acc +
  * bias) -> BF16; 1: acc + bias -> FP32; 2: acc * GELU'(z) -> BF16 with z [M, N] BF16;

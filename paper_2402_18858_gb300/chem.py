@@ -70,6 +70,7 @@ def lib(auto_build: bool = False):
         L.chem_fp64_peak_gflops.argtypes = [C.POINTER(dbl), vp]
         L.chem_selftest_exp.argtypes = [vp, i64, vp, vp, vp]
         L.chem_selftest_log.argtypes = [vp, i64, vp, vp, vp]
+        L.chem_selftest_rcp.argtypes = [i64, vp, vp, vp]
         L.chem_selftest_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.chem_selftest_gemm_grouped.argtypes = [i32, i32, i32, i32, i32, vp, i64, i32, i32, vp, i64, i32, i32,
                                                  vp, i32, vp, i64, i64, vp, i64, i64, vp, vp]
@@ -242,6 +243,10 @@ def chem_selftest_exp(m: Mech, x, y, stream=None) -> None:
 def chem_selftest_log(m: Mech, x, y, stream=None) -> None:
     _check(lib().chem_selftest_log(m.handle, x.numel(), _ptr(x, torch.float64),
                                    _ptr(y, torch.float64), _stream(stream)))
+
+
+def chem_selftest_rcp(x, y, stream=None) -> None:
+    _check(lib().chem_selftest_rcp(x.numel(), _ptr(x, torch.float64), _ptr(y, torch.float64), _stream(stream)))
 
 
 def chem_selftest_gemm(epi: int, A, B, out, bias=None, z=None, err=None, stream=None) -> None:

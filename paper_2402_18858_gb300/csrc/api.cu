@@ -659,6 +659,12 @@ int chem_selftest_log(chem_mech m, int64_t n, const double* x, double* y, chem_s
   return launch_log_selftest(m->dev, n, x, y, (cudaStream_t)stream);
 }
 
+int chem_selftest_rcp(int64_t n, const double* x, double* y, chem_stream stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return set_error(CHEM_E_ARG, "chem_selftest_rcp: bad arguments");
+  if (n == 0) return CHEM_OK;
+  return launch_rcp_selftest(n, x, y, (cudaStream_t)stream);
+}
+
 int chem_fp64_peak_gflops(double* gflops, chem_stream stream) {
   if (!gflops) return set_error(CHEM_E_ARG, "chem_fp64_peak_gflops: null output");
   return launch_fp64_probe(gflops, (cudaStream_t)stream);

@@ -33,6 +33,23 @@ __device__ __forceinline__ double wsum(double v) {
   return __shfl_sync(FULLMASK, v, 0);
 }
 
+// the sums of a and b over the warp with one addition per tree level: the first level adds a
+// in lanes 0-15 and b in lanes 16-31 (each lane keeps one value and sends the other across the
+// halves), the next four reduce each half into its first lane, which is broadcast
+__device__ __forceinline__ void wsum2(double a, double b, int lane, double& sa, double& sb) {
+  const bool lo = lane < 16;
+  double v = (lo ? a : b) + __shfl_xor_sync(FULLMASK, lo ? b : a, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_down_sync(FULLMASK, v, o, 16);
+  sa = __shfl_sync(FULLMASK, v, 0);
+  sb = __shfl_sync(FULLMASK, v, 16);
+}
+
+// x is finite, tested on its exponent bits (integer pipe)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned int)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7ff00000u) != 0x7ff00000u;
+}
+
 __device__ __forceinline__ float wsumf(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULLMASK, v, o);
@@ -212,7 +229,8 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
   const double T = comp_get<NPL>(y, K);
   const double lnT = log_t(T, m.logtab), RT = kR * T;
   const double* __restrict__ et = m.exptab;
-  const int hi = T >= m.Tmid ? 1 : 0;
+  // T >= T_mid on the bit patterns (both positive: they order like the values)
+  const int hi = __double_as_longlong(T) >= __double_as_longlong(m.Tmid) ? 1 : 0;
   // pass 1: c_p/R per species and the two mixture sums sum Y/W and sum Y c_p/(R W)
   double sYW = 0.0, cpp = 0.0, ywr[NPL];
 #pragma unroll
@@ -232,18 +250,17 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
       sp.cpR[s] = cpR;
     }
   }
-  sYW = wsum(sYW);
-  cpp = wsum(cpp);
+  wsum2(sYW, cpp, lane, sYW, cpp);
   // one division gives 1/T, the mean molar mass and 1/c_p
   const double TsY = T * sYW;
   const double inv = rcp_nr(TsY * cpp);
   const double invT = inv * (sYW * cpp);
-  const double Wbar = inv * (T * cpp);
+  const double Wbar = JAC ? inv * (T * cpp) : 0.0;   // the mean molar mass and c_p: Jacobian only
   const double icp = inv * TsY * (1.0 / kR);
   const double rho = p * (inv * cpp) * (1.0 / kR);   // p Wbar / (R T)
   const double irho = sYW * RT * ip;                 // 1 / rho
   const double ctot = rho * sYW;                     // sum of the concentrations
-  const double cp = cpp * kR;
+  const double cp = JAC ? cpp * kR : 0.0;
   // pass 2: h/RT, g/RT and the concentrations (and the sentinel slots of the two-partner
   // reactions, which the production-rate runs of the previous call may have overwritten)
   double Cs[NPL];
@@ -527,8 +544,7 @@ __device__ void jac_assemble(const DevMech& m, const WarpMem& w, const double (&
       dcp += y[s] * sp.dcpR[s] * kR * iW;
     }
   }
-  dq = wsum(dq);
-  dcp = wsum(dcp);
+  wsum2(dq, dcp, lane, dq, dcp);
   if (lane == 0) w.J[(size_t)K * ld + K] = -dq * irc + Qrc2 * (-rc * cs.invT + rho * dcp);
   __syncwarp();
 }
@@ -571,8 +587,8 @@ __device__ bool lu_factor(const WarpMem& w, int n, double c, int lane) {
     const unsigned int mhi = __reduce_max_sync(FULLMASK, hi);
     const unsigned int mlo = __reduce_max_sync(FULLMASK, hi == mhi ? lo : 0u);
     const unsigned int bi = __reduce_min_sync(FULLMASK, (hi == mhi && lo == mlo) ? row : 0xffffffffu);
-    const double bv = __longlong_as_double((long long)(((unsigned long long)mhi << 32) | mlo));
-    if (!(bv > 0.0) || !isfinite(bv) || bi >= (unsigned int)n) { ok = false; break; }
+    // a pivot that is zero or not finite (its |value| bits: zero, or exponent all ones)
+    if ((mhi | mlo) == 0u || mhi >= 0x7ff00000u || bi >= (unsigned int)n) { ok = false; break; }
     if ((int)bi != col) {
       for (int cc = lane; cc < n; cc += 32) {
         const double t = w.LU[(size_t)col * ld + cc];
@@ -960,7 +976,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
       bool ok = true;
 #pragma unroll
       for (int s = 0; s < NPL; ++s) {
-        if (!isfinite(f[s])) ok = false;
+        if (!finite_bits(f[s])) ok = false;
         dy[s] = c * f[s] - psi[s] - d[s];
       }
       if (__any_sync(FULLMASK, !ok)) break;
@@ -1181,9 +1197,20 @@ __global__ void log_selftest_kernel(const double* __restrict__ tab, int64_t n, c
     y[i] = log_t(x[i], tab);
 }
 
+__global__ void rcp_selftest_kernel(int64_t n, const double* x, double* y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = rcp_nr(x[i]);
+}
+
 // ------------------------------------------------------------------------------------------
 // launches
 // ------------------------------------------------------------------------------------------
+int launch_rcp_selftest(int64_t n, const double* x, double* y, cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  rcp_selftest_kernel<<<(int)blocks, 256, 0, s>>>(n, x, y);
+  return cuda_check(cudaGetLastError(), "rcp_selftest_kernel launch");
+}
+
 int launch_exp_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s) {
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
   exp_selftest_kernel<<<(int)blocks, 256, 0, s>>>(m.exptab, n, x, y);

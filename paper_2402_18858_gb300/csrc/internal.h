@@ -129,17 +129,19 @@ __device__ __forceinline__ double log_t(double x, const double* __restrict__ tab
 }
 constexpr int kMaxElem = 8;
 
-// 1/x from the hardware reciprocal estimate and two Newton-Raphson steps y += y (1 - x y), each
-// of which squares the relative error, so the result is within about an ulp of 1/x for finite
-// normal x; 4 FP64 instructions against about twice that for a correctly rounded division.
-// Zero, subnormal or infinite x give NaN (every caller treats that as a failed evaluation).
+// 1/x from the hardware reciprocal estimate and one third-order step of the Newton-Raphson
+// family for f(y) = 1/y - x (the series 1/x = y / (1 - e) = y (1 + e + e^2 + ...) with
+// e = 1 - x y, truncated after e^2; e.g. Muller et al., Handbook of Floating-Point Arithmetic,
+// ch. on iterative division): the relative error goes from eps to about eps^3.  The estimate
+// was measured within 2^-19.9 relative on 2e8 random x, so one step reaches the rounding
+// level: within 1 ulp of 1/x there.  3 FP64 instructions against 4 for two quadratic steps and
+// about twice that for a correctly rounded division.  Zero, subnormal or infinite x give NaN
+// (every caller treats that as a failed evaluation).
 __device__ __forceinline__ double rcp_nr(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 
 // FP64 -> FP32 on the integer pipe for values that only steer heuristics or feed FP32 sums
@@ -195,6 +197,7 @@ int launch_group_out_dgrad(const __nv_bfloat16* dU, int ldu, const __nv_bfloat16
                            int64_t B, int G, int h, __nv_bfloat16* dZ, cudaStream_t s);
 size_t di_smem_per_warp(const DevMech& m);
 
+int launch_rcp_selftest(int64_t n, const double* x, double* y, cudaStream_t s);
 int launch_exp_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s);
 int launch_log_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s);
 

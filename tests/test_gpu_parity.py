@@ -279,6 +279,28 @@ def test_table_exp_against_cuda_exp(lc, gmech):
     assert np.isnan(v[0]) and v[1] == np.inf and v[2] == 0.0 and v[3] == 0.0 and v[4] == np.inf
 
 
+def test_reciprocal_against_division(lc):
+    """The kernels' FP64 reciprocal (hardware estimate, one third-order step) stays within 1 ulp
+    of the correctly rounded 1/x over the normal range, and gives NaN for 0 and inf."""
+    rng = np.random.default_rng(6)
+    x = np.concatenate([np.exp(rng.uniform(-700, 700, 300000)), rng.uniform(0.5, 2.0, 200000),
+                        -np.exp(rng.uniform(-50, 50, 100000)), rng.uniform(200.0, 4000.0, 100000),
+                        [1.0, 2.0, 3.0, 0.1, 1.0 - 2.0 ** -53, 1.0 + 2.0 ** -52]])
+    xd = _dev(x)
+    y = torch.empty_like(xd)
+    lc.chem_selftest_rcp(xd, y)
+    torch.cuda.synchronize()
+    yy, rr = y.cpu().numpy(), 1.0 / x
+    ulp = np.abs(yy - rr) / np.spacing(np.abs(rr))
+    assert ulp.max() <= 1.0, (ulp.max(), x[np.argmax(ulp)])
+    assert yy[x == 1.0][0] == 1.0 and yy[x == 2.0][0] == 0.5
+    spec = _dev(np.array([0.0, np.inf, -np.inf]))
+    ys = torch.empty_like(spec)
+    lc.chem_selftest_rcp(spec, ys)
+    torch.cuda.synchronize()
+    assert np.isnan(ys.cpu().numpy()).all()
+
+
 def test_table_log_against_cuda_log(lc, gmech):
     """The kernels' table-driven FP64 log stays within 3 ulp of CUDA's log, including near 1
     (its own error is about 2 ulp at most, CUDA's under 1)."""
