@@ -324,6 +324,32 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
       for (int e = 0; e < E; ++e) acc += (double)hm.comp[(size_t)k * E + e] * Linv[(size_t)e * R + r];
       Pm[(size_t)k * R + r] = acc;
     }
+  // -g'_k/RT per species and range as one polynomial in (1, ln T, T, T^2, T^3, T^4, 1/T):
+  // g/RT = h/RT - s/R = (a1 - a7) - a1 ln T - a2 T/2 - a3 T^2/6 - a4 T^3/12 - a5 T^4/20 + a6/T
+  // of the NASA-7 fit (coefficients a1..a7), shifted by the element potentials,
+  // g' = g - sum_r P[k][r] g_ref_r (formed in long double, rounded once)
+  std::vector<double> gneg((size_t)K * 2 * 8, 0.0);
+  for (int rg = 0; rg < 2; ++rg) {
+    auto gcoef = [&](int k, long double* c) {
+      const double* a = &hm.nasa[(size_t)k * 14 + 7 * rg];
+      c[0] = (long double)a[0] - (long double)a[6];
+      c[1] = -(long double)a[0];
+      c[2] = -(long double)a[1] / 2;
+      c[3] = -(long double)a[2] / 6;
+      c[4] = -(long double)a[3] / 12;
+      c[5] = -(long double)a[4] / 20;
+      c[6] = (long double)a[5];
+    };
+    for (int k = 0; k < K; ++k) {
+      long double c[7], cr[7];
+      gcoef(k, c);
+      for (int r = 0; r < R; ++r) {
+        gcoef(refs[r], cr);
+        for (int i = 0; i < 7; ++i) c[i] -= (long double)Pm[(size_t)k * R + r] * cr[i];
+      }
+      for (int i = 0; i < 7; ++i) gneg[((size_t)k * 2 + rg) * 8 + i] = (double)(-c[i]);
+    }
+  }
   std::vector<double> exptab(256);
   for (int j = 0; j < 256; ++j) exptab[j] = (double)std::exp2((long double)j / 256.0L);
   std::vector<double> logtab(3 * 97);
@@ -354,8 +380,6 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
     if (tp[7] != 0.0) x[18] = tp[6];                                  // exp(-T** / T)
     else x[16] = -1e300;                                              // absent term: 0
   }
-  std::vector<int> refs_pad(refs);
-  if (refs_pad.empty()) refs_pad.push_back(0);
 
   std::vector<int> sp_ptr(K + 1, 0), sp_rxn;
   std::vector<double> sp_nu;
@@ -436,7 +460,7 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   size_t oexs = add(ex_sp.data(), ex_sp.size() * 4), oexa = add(ex_a.data(), ex_a.size() * 8);
   size_t otroe = add(troe.data(), troe.size() * 8), optr = add(sp_ptr.data(), sp_ptr.size() * 4);
   size_t orxn = add(sp_rxn.data(), sp_rxn.size() * 4), onu = add(sp_nu.data(), sp_nu.size() * 8);
-  size_t oref = add(refs_pad.data(), refs_pad.size() * 4), oP = add(Pm.data(), Pm.size() * 8);
+  size_t ogn = add(gneg.data(), gneg.size() * 8);
   size_t oexp = add(exptab.data(), exptab.size() * 8), ocw = add(compW.data(), compW.size() * 8);
   size_t oxa = add(xarg.data(), xarg.size() * 8), olog = add(logtab.data(), logtab.size() * 8);
   size_t obal = add(bal.data(), bal.size() * 4), orun = add(run_ptr.data(), run_ptr.size() * 4);
@@ -462,7 +486,7 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   m.ex_sp = (const int*)(b + oexs); m.ex_a = (const double*)(b + oexa);
   m.troe = (const double*)(b + otroe); m.sp_ptr = (const int*)(b + optr);
   m.sp_rxn = (const int*)(b + orxn); m.sp_nu = (const double*)(b + onu);
-  m.n_ref = R; m.ref_sp = (const int*)(b + oref); m.P = (const double*)(b + oP);
+  m.gneg = (const double*)(b + ogn);
   m.exptab = (const double*)(b + oexp);
   m.logtab = (const double*)(b + olog);
   m.compW = (const double*)(b + ocw);

@@ -72,7 +72,7 @@ struct WarpMem {
   double* LU;     // n x ld (factors of I - c J)
   double* C;      // K concentrations
   double* hRT;    // K
-  double* g;      // K   g/RT = h/RT - s/R
+  double* g;      // K   run slots of the production rates (with eg and ieg, which follow it)
   double* eg;     // K   exp(-(g/RT - shift)) p0/RT, shift = element-potential term
   double* ieg;    // K   exp(+(g/RT - shift)) RT/p0
   double* q;      // I   net rates of progress
@@ -153,67 +153,95 @@ struct CellSc {
   double T, lnT, invT, RT, rho, Wbar, cp, Q;
 };
 
+// per-cell constants of the right-hand side: p / R and R / p (constant pressure)
+struct CellP {
+  double pR, Rp;
+};
+__device__ __forceinline__ CellP cell_p(double p) {
+  CellP c;
+  c.pR = p * (1.0 / kR);
+  c.Rp = kR / p;
+  return c;
+}
+
 // ------------------------------------------------------------------------------------------
 // Troe falloff (Lindemann form with the Troe broadening factor, Gilbert, Luther & Troe 1983)
 // for all falloff reactions of a cell.  The exponential rounds of rhs_eval have already put
-// [0] k_inf, [1] k_0/k_inf, [2] exp(-T/T***), [3] exp(-T/T*), [4] exp(-T**/T) into w.tr; here
-// P_r = (k_0/k_inf)[M] and F_cent (no division), their base-10 logarithms (one lane each), and
-// F and k with two divisions per reaction.  Results: [10] k, [11] dk/d[M], [12] d ln k/dT at
-// fixed [M].
+// [0] k_inf, [1] k_0/k_inf, [2] exp(-T/T***), [3] exp(-T/T*), [4] exp(-T**/T) into w.tr.
+// Reaction jt is worked by the lane pair t = 2 jt + q in rounds of 32 lanes, both lanes running
+// one instruction stream on selected operands: lane q = 0 forms F_cent, lane q = 1 forms
+// P_r = (k_0/k_inf)[M]; each takes the logarithm of its own value; after an exchange both
+// have ln F_cent and ln P_r, form c, n and x = log10 P_r + c, and take one reciprocal: lane 0
+// of 1/(den^2 + x^2) (den = n - 0.14 x), lane 1 of 1/(1 + P_r).  Lane 0 then forms
+// F = exp(ln F_cent den^2 / (den^2 + x^2)) (the base-10 form of log10 F = log10 F_cent /
+// (1 + (x/den)^2) with both sides times ln 10) and k = k_inf P_r/(1 + P_r) F.
+// Results: [10] k, [11] dk/d[M], [12] d ln k/dT at fixed [M].
 // ------------------------------------------------------------------------------------------
 template <bool JAC>
 __device__ __forceinline__ void troe_phase(const DevMech& m, const WarpMem& w, double invT, double ctot, int lane) {
   const int nT = m.I - m.n_tb_end;
   const double* __restrict__ et = m.exptab;
-  for (int jt = lane; jt < nT; jt += 32) {
+  const double kS = 0.4342944819032518;   // 1 / ln 10
+  for (int t0 = 0; t0 < 2 * nT; t0 += 32) {
+    const int t = t0 + lane, jt = t >> 1, q = t & 1;
+    const bool act = t < 2 * nT;
     const int j = m.n_tb_end + jt;
-    const double* tp = m.troe + 8 * (size_t)j;
-    double* r = w.tr + kTroeSlots * jt;
-    double M = ctot;
+    double* r = w.tr + kTroeSlots * (act ? jt : 0);
+    // q = 0: F_cent = (1 - a) e_*** + a e_* + e_**;  q = 1: (k_0/k_inf) ([M] = ctot + sum_e
+    // (alpha_e - 1) C_e), both as scale * (base + sum of four products)
+    double c4[4] = {0.0, 0.0, 0.0, 0.0}, u4[4] = {0.0, 0.0, 0.0, 0.0}, base = 1.0, scale = 1.0;
+    if (act) {
+      if (q == 0) {
+        const double a = __ldg(m.troe + 8 * (size_t)j + 3);
+        c4[0] = 1.0 - a; u4[0] = r[2];
+        c4[1] = a;       u4[1] = r[3];
+        base = r[4];
+      } else {
 #pragma unroll
-    for (int e = 0; e < kMaxEx; ++e) {
-      const int se = __ldg(m.ex_sp + (size_t)j * kMaxEx + e);
-      if (se >= 0) M += __ldg(m.ex_a + (size_t)j * kMaxEx + e) * w.C[se];
+        for (int e = 0; e < kMaxEx; ++e) {
+          const int se = __ldg(m.ex_sp + (size_t)j * kMaxEx + e);
+          if (se >= 0) { c4[e] = __ldg(m.ex_a + (size_t)j * kMaxEx + e); u4[e] = w.C[se]; }
+        }
+        base = ctot;
+        scale = r[1];
+      }
     }
-    const double a = __ldg(tp + 3);
-    r[5] = (1.0 - a) * r[2] + a * r[3] + r[4];
-    r[6] = fmax(r[1] * M, 1e-300);
-  }
-  __syncwarp();
-  for (int t = lane; t < 2 * nT; t += 32) {
-    const int jt = t >> 1, q = t & 1;
-    w.tr[kTroeSlots * jt + 8 + q] = log_t(w.tr[kTroeSlots * jt + 5 + q], m.logtab) * 0.4342944819032518;   // log10
-  }
-  __syncwarp();
-  for (int jt = lane; jt < nT; jt += 32) {
-    const int j = m.n_tb_end + jt;
-    double* r = w.tr + kTroeSlots * jt;
-    const double kinf = r[0], Fc = r[5], Pr = r[6], L = r[8];
-    const double c = -0.4 - 0.67 * L;
-    const double nn = 0.75 - 1.27 * L;
-    const double x = r[9] + c;
-    const double den = nn - 0.14 * x;
+    const double v = fmax(scale * fma(c4[3], u4[3], fma(c4[2], u4[2], fma(c4[1], u4[1], fma(c4[0], u4[0], base)))), 1e-300);
+    const double lv = log_t(v, m.logtab);
+    const int l0 = lane & ~1, l1 = lane | 1;
+    const double lc = __shfl_sync(FULLMASK, lv, l0);   // ln F_cent
+    const double lp = __shfl_sync(FULLMASK, lv, l1);   // ln P_r
+    const double Pr = __shfl_sync(FULLMASK, v, l1);
+    const double c = fma(-0.67 * kS, lc, -0.4);
+    const double nn = fma(-1.27 * kS, lc, 0.75);
+    const double x = fma(kS, lp, c);
+    const double den = fma(-0.14, x, nn);
     const double d2 = den * den;
-    // log10 F = log10 F_cent / (1 + (x / den)^2) = log10 F_cent den^2 / (den^2 + x^2)
-    const double F = exp_t(2.302585092994046 * (L * d2 * rcp_nr(d2 + x * x)), et);
-    const double ipr = rcp_nr(1.0 + Pr);
-    r[10] = kinf * Pr * ipr * F;
-    if (JAC) {
-      const double* tp = m.troe + 8 * (size_t)j;
-      const double* ar = m.arr + 4 * (size_t)j;
-      const double k0 = kinf * r[1];
-      const double f1 = x / den;
-      const double opf = 1.0 + f1 * f1;
-      const double aa = __ldg(tp + 3), iT3 = __ldg(tp + 4), iT1 = __ldg(tp + 5);
-      const double dFc = -(1.0 - aa) * iT3 * r[2] - aa * iT1 * r[3] + __ldg(tp + 6) * invT * invT * r[4];
-      const double df1dx = nn / d2;
-      const double gg = -L * 2.0 * f1 / (opf * opf) * df1dx;          // d log F / d log Pr
-      r[11] = k0 * F * (ipr * ipr + gg * ipr);
-      const double df1dL = df1dx * (-0.67) + (-x / d2) * (-1.27);
-      const double dlogFdL = 1.0 / opf - L * 2.0 * f1 / (opf * opf) * df1dL;
-      const double dlnkinf = __ldg(ar + 1) * invT + __ldg(ar + 2) * invT * invT;
-      const double dlnk0 = __ldg(tp + 1) * invT + __ldg(tp + 2) * invT * invT;
-      r[12] = dlnkinf + (ipr + gg) * (dlnk0 - dlnkinf) + dlogFdL * dFc / Fc;
+    const double iS = rcp_nr(q ? 1.0 + Pr : fma(x, x, d2));
+    const double ipr = __shfl_sync(FULLMASK, iS, l1);
+    if (act && q == 0) {
+      const double F = exp_t(lc * d2 * iS, et);
+      const double kinf = r[0];
+      r[10] = kinf * Pr * ipr * F;
+      if (JAC) {
+        const double L = kS * lc;   // log10 F_cent
+        const double Fc = v;
+        const double* tp = m.troe + 8 * (size_t)j;
+        const double* ar = m.arr + 4 * (size_t)j;
+        const double k0 = kinf * r[1];
+        const double f1 = x / den;
+        const double opf = 1.0 + f1 * f1;
+        const double aa = __ldg(tp + 3), iT3 = __ldg(tp + 4), iT1 = __ldg(tp + 5);
+        const double dFc = -(1.0 - aa) * iT3 * r[2] - aa * iT1 * r[3] + __ldg(tp + 6) * invT * invT * r[4];
+        const double df1dx = nn / d2;
+        const double gg = -L * 2.0 * f1 / (opf * opf) * df1dx;          // d log F / d log Pr
+        r[11] = k0 * F * (ipr * ipr + gg * ipr);
+        const double df1dL = df1dx * (-0.67) + (-x / d2) * (-1.27);
+        const double dlogFdL = 1.0 / opf - L * 2.0 * f1 / (opf * opf) * df1dL;
+        const double dlnkinf = __ldg(ar + 1) * invT + __ldg(ar + 2) * invT * invT;
+        const double dlnk0 = __ldg(tp + 1) * invT + __ldg(tp + 2) * invT * invT;
+        r[12] = dlnkinf + (ipr + gg) * (dlnk0 - dlnkinf) + dlogFdL * dFc / Fc;
+      }
     }
   }
   __syncwarp();
@@ -223,7 +251,7 @@ __device__ __forceinline__ void troe_phase(const DevMech& m, const WarpMem& w, d
 // right-hand side f(z) of the reactor, z = (Y_1..Y_K, T)  [Eq. 1]
 // ------------------------------------------------------------------------------------------
 template <int NPL, bool JAC>
-__device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip, const double (&y)[NPL],
+__device__ void rhs_eval(const DevMech& m, const WarpMem& w, const CellP& cp0, const double (&y)[NPL],
                          double (&f)[NPL], LaneSp<NPL>& sp, CellSc& cs, int lane) {
   const int K = m.K, I = m.I;
   const double T = comp_get<NPL>(y, K);
@@ -251,23 +279,27 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
     }
   }
   wsum2(sYW, cpp, lane, sYW, cpp);
-  // one division gives 1/T, the mean molar mass and 1/c_p
+  // one reciprocal gives 1/T, 1/(T sum Y/W) and 1/c_p (with p/R and R/p per cell: no division)
   const double TsY = T * sYW;
   const double inv = rcp_nr(TsY * cpp);
   const double invT = inv * (sYW * cpp);
   const double Wbar = JAC ? inv * (T * cpp) : 0.0;   // the mean molar mass and c_p: Jacobian only
   const double icp = inv * TsY * (1.0 / kR);
-  const double rho = p * (inv * cpp) * (1.0 / kR);   // p Wbar / (R T)
-  const double irho = sYW * RT * ip;                 // 1 / rho
-  const double ctot = rho * sYW;                     // sum of the concentrations
+  const double rho = cp0.pR * (inv * cpp);           // p Wbar / (R T) = (p/R) / (T sum Y/W)
+  const double irho = cp0.Rp * TsY;                  // 1 / rho
+  const double ctot = cp0.pR * invT;                 // sum of the concentrations, p / (R T)
   const double cp = JAC ? cpp * kR : 0.0;
-  // pass 2: h/RT, g/RT and the concentrations (and the sentinel slots of the two-partner
-  // reactions, which the production-rate runs of the previous call may have overwritten)
-  double Cs[NPL];
+  // pass 2: h/RT and the concentrations (and the sentinel slots of the two-partner reactions,
+  // which the production-rate runs of the previous call may have overwritten), and per species
+  // e = exp(-g'/RT) with g' the free energy shifted by element potentials (one exp per species
+  // instead of one per reaction; the shift cancels in every balanced reaction).
+  // kr / kf = 1/K_c = prod_r e_r prod_p (1/e_p) (RT/p0)^(sum nu): the pressure factor goes
+  // into the per-species values, p0/RT with every reactant and RT/p0 with every product
+  const double P0RT = (kP0 / kR) * invT, RTP0 = RT * (1.0 / kP0);
+  const bool two = !JAC && m.arity2;   // warp-uniform
 #pragma unroll
   for (int s = 0; s < NPL; ++s) {
     const int k = lane + 32 * s;
-    Cs[s] = 0.0;
     if (k == K) {
       w.C[K] = 1.0;
       w.eg[K] = 1.0;
@@ -277,33 +309,18 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, double p, double ip
       const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
       const double hRT = __ldg(a + 5) + T * (__ldg(a + 6) + T * (__ldg(a + 7) + T * (__ldg(a + 8) + T * __ldg(a + 9))))
                          + __ldg(a + 10) * invT;
-      const double sR = __ldg(a + 11) * lnT + T * (__ldg(a + 12) + T * (__ldg(a + 13) + T * (__ldg(a + 14) + T * __ldg(a + 15))))
-                        + __ldg(a + 16);
+      const double* gc = m.gneg + ((size_t)k * 2 + hi) * 8;
+      const double2 g01 = __ldg((const double2*)gc), g23 = __ldg((const double2*)(gc + 2));
+      const double2 g45 = __ldg((const double2*)(gc + 4));
+      const double g6 = __ldg(gc + 6);
+      const double ng = fma(T, T * fma(T, fma(T, g45.y, g45.x), g23.y) + g23.x, fma(g6, invT, fma(g01.y, lnT, g01.x)));
       const double Ck = rho * ywr[s];
       w.C[k] = Ck;
-      Cs[s] = Ck;
       w.hRT[k] = hRT;
-      w.g[k] = hRT - sR;
       sp.hRT[s] = hRT;
-    }
-  }
-  __syncwarp();
-  // exp(-g'/RT) per species, g' = g - sum_r P_kr g_ref_r (one exp per species instead of
-  // one per reaction; the element-potential shift cancels in every balanced reaction)
-  // kr / kf = 1/K_c = prod_r e_r prod_p (1/e_p) (RT/p0)^(sum nu): the pressure factor goes
-  // into the per-species values, p0/RT with every reactant and RT/p0 with every product
-  const double P0RT = (kP0 / kR) * invT, RTP0 = RT * (1.0 / kP0);
-  const int R = m.n_ref;
-  const bool two = !JAC && m.arity2;   // warp-uniform
-#pragma unroll
-  for (int s = 0; s < NPL; ++s) {
-    const int k = lane + 32 * s;
-    if (k < K) {
-      double gs = w.g[k];
-      for (int r = 0; r < R; ++r) gs -= __ldg(m.P + (size_t)k * R + r) * w.g[__ldg(m.ref_sp + r)];
-      const double e = exp_t(-gs, et);
+      const double e = exp_t(ng, et);
       w.eg[k] = e * P0RT;
-      w.ieg[k] = rcp_nr(e) * (two ? RTP0 * Cs[s] : RTP0);
+      w.ieg[k] = rcp_nr(e) * (two ? RTP0 * Ck : RTP0);
     }
   }
   // exponential rounds: k_f of every non-falloff reaction (into w.q, read back by the same
@@ -869,12 +886,12 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
   const double EPS = 2.220446049250313e-16;
   const float ntol = (float)o.newton_tol;
   const RescaleLane rc = rescale_lane(lane);
-  const double ip = 1.0 / pc;
+  const CellP pp = cell_p(pc);
 
   double D[kMaxOrd + 3][NPL];
   double f[NPL], y[NPL], d[NPL], dy[NPL], psi[NPL];
   // initial step (Hairer, Norsett & Wanner, Sec. II.4, order 1)
-  rhs_eval<NPL, false>(m, w, pc, ip, z, f, sp, cs, lane);
+  rhs_eval<NPL, false>(m, w, pp, z, f, sp, cs, lane);
   cnt[1]++;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) isc[s] = __frcp_rn(fmaf(rtolf, fabsf(narrow_f32(z[s])), atolf[s]));
@@ -883,7 +900,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
   h0 = fmin(h0, dt);
 #pragma unroll
   for (int s = 0; s < NPL; ++s) y[s] = z[s] + h0 * f[s];
-  rhs_eval<NPL, false>(m, w, pc, ip, y, dy, sp, cs, lane);
+  rhs_eval<NPL, false>(m, w, pp, y, dy, sp, cs, lane);
   cnt[1]++;
 #pragma unroll
   for (int s = 0; s < NPL; ++s) dy[s] -= f[s];
@@ -937,7 +954,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     const double c = h * ig;
     bool f_at_pred = false;
     if (need_jac) {
-      rhs_eval<NPL, true>(m, w, pc, ip, y, f, sp, cs, lane);
+      rhs_eval<NPL, true>(m, w, pp, y, f, sp, cs, lane);
       jac_assemble<NPL>(m, w, y, sp, cs, lane);
       cnt[1]++;
       cnt[2]++;
@@ -970,7 +987,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     newton_iters = 0;
     for (int it = 0; it < kNewtonMax; ++it) {
       if (!(it == 0 && f_at_pred)) {
-        rhs_eval<NPL, false>(m, w, pc, ip, y, f, sp, cs, lane);
+        rhs_eval<NPL, false>(m, w, pp, y, f, sp, cs, lane);
         cnt[1]++;
       }
       bool ok = true;
@@ -1154,7 +1171,7 @@ __global__ void __launch_bounds__(128) rates_kernel(DevMech m, int64_t n, int64_
     CellSc cs;
     load_cell<NPL>(m, col, ld, T, Y, z, lane);
     const double pc = p[col];
-    rhs_eval<NPL, false>(m, w, pc, 1.0 / pc, z, f, sp, cs, lane);
+    rhs_eval<NPL, false>(m, w, cell_p(pc), z, f, sp, cs, lane);
 #pragma unroll
     for (int s = 0; s < NPL; ++s) {
       const int k = lane + 32 * s;
@@ -1179,7 +1196,7 @@ __global__ void __launch_bounds__(128) jacobian_kernel(DevMech m, int64_t n, int
     CellSc cs;
     load_cell<NPL>(m, col, ld, T, Y, z, lane);
     const double pc = p[col];
-    rhs_eval<NPL, true>(m, w, pc, 1.0 / pc, z, f, sp, cs, lane);
+    rhs_eval<NPL, true>(m, w, cell_p(pc), z, f, sp, cs, lane);
     jac_assemble<NPL>(m, w, z, sp, cs, lane);
     double* out = jac + (size_t)col * nn * nn;
     for (int e = lane; e < nn * nn; e += 32) out[e] = w.J[(size_t)(e / nn) * w.ld + (e % nn)];

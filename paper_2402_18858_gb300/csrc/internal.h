@@ -38,12 +38,12 @@ struct DevMech {
   const int* sp_ptr;       // [K+1]
   const int* sp_rxn;       // [nnz]
   const double* sp_nu;     // [nnz]
-  // Element-potential shift of g/RT for the equilibrium constants: species k uses
-  // g_k - sum_r P[k][r] g_{ref_r}, with P = composition x pinv(reference compositions).
-  // Balanced reactions cancel the shift exactly; it keeps exp(-g) products in range.
-  int n_ref;               // number of reference species (rank of the composition matrix)
-  const int* ref_sp;       // [n_ref]
-  const double* P;         // [K][n_ref]
+  // -g'_k/RT for the equilibrium constants, g' = g_k - sum_r P[k][r] g_{ref_r} the free
+  // energy shifted by element potentials (P = composition x pinv(reference compositions));
+  // balanced reactions cancel the shift exactly, and it keeps exp(-g') products in range.
+  // Per species and range one polynomial: [0] + [1] ln T + T ([2] + T ([3] + T ([4] + T [5])))
+  // + [6] / T ([7] unused).
+  const double* gneg;      // [K][2][8]
   const double* exptab;    // [256] 2^(j/256), the table of the FP64 exponential below
   const double* logtab;    // [97][3] F = j/128, 1/F, log F (j = 96..192): the table of log_t below
   const double* compW;     // [K][E] element counts divided by the molar mass (mol/kg)
@@ -66,21 +66,45 @@ struct DevMech {
   const int4* rsp2;          // [I]
 };
 
+// FP64 -> FP32 on the integer pipe for values that only steer heuristics or feed FP32 sums
+// (exponent rebias, mantissa truncated: relative error below 2^-23).  |x| < 2^-126 gives a
+// signed zero, |x| >= 2^128, inf and NaN give a signed inf.
+__device__ __forceinline__ float narrow_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
+  const unsigned int e = (hi >> 20) & 0x7ffu, sgn = hi & 0x80000000u;
+  const unsigned int f = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(e > 896u ? (e < 1151u ? (sgn | f) : (sgn | 0x7f800000u)) : sgn);
+}
+
+// FP32 -> FP64 on the integer pipe, exact for zero and normal numbers (sign kept, exponent
+// rebiased by 1023 - 127, mantissa widened); used for small integers held in FP32.
+__device__ __forceinline__ double widen_f64(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int mag = b & 0x7fffffffu, sgn = b & 0x80000000u;
+  const unsigned int hi = mag ? (sgn | ((mag >> 3) + 0x38000000u)) : sgn;
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 // FP64 exponential by the table-driven method (P. T. P. Tang, "Table-driven implementation of
 // the exponential function in IEEE floating-point arithmetic", ACM TOMS 15, 1989), here with a
-// 256-entry table: x = (256 k + j) ln2/256 + r with |r| <= ln2/512, exp(x) = 2^k 2^(j/256) e^r,
-// e^r - 1 from its degree-4 Taylor polynomial (truncation |r|^5/120 < 4e-17 relative, a third
-// of an ulp).  9 FP64 instructions against ~22 FP64-pipe slots for the library exp on GB300;
-// within 2 ulp of a correctly rounded exp (tested).
+// 256-entry table: x = (256 k + j) ln2/256 + r, exp(x) = 2^k 2^(j/256) e^r, e^r - 1 from its
+// degree-4 Taylor polynomial.  The split n = 256 k + j only has to keep r small, so it is
+// taken from the FP32 value of x (integer-pipe narrowing, one FP32 FMA against 1.5 * 2^23,
+// which rounds to an integer): for |x| < 709.8, |x 256/ln2 - n| <= 0.5 + 0.05, so |r| <=
+// 1.49e-3 and the truncation |r|^5/120 < 6e-17 relative stays below an ulp.  n goes back to
+// FP64 exactly through FP32 (|n| < 2^18) on the integer pipe, and n ln2/256 is split so that
+// n times its high part is exact.  7 FP64 instructions (against ~22 FP64-pipe slots for the
+// library exp on GB300); within 2 ulp of a correctly rounded exp (tested).
 // Arguments below -708 return 0, above 709.78 return +inf, NaN propagates.
 __device__ __forceinline__ double exp_t(double x, const double* __restrict__ tab) {
-  const double kInvL = 369.3299304675746;            // 256 / ln 2
+  const float kInvLf = 369.329930467574f;            // 256 / ln 2
+  const float kMagicf = 12582912.0f;                 // 1.5 * 2^23: rounds to an integer
   const double kL1 = 0x1.62e42ff000000p-9;           // ln 2 / 256, high part (29 bits: nd kL1 exact)
   const double kL2 = -1.6409824502660487e-13;        // ln 2 / 256 - kL1
-  const double kMagic = 6755399441055744.0;          // 1.5 * 2^52: rounds to an integer
-  const double t = fma(x, kInvL, kMagic);
-  const double nd = t - kMagic;
-  const int nn = (int)(unsigned int)(unsigned long long)__double_as_longlong(t);
+  const float tf = fmaf(narrow_f32(x), kInvLf, kMagicf);
+  const int nn = (int)(__float_as_uint(tf) - 0x4B400000u);   // tf = 1.5 * 2^23 + n
+  const double nd = widen_f64(tf - kMagicf);                 // n, exactly
   const double r = fma(-nd, kL2, fma(-nd, kL1, x));
   double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   q = fma(q, r, 0.5);
@@ -120,10 +144,10 @@ __device__ __forceinline__ double log_t(double x, const double* __restrict__ tab
   pl = fma(pl, u, -0.25);
   pl = fma(pl, u, 1.0 / 3.0);
   pl = fma(pl, u, -0.5);
-  // k as a double without a conversion instruction: 1.5 * 2^52 + k (any sign) has k in its
-  // low bits and the same exponent
+  // k as a double without an FP64 instruction: 1.5 * 2^23 + k (any sign) has k in its low
+  // bits, one FP32 subtraction leaves k exactly, and the integer pipe widens it
   const int k = (int)(hw >> 20) - 1023 + up;
-  const double kd = __longlong_as_double(0x4338000000000000LL + (long long)k) - 6755399441055744.0;
+  const double kd = widen_f64(__uint_as_float(0x4B400000u + (unsigned int)k) - 12582912.0f);
   const double kLn2Hi = 0x1.62e42fee00000p-1, kLn2Lo = 1.9082149292705877e-10;
   return fma(kd, kLn2Hi, __ldg(t + 2)) + fma(kd, kLn2Lo, fma(pl, u * u, u));
 }
@@ -142,17 +166,6 @@ __device__ __forceinline__ double rcp_nr(double x) {
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
   const double e = fma(-x, y, 1.0);
   return fma(y, fma(e, e, e), y);
-}
-
-// FP64 -> FP32 on the integer pipe for values that only steer heuristics or feed FP32 sums
-// (exponent rebias, mantissa truncated: relative error below 2^-23).  |x| < 2^-126 gives a
-// signed zero, |x| >= 2^128, inf and NaN give a signed inf.
-__device__ __forceinline__ float narrow_f32(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
-  const unsigned int e = (hi >> 20) & 0x7ffu, sgn = hi & 0x80000000u;
-  const unsigned int f = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  return __uint_as_float(e > 896u ? (e < 1151u ? (sgn | f) : (sgn | 0x7f800000u)) : sgn);
 }
 
 struct HostMech;   // parsed mechanism (host)
