@@ -427,6 +427,12 @@ int chem_pasr_source(chem_mech mech, int64_t n, int64_t ld, double dt, const dou
  * method the kernels use), for comparison with CUDA's exp.  Device pointers, n >= 0. */
 int chem_selftest_exp(chem_mech mech, int64_t n, const double* x, double* y, chem_stream stream);
 
+/* Testing hook: y[i] = 2^(x[i]/256) = exp(x[i] ln2/256) by the library's FP64 exponential of
+ * pre-scaled arguments (the form the chemistry kernels use for rate constants and equilibrium
+ * constants, whose exponents are linear in coefficients stored times 256/ln 2), for comparison
+ * with an exact-argument exp2.  Device pointers, n >= 0. */
+int chem_selftest_exp256(chem_mech mech, int64_t n, const double* x, double* y, chem_stream stream);
+
 /* Testing hook: y[i] = log(x[i]) by the library's own FP64 logarithm (the table-driven method
  * the kernels use for ln T and the falloff logarithms), for comparison with CUDA's log.  Device
  * pointers, n >= 0. */

@@ -70,6 +70,7 @@ def lib(auto_build: bool = False):
         L.chem_fp64_peak_gflops.argtypes = [C.POINTER(dbl), vp]
         L.chem_selftest_exp.argtypes = [vp, i64, vp, vp, vp]
         L.chem_selftest_log.argtypes = [vp, i64, vp, vp, vp]
+        L.chem_selftest_exp256.argtypes = [vp, i64, vp, vp, vp]
         L.chem_selftest_rcp.argtypes = [i64, vp, vp, vp]
         L.chem_selftest_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.chem_selftest_gemm_grouped.argtypes = [i32, i32, i32, i32, i32, vp, i64, i32, i32, vp, i64, i32, i32,
@@ -238,6 +239,11 @@ def chem_fp64_peak_gflops(stream=None) -> float:
 def chem_selftest_exp(m: Mech, x, y, stream=None) -> None:
     _check(lib().chem_selftest_exp(m.handle, x.numel(), _ptr(x, torch.float64),
                                    _ptr(y, torch.float64), _stream(stream)))
+
+
+def chem_selftest_exp256(m: Mech, x, y, stream=None) -> None:
+    _check(lib().chem_selftest_exp256(m.handle, x.numel(), _ptr(x, torch.float64),
+                                      _ptr(y, torch.float64), _stream(stream)))
 
 
 def chem_selftest_log(m: Mech, x, y, stream=None) -> None:

@@ -324,6 +324,8 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
       for (int e = 0; e < E; ++e) acc += (double)hm.comp[(size_t)k * E + e] * Linv[(size_t)e * R + r];
       Pm[(size_t)k * R + r] = acc;
     }
+  // exponent arguments of the kernels' exponential are kept in units of ln2/256
+  const long double kExpScale = 256.0L / 0.693147180559945309417232121458176568L;
   // -g'_k/RT per species and range as one polynomial in (1, ln T, T, T^2, T^3, T^4, 1/T):
   // g/RT = h/RT - s/R = (a1 - a7) - a1 ln T - a2 T/2 - a3 T^2/6 - a4 T^3/12 - a5 T^4/20 + a6/T
   // of the NASA-7 fit (coefficients a1..a7), shifted by the element potentials,
@@ -347,7 +349,7 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
         gcoef(refs[r], cr);
         for (int i = 0; i < 7; ++i) c[i] -= (long double)Pm[(size_t)k * R + r] * cr[i];
       }
-      for (int i = 0; i < 7; ++i) gneg[((size_t)k * 2 + rg) * 8 + i] = (double)(-c[i]);
+      for (int i = 0; i < 7; ++i) gneg[((size_t)k * 2 + rg) * 8 + i] = (double)(-c[i] * kExpScale);
     }
   }
   std::vector<double> exptab(256);
@@ -380,6 +382,7 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
     if (tp[7] != 0.0) x[18] = tp[6];                                  // exp(-T** / T)
     else x[16] = -1e300;                                              // absent term: 0
   }
+  for (auto& v : xarg) v = (double)((long double)v * kExpScale);
 
   std::vector<int> sp_ptr(K + 1, 0), sp_rxn;
   std::vector<double> sp_nu;
@@ -673,6 +676,14 @@ int chem_selftest_exp(chem_mech m, int64_t n, const double* x, double* y, chem_s
   if (n < 0 || (n > 0 && (!x || !y))) return set_error(CHEM_E_ARG, "chem_selftest_exp: bad arguments");
   if (n == 0) return CHEM_OK;
   return launch_exp_selftest(m->dev, n, x, y, (cudaStream_t)stream);
+}
+
+int chem_selftest_exp256(chem_mech m, int64_t n, const double* x, double* y, chem_stream stream) {
+  int rc = check_mech(m);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!x || !y))) return set_error(CHEM_E_ARG, "chem_selftest_exp256: bad arguments");
+  if (n == 0) return CHEM_OK;
+  return launch_exp256_selftest(m->dev, n, x, y, (cudaStream_t)stream);
 }
 
 int chem_selftest_log(chem_mech m, int64_t n, const double* x, double* y, chem_stream stream) {

@@ -318,7 +318,7 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, const CellP& cp0, c
       w.C[k] = Ck;
       w.hRT[k] = hRT;
       sp.hRT[s] = hRT;
-      const double e = exp_t(ng, et);
+      const double e = exp_s256(ng, et);
       w.eg[k] = e * P0RT;
       w.ieg[k] = rcp_nr(e) * (two ? RTP0 * Ck : RTP0);
     }
@@ -332,12 +332,12 @@ __device__ void rhs_eval(const DevMech& m, const WarpMem& w, const CellP& cp0, c
   for (int t = lane; t < n_plain; t += 32) {
     const double2 x01 = __ldg((const double2*)(m.xarg + 4 * (size_t)t));
     const double x2 = __ldg(m.xarg + 4 * (size_t)t + 2);
-    w.q[t] = exp_t(fma(-x2, invT, fma(x01.y, lnT, x01.x)), et);
+    w.q[t] = exp_s256(fma(-x2, invT, fma(x01.y, lnT, x01.x)), et);
   }
   for (int t = n_plain + lane; t < m.n_x; t += 32) {
     const double2 x01 = __ldg((const double2*)(m.xarg + 4 * (size_t)t));
     const double2 x23 = __ldg((const double2*)(m.xarg + 4 * (size_t)t + 2));
-    const double e = exp_t(fma(x23.y, T, fma(-x23.x, invT, fma(x01.y, lnT, x01.x))), et);
+    const double e = exp_s256(fma(x23.y, T, fma(-x23.x, invT, fma(x01.y, lnT, x01.x))), et);
     if (t < nb) {
       w.q[t] = e;
     } else {
@@ -1209,6 +1209,11 @@ __global__ void exp_selftest_kernel(const double* __restrict__ tab, int64_t n, c
     y[i] = exp_t(x[i], tab);
 }
 
+__global__ void exp256_selftest_kernel(const double* __restrict__ tab, int64_t n, const double* x, double* y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = exp_s256(x[i], tab);
+}
+
 __global__ void log_selftest_kernel(const double* __restrict__ tab, int64_t n, const double* x, double* y) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = log_t(x[i], tab);
@@ -1232,6 +1237,12 @@ int launch_exp_selftest(const DevMech& m, int64_t n, const double* x, double* y,
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
   exp_selftest_kernel<<<(int)blocks, 256, 0, s>>>(m.exptab, n, x, y);
   return cuda_check(cudaGetLastError(), "exp_selftest_kernel launch");
+}
+
+int launch_exp256_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  exp256_selftest_kernel<<<(int)blocks, 256, 0, s>>>(m.exptab, n, x, y);
+  return cuda_check(cudaGetLastError(), "exp256_selftest_kernel launch");
 }
 
 int launch_log_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s) {

@@ -42,14 +42,15 @@ struct DevMech {
   // energy shifted by element potentials (P = composition x pinv(reference compositions));
   // balanced reactions cancel the shift exactly, and it keeps exp(-g') products in range.
   // Per species and range one polynomial: [0] + [1] ln T + T ([2] + T ([3] + T ([4] + T [5])))
-  // + [6] / T ([7] unused).
+  // + [6] / T ([7] unused), times 256/ln 2 (exp_s256's argument unit).
   const double* gneg;      // [K][2][8]
   const double* exptab;    // [256] 2^(j/256), the table of the FP64 exponential below
   const double* logtab;    // [97][3] F = j/128, 1/F, log F (j = 96..192): the table of log_t below
   const double* compW;     // [K][E] element counts divided by the molar mass (mol/kg)
   // Exponentials of one right-hand side, in lane rounds: item t < n_tb_end is k_f of reaction
   // t, then 5 per falloff reaction (k_inf, k_0/k_inf, the three F_cent terms).  Item t is
-  // exp(xarg[4t] + xarg[4t+1] ln T - xarg[4t+2] / T + xarg[4t+3] T).
+  // exp(x) with x = xarg[4t] + xarg[4t+1] ln T - xarg[4t+2] / T + xarg[4t+3] T, the
+  // coefficients stored times 256/ln 2 (exp_s256's argument unit).
   int n_x;
   const double* xarg;      // [n_x][4]
   // Lane-balanced species production rates: lane L walks entries bal[i*32 + L], i < bal_P,
@@ -120,6 +121,39 @@ __device__ __forceinline__ double exp_t(double x, const double* __restrict__ tab
   }
   return res;
 }
+// exp of an argument given in units of ln2/256: exp_s256(y) = 2^(y/256) = exp(y ln2/256), the
+// same table-driven method as exp_t for callers whose arguments are linear in tabulated
+// coefficients (the rate constants and free energies of the chemistry kernels), which are
+// stored pre-scaled by 256/ln 2.  y = 256 k + j + r_s with n = 256 k + j rounded from the FP32
+// value of y (|y - n| <= 0.53) and r_s = y - n exact (Sterbenz); e^(r_s ln2/256) - 1 from
+// its degree-4 Taylor polynomial in r_s, whose coefficients carry the powers of ln2/256
+// (truncation below 5e-17 relative).  6 FP64 instructions; within 2 ulp of 2^(y/256)
+// (tested).  y below -261485.59 (x < -708) returns 0, y >= 2^18 (x > 709.78) +inf, NaN
+// propagates.
+__device__ __forceinline__ double exp_s256(double y, const double* __restrict__ tab) {
+  const float kMagicf = 12582912.0f;                 // 1.5 * 2^23: rounds to an integer
+  const double c1 = 0.0027076061740622863;           // ln 2 / 256
+  const double c2 = 3.6655655969101062e-06;          // c1^2 / 2
+  const double c3 = 3.3083026805413713e-09;          // c1^3 / 6
+  const double c4 = 2.239395190875157e-12;           // c1^4 / 24
+  const float tf = narrow_f32(y) + kMagicf;
+  const int nn = (int)(__float_as_uint(tf) - 0x4B400000u);   // tf = 1.5 * 2^23 + n
+  const double rs = y - widen_f64(tf - kMagicf);             // y - n, exactly
+  double q = fma(rs, c4, c3);
+  q = fma(q, rs, c2);
+  q = fma(q, rs, c1);
+  const double tj = __ldg(tab + (nn & 255));
+  double res = fma(tj * rs, q, tj);                  // 2^(j/256) (1 + r_s q)
+  res = __longlong_as_double(__double_as_longlong(res) + ((long long)(nn >> 8) << 52));
+  // |y| >= 261485, inf and NaN, detected on the exponent bits (integer pipe, rare branch)
+  if (((unsigned int)((unsigned long long)__double_as_longlong(y) >> 32) & 0x7fffffffu) >= 0x410feb68u) {
+    if (y != y) res = y;
+    else if (y < -261485.59077104286) res = 0.0;
+    else if (y >= 262144.0) res = __longlong_as_double(0x7ff0000000000000LL);
+  }
+  return res;
+}
+
 // FP64 natural logarithm by the table-driven method (P. T. P. Tang, "Table-driven
 // implementation of the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16,
 // 1990): x = 2^k m with m in [0.75, 1.5), F = j/128 the grid point nearest m (j = 96..192),
@@ -212,6 +246,7 @@ size_t di_smem_per_warp(const DevMech& m);
 
 int launch_rcp_selftest(int64_t n, const double* x, double* y, cudaStream_t s);
 int launch_exp_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s);
+int launch_exp256_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s);
 int launch_log_selftest(const DevMech& m, int64_t n, const double* x, double* y, cudaStream_t s);
 
 // thermo.cu

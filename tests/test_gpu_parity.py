@@ -279,6 +279,28 @@ def test_table_exp_against_cuda_exp(lc, gmech):
     assert np.isnan(v[0]) and v[1] == np.inf and v[2] == 0.0 and v[3] == 0.0 and v[4] == np.inf
 
 
+def test_scaled_exp_against_exp2(lc, gmech):
+    """The kernels' FP64 exponential of pre-scaled arguments, 2^(x/256), stays within 2 ulp of
+    exp2(x/256) over the range the rate and equilibrium constants use, and handles the ends."""
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.uniform(-261485.0, 262143.9, 200000), rng.uniform(-300, 300, 100000),
+                        rng.uniform(-20000, 20000, 100000), [0.0, -0.0, 1e-300, 256.0, -256.0, 262143.9]])
+    xd = _dev(x)
+    y = torch.empty_like(xd)
+    lc.chem_selftest_exp256(gmech["h2_9"], xd, y)
+    torch.cuda.synchronize()
+    yy, rr = y.cpu().numpy(), np.exp2(x / 256.0)
+    ulp = np.abs(yy - rr) / np.spacing(np.abs(rr))
+    assert ulp.max() <= 2.0, (ulp.max(), x[np.argmax(ulp)])
+    assert yy[x == 0.0][0] == 1.0 and yy[x == 256.0][0] == 2.0
+    spec = _dev(np.array([np.nan, np.inf, -np.inf, -300000.0, 262144.0, 1e300]))
+    ys = torch.empty_like(spec)
+    lc.chem_selftest_exp256(gmech["h2_9"], spec, ys)
+    torch.cuda.synchronize()
+    v = ys.cpu().numpy()
+    assert np.isnan(v[0]) and v[1] == np.inf and v[2] == 0.0 and v[3] == 0.0 and v[4] == np.inf and v[5] == np.inf
+
+
 def test_reciprocal_against_division(lc):
     """The kernels' FP64 reciprocal (hardware estimate, one third-order step) stays within 1 ulp
     of the correctly rounded 1/x over the normal range, and gives NaN for 0 and inf."""
