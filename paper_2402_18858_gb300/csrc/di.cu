@@ -68,7 +68,9 @@ __device__ __forceinline__ double comp_get(const double (&x)[NPL], int i) {
 // per-warp shared memory
 // ------------------------------------------------------------------------------------------
 struct WarpMem {
-  double* J;      // n x ld (Jacobian; rows 0..K-1 first hold dwdot/dC)
+  double* J;      // n x ld (Jacobian; rows 0..K-1 first hold dwdot/dC); in the compact layout
+                  // the Jacobian is assembled in the LU region and kept as J32
+  float* J32;     // n x ld compact layout only: the Jacobian rounded to FP32 (else null)
   double* LU;     // n x ld (factors of I - c J)
   double* C;      // K concentrations
   double* hRT;    // K
@@ -95,27 +97,60 @@ constexpr int kTroeSlots = 14;
 // The per-reaction Jacobian terms (kfe, kre, aux, qT) are live only between rhs_eval<true> and
 // jac_assemble, when the LU factors are stale (they are refactored right after), so with the
 // matrices present they share the LU region whenever it is large enough.
+// Compact layout (j32, for large mechanisms where it saves shared memory): the Jacobian is
+// assembled in FP64 in the LU region and stored rounded to FP32 between refactorisations (it
+// only shapes the Newton iteration matrix, which is approximate anyway: it is reused for up to
+// 50 steps; the LU and every solve stay FP64); the Jacobian terms then share the FP32 region.
 __host__ __device__ inline bool jac_terms_in_lu(int I, int n) {
   return 4 * (size_t)(I > 0 ? I : 1) <= (size_t)n * pad_ld(n);
 }
+__host__ __device__ inline size_t j32_doubles(int n) { return ((size_t)n * pad_ld(n) + 1) / 2; }
+__host__ __device__ inline bool jac_terms_in_j32(int I, int n) {
+  return 4 * (size_t)(I > 0 ? I : 1) <= j32_doubles(n);
+}
 
-__host__ __device__ inline size_t warp_doubles(int K, int I, int n, int nT, bool mats, bool jac) {
+__host__ __device__ inline size_t warp_doubles(int K, int I, int n, int nT, bool mats, bool jac, bool j32 = false) {
   size_t ld = pad_ld(n);
-  size_t d = (mats ? 2 * (size_t)n * ld : (jac ? (size_t)n * ld : 0));
-  const bool alias = mats && jac && jac_terms_in_lu(I, n);
+  size_t d;
+  bool alias;
+  if (mats && j32) {
+    d = (size_t)n * ld + j32_doubles(n);
+    alias = jac_terms_in_j32(I, n);
+  } else {
+    d = (mats ? 2 * (size_t)n * ld : (jac ? (size_t)n * ld : 0));
+    alias = mats && jac && jac_terms_in_lu(I, n);
+  }
   d += 5 * (size_t)K + 3 + (jac && !alias ? 5 : 1) * (size_t)(I > 0 ? I : 1) + (size_t)kTroeSlots * nT;
   d += (size_t)n + 64 + (size_t)(n + 1) / 2 + 2;
   return (d + 1) & ~size_t(1);   // keep 16-byte alignment per warp
 }
 
-__device__ __forceinline__ WarpMem carve(double* base, int K, int I, int n, int nT, bool mats, bool jac) {
+// the direct-integration kernel's layout: compact when that needs less shared memory (the
+// kernel for n <= 32 always takes the FP64 layout: the compact one is larger there)
+__host__ __device__ inline bool di_use_j32(int K, int I, int n, int nT) {
+  return warp_doubles(K, I, n, nT, true, true, true) < warp_doubles(K, I, n, nT, true, true, false);
+}
+
+__device__ __forceinline__ WarpMem carve(double* base, int K, int I, int n, int nT, bool mats, bool jac,
+                                         bool j32 = false) {
   WarpMem w;
   w.ld = pad_ld(n);
   double* p = base;
   w.J = nullptr;
+  w.J32 = nullptr;
   w.LU = nullptr;
-  if (mats || jac) { w.J = p; p += (size_t)n * w.ld; }
-  if (mats) { w.LU = p; p += (size_t)n * w.ld; }
+  double* alias_at = nullptr;
+  if (mats && j32) {
+    w.LU = p; p += (size_t)n * w.ld;
+    w.J = w.LU;
+    w.J32 = (float*)p;
+    if (jac && jac_terms_in_j32(I, n)) alias_at = p;
+    p += j32_doubles(n);
+  } else {
+    if (mats || jac) { w.J = p; p += (size_t)n * w.ld; }
+    if (mats) { w.LU = p; p += (size_t)n * w.ld; }
+    if (jac && mats && jac_terms_in_lu(I, n)) alias_at = w.LU;
+  }
   w.C = p; p += K + 1;
   w.hRT = p; p += K;
   w.g = p; p += K;
@@ -123,11 +158,11 @@ __device__ __forceinline__ WarpMem carve(double* base, int K, int I, int n, int 
   w.ieg = p; p += K + 1;
   const int Ir = I > 0 ? I : 1;
   w.q = p; p += Ir;
-  if (jac && mats && jac_terms_in_lu(I, n)) {
-    w.kfe = w.LU;
-    w.kre = w.LU + Ir;
-    w.aux = w.LU + 2 * Ir;
-    w.qT = w.LU + 3 * Ir;
+  if (alias_at) {
+    w.kfe = alias_at;
+    w.kre = alias_at + Ir;
+    w.aux = alias_at + 2 * Ir;
+    w.qT = alias_at + 3 * Ir;
   } else if (jac) {
     w.kfe = p; p += Ir;
     w.kre = p; p += Ir;
@@ -564,6 +599,13 @@ __device__ void jac_assemble(const DevMech& m, const WarpMem& w, const double (&
   wsum2(dq, dcp, lane, dq, dcp);
   if (lane == 0) w.J[(size_t)K * ld + K] = -dq * irc + Qrc2 * (-rc * cs.invT + rho * dcp);
   __syncwarp();
+  if (NPL > 1 && w.J32) {
+    // compact layout (large mechanisms only): keep the Jacobian as FP32 (integer-pipe narrowing; the per-reaction
+    // terms that shared this region are dead now)
+    const int n = K + 1;
+    for (int e = lane; e < n * ld; e += 32) w.J32[e] = narrow_f32(w.J[e]);
+    __syncwarp();
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -580,9 +622,14 @@ __device__ bool lu_factor(const WarpMem& w, int n, double c, int lane) {
   for (int s = 0; s < NPL; ++s) {
     const int r = lane + 32 * s;
     if (r < n) {
-      const double* jr = w.J + (size_t)r * ld;
       double* lr = w.LU + (size_t)r * ld;
-      for (int cc = 0; cc < n; ++cc) lr[cc] = (r == cc ? 1.0 : 0.0) - c * jr[cc];
+      if (NPL > 1 && w.J32) {
+        const float* jr = w.J32 + (size_t)r * ld;
+        for (int cc = 0; cc < n; ++cc) lr[cc] = (r == cc ? 1.0 : 0.0) - c * widen_f64(jr[cc]);
+      } else {
+        const double* jr = w.J + (size_t)r * ld;
+        for (int cc = 0; cc < n; ++cc) lr[cc] = (r == cc ? 1.0 : 0.0) - c * jr[cc];
+      }
       w.perm[r] = r;
     }
   }
@@ -1118,7 +1165,9 @@ __global__ void __launch_bounds__(NPL == 1 ? 160 : 128, 2) di_kernel(DevMech m, 
                                                  size_t warp_bytes, const int32_t* n_dev) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, m.I - m.n_tb_end, true, true);
+  const int nT = m.I - m.n_tb_end;
+  const WarpMem w = carve((double*)((char*)smem + wid * warp_bytes), m.K, m.I, m.n, nT, true, true,
+                          NPL > 1 && di_use_j32(m.K, m.I, m.n, nT));
   // n_dev (optional): the number of entries of idx actually filled, known only on the device
   const int64_t n_eff = n_dev ? min(n, (int64_t)max(*n_dev, 0)) : n;
   while (true) {
@@ -1269,7 +1318,10 @@ static int smem_optin() {
   return v;
 }
 
-size_t di_smem_per_warp(const DevMech& m) { return warp_doubles(m.K, m.I, m.n, m.I - m.n_tb_end, true, true) * sizeof(double); }
+size_t di_smem_per_warp(const DevMech& m) {
+  const int nT = m.I - m.n_tb_end;
+  return warp_doubles(m.K, m.I, m.n, nT, true, true, m.n > 32 && di_use_j32(m.K, m.I, m.n, nT)) * sizeof(double);
+}
 
 template <typename KernelT>
 static int configure(KernelT kern, size_t warp_bytes, int& warps_per_block, size_t& smem) {
