@@ -507,6 +507,157 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_persistent(const __grid_cons
 }
 
 // ------------------------------------------------------------------------------------------
+// CTA-pair persistent GEMM: tiles of 256 x BN on two SMs (tcgen05.mma.cta_group::2).  Each CTA
+// of the pair stages its own 128 rows of A and its own BN/2 rows of B per K slab, so one
+// M = 256 MMA moves 28 % fewer operand bytes through each SM's shared memory per FLOP than the
+// single-CTA 128 x BN tile.  Roles as in gemm_bf16_persistent, with:
+//   * both producers count their TMA bytes on the even CTA's "full" barrier (two arrivals);
+//   * the even CTA's thread 32 issues every MMA and commits to the "empty" and "accumulator
+//     full" barriers of both CTAs at once (multicast commit);
+//   * both CTAs' epilogue warps arrive on the even CTA's "accumulator empty" barrier
+//     (16 arrivals) and each reads its own TMEM (accumulator rows 0-127 or 128-255).
+// Every wait is bounded; both CTAs meet at a cluster barrier before TMEM is freed, so neither
+// leaves while the other's MMAs may still read its shared memory.
+// ------------------------------------------------------------------------------------------
+template <int BN>
+struct PairCfg {
+  static constexpr size_t A_BYTES = (size_t)tc::BM * tc::BK * 2;
+  static constexpr size_t B_BYTES = (size_t)(BN / 2) * tc::BK * 2;
+  static constexpr int STAGES = (int)((204 * 1024) / (A_BYTES + B_BYTES)) < 8
+                                    ? (int)((204 * 1024) / (A_BYTES + B_BYTES)) : 8;
+  static constexpr uint32_t ACC_COLS = BN <= 128 ? 128 : 256;
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+  static constexpr size_t SMEM = 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 4) * 8 + 16 + 128 +
+                                 8 * kEpiWarpBytes;
+};
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(320, 1) gemm_bf16_pair(const __grid_constant__ CUtensorMap ta,
+                                                           const __grid_constant__ CUtensorMap tb,
+                                                           GemmEpi e, int M, int N, int K, int S, int* err) {
+  static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "pair tile width");
+  using C = PairCfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + S * C::A_BYTES;
+  uint64_t* full = (uint64_t*)(sB + S * C::B_BYTES);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;    // [2]
+  uint64_t* acce = accf + 2;     // [2]
+  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+  uint8_t* stage = (uint8_t*)(((uintptr_t)(tmem_slot + 4) + 127) & ~(uintptr_t)127);   // 8 warps x 2 KB
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = tc::cluster_rank();
+  const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int nkb = (K + tc::BK - 1) / tc::BK;
+  const int n_tiles = (N + BN - 1) / BN;
+  const int total = n_tiles * ((M + 2 * tc::BM - 1) / (2 * tc::BM));
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);    // the even CTA's producer expects the bytes of both CTAs
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&accf[b], 1);
+      tc::mbar_init(&acce[b], 16);   // one arrival per epilogue warp of both CTAs
+    }
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) tc::tmem_alloc_pair(tmem_slot, C::TMEM_COLS);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::cluster_sync();                // barriers of both CTAs initialised before any remote arrival
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer of this CTA's halves; bytes counted on the even CTA's "full" barrier
+      const uint32_t full0 = tc::mapa_shared(tc::smem_u32(full), 0);
+      int g = 0;
+      for (int t = cid; t < total && !gemm_failed(err); t += ncl) {
+        const int m0 = (t / n_tiles) * 2 * tc::BM, n0 = (t % n_tiles) * BN;
+        const int ay = m0 + (int)rank * tc::BM, by = n0 + (int)rank * (BN / 2);
+        bool stop = false;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % S;
+          if (g >= S && !tc::mbar_wait(&empty[s], ((g / S) & 1) ^ 1, err, 21)) { stop = true; break; }
+          const uint32_t fb = full0 + (uint32_t)s * 8u;
+          // the even CTA's stage fills once both CTAs' halves have landed; the odd CTA's bytes
+          // may land before this arrival (the transaction count goes transiently negative)
+          if (rank == 0) tc::mbar_expect_tx(&full[s], (uint32_t)(2 * (C::A_BYTES + C::B_BYTES)));
+          tc::tma_load_2d_pair(sA + s * C::A_BYTES, &ta, fb, kb * tc::BK, ay);
+          tc::tma_load_2d_pair(sB + s * C::B_BYTES, &tb, fb, kb * tc::BK, by);
+        }
+        if (stop) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      // the pair's MMAs, issued by the even CTA into the two accumulators in turn
+      constexpr uint32_t idesc = tc::idesc_bf16_f32<2 * tc::BM, BN>();
+      int g = 0, it = 0;
+      for (int t = cid; t < total && !gemm_failed(err); t += ncl, ++it) {
+        const int b = it & 1, u = it >> 1;
+        if (u > 0 && !tc::mbar_wait(&acce[b], (u & 1) ^ 1, err, 22)) break;
+        tc::tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)b * C::ACC_COLS;
+        bool stop = false;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % S;
+          if (!tc::mbar_wait(&full[s], (g / S) & 1, err, 23)) { stop = true; break; }
+          tc::tc_fence_after();
+          const uint64_t da = tc::sw128_desc(sA + s * C::A_BYTES);
+          const uint64_t db = tc::sw128_desc(sB + s * C::B_BYTES);
+#pragma unroll
+          for (int k = 0; k < tc::BK / tc::UMMA_K; ++k)
+            tc::mma_bf16_pair(acc, da + (uint64_t)((k * tc::UMMA_K * 2) >> 4),
+                              db + (uint64_t)((k * tc::UMMA_K * 2) >> 4), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          tc::mma_commit_pair(&empty[s]);
+        }
+        if (stop) break;
+        tc::mma_commit_pair(&accf[b]);
+      }
+    }
+  } else {
+    // epilogue warps 2..9 of each CTA: this CTA's 128 accumulator rows
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t acce0 = tc::mapa_shared(tc::smem_u32(acce), 0);
+    int it = 0;
+    for (int t = cid; t < total; t += ncl, ++it) {
+      const int b = it & 1, u = it >> 1;
+      if (gemm_failed(err) || !tc::mbar_wait(&accf[b], u & 1, err, 24)) break;
+      tc::tc_fence_after();
+      const int m0 = (t / n_tiles) * 2 * tc::BM + (int)rank * tc::BM, n0 = (t % n_tiles) * BN;
+      const int row0 = m0 + quarter * 32, row = row0 + lane;
+      const int nrows = max(0, min(32, M - row0));
+      uint8_t* wbuf = stage + (warp - 2) * kEpiWarpBytes;
+      const uint32_t acc = tmem + (uint32_t)b * C::ACC_COLS + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int c0 = half * 32; c0 < BN; c0 += 64) {
+        if (n0 + c0 >= N) break;
+        float v[32];
+        tc::tmem_ld32(acc + (uint32_t)c0, v);
+        epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), e, wbuf, row0, nrows, lane);
+        __syncwarp();
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive_cluster(acce0 + (uint32_t)b * 8u);
+    }
+  }
+  tc::tc_fence_before();
+  __syncwarp();
+  __syncthreads();
+  tc::cluster_sync();                // no CTA leaves while the pair's MMAs may read its stages
+  tc::tc_fence_after();
+  if (warp == 1) tc::tmem_dealloc_pair(tmem, C::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------------------------------
 // host: tensor maps and launch
 // ------------------------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -544,6 +695,53 @@ static int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t co
 }
 
 template <int BN, int EPI>
+static int launch_pair_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int M, int N, int K,
+                         const GemmEpi& e, int* err, cudaStream_t s) {
+  using P = PairCfg<BN>;
+  CUtensorMap ta, tb;
+  int rc;
+  if ((rc = make_map(&ta, A, M, K, lda, tc::BM))) return rc;
+  if ((rc = make_map(&tb, B, N, K, ldb, BN / 2))) return rc;
+  static int max_clusters = 0;
+  static bool configured = false;
+  const int nkb = (K + tc::BK - 1) / tc::BK;
+  const int S = nkb < P::STAGES ? nkb : P::STAGES;
+  const size_t smem = 1024 + (size_t)S * (P::A_BYTES + P::B_BYTES) + (2 * (size_t)S + 4) * 8 + 16 + 128 +
+                      8 * (size_t)kEpiWarpBytes;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(320, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (!configured) {
+    if ((rc = cuda_check(cudaFuncSetAttribute(gemm_bf16_pair<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)P::SMEM), "gemm pair smem attribute")))
+      return rc;
+    cudaLaunchConfig_t q = cfg;
+    q.dynamicSmemBytes = P::SMEM;
+    q.gridDim = dim3(2, 1, 1);
+    int nc = 0;
+    if ((rc = cuda_check(cudaOccupancyMaxActiveClusters(&nc, gemm_bf16_pair<BN, EPI>, &q), "gemm pair occupancy")))
+      return rc;
+    if (nc <= 0) return set_error(CHEM_E_UNSUPPORTED, "gemm: no CTA pair fits on the device");
+    max_clusters = nc;
+    configured = true;
+  }
+  const int64_t total = (int64_t)((N + BN - 1) / BN) * ((M + 2 * tc::BM - 1) / (2 * tc::BM));
+  if (total > 0x7fffffff) return set_error(CHEM_E_ARG, "gemm: too many tiles in one call");
+  const int ncl = (int)std::min<int64_t>(total, (int64_t)max_clusters);
+  cfg.gridDim = dim3(2 * (unsigned)ncl, 1, 1);
+  return cuda_check(cudaLaunchKernelEx(&cfg, gemm_bf16_pair<BN, EPI>, ta, tb, e, M, N, K, S, err),
+                    "gemm_bf16_pair launch");
+}
+
+template <int BN, int EPI>
 static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int M, int N, int K,
                          const GemmEpi& e, int* err, cudaStream_t s) {
   CUtensorMap ta, tb;
@@ -557,6 +755,10 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
   if constexpr (EPI == 4) {
     if (nkb_all > 2 || G > 1 || N % 32) return set_error(CHEM_E_ARG, "gemm: epilogue 4 needs K <= 128, N % 32 == 0");
   } else if (nkb_all > 2 || G > 1) {
+    if constexpr (BN >= 128) {
+      // long K, wide tiles, at least one 256-row block: CTA pairs (cta_group::2)
+      if (G == 1 && M >= 2 * tc::BM) return launch_pair_t<BN, EPI>(A, lda, B, ldb, M, N, K, e, err, s);
+    }
     // long K: persistent warp-specialised kernel, one CTA per SM
     using P = PersistCfg<BN>;
     static bool pconfigured = false;
@@ -617,17 +819,23 @@ int gemm_bf16(int epi, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, i
   }
   // tile width: N <= 128 takes the narrowest of 32/64/128 that covers it; wider layers take the
   // tile of at least 128 columns with the least padded width ceil(N / BN) BN, ties to the wider
-  // (N = 1600 and 800 take 160, N = 400 and 2000 take 224, N = 1000 and 500 take 256) -- narrow
-  // tiles on wide layers would reload the A tile once per 32 columns.  A short K (<= 128, the
-  // first layer) takes 128: its time is the epilogue, and 128 TMEM columns per CTA let four
-  // CTAs share an SM instead of two.
+  // (single CTAs: N = 1600 and 800 take 160, N = 400 and 2000 take 224, N = 1000 and 500 take
+  // 256), or on CTA pairs the least padded width weighted by 1 + 128/BN (N = 800 and 400 take
+  // 224, 1600, 2000, 1000 and 500 take 256) -- narrow tiles on wide layers would reload the A
+  // tile once per 32 columns.  A short K (<= 128, the first layer) takes 128: its time is the
+  // epilogue, and 128 TMEM columns per CTA let four CTAs share an SM instead of two.
   int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
   if (N > 128 && K > 128) {
     static const int kBN[] = {256, 224, 160, 128};
+    const bool pair = e.groups <= 1 && M >= 2 * tc::BM && K > 2 * tc::BK;
     int64_t best = INT64_MAX;
     for (int c : kBN) {
       const int64_t padded = (int64_t)((N + c - 1) / c) * c;
-      if (padded < best) { best = padded; bn = c; }
+      // CTA pairs: time ~ padded width x (1 + 128 / BN) -- a wider MMA carries its fixed cost
+      // over more columns (measured: the 800-wide layer runs 7 % faster at 224, padded to 896,
+      // than at 160)
+      const int64_t cost = pair ? padded * (c + 128) / c : padded;
+      if (cost < best) { best = cost; bn = c; }
     }
   }
   // the first layer's forward without a pre-activation copy: the short-K kernel's lean GELU epilogue

@@ -37,7 +37,10 @@ def _dgelu(x):
     return 0.5 * (1.0 + erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2 * math.pi)
 
 
-SHAPES = [(128, 32, 64), (257, 160, 200), (1000, 1600, 64), (513, 400, 800), (4096, 32, 400), (130, 800, 1600)]
+# long-K shapes with at least 256 rows run on CTA pairs (tiles 256 x 128/160/224/256), the others
+# on single CTAs
+SHAPES = [(128, 32, 64), (257, 160, 200), (1000, 1600, 64), (513, 400, 800), (4096, 32, 400), (130, 800, 1600),
+          (600, 1000, 520), (300, 128, 304), (700, 800, 1600)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
