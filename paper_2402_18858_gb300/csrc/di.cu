@@ -45,6 +45,10 @@ __device__ __forceinline__ void wsum2(double a, double b, int lane, double& sa, 
   sb = __shfl_sync(FULLMASK, v, 16);
 }
 
+// a < b and a > b for non-negative doubles (not -0), on their bit patterns (integer pipe)
+__device__ __forceinline__ bool pos_lt(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+__device__ __forceinline__ bool pos_gt(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
+
 // x is finite, tested on its exponent bits (integer pipe)
 __device__ __forceinline__ bool finite_bits(double x) {
   return ((unsigned int)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7ff00000u) != 0x7ff00000u;
@@ -972,18 +976,19 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
   double t = 0.0;
   int status = CHEM_CELL_OK;
 
-  while (t < dt) {
+  // t, h, dt and hmin are positive (t starts at +0): their comparisons run on the bit patterns
+  while (pos_lt(t, dt)) {
     if (cnt[0] >= o.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
-    const double hmin = 10.0 * EPS * fabs(t) + 1e-300;
-    if (t + h > dt) {
+    const double hmin = fma(10.0 * EPS, t, 1e-300);
+    if (pos_gt(t + h, dt)) {
       const double hn = dt - t;
       rescale_D<NPL>(D, order, hn / h, w, rc, lane);
       h = hn;
       n_equal = 0;
     }
-    if (h < hmin || fails > 60) { status = CHEM_CELL_STEP_FAIL; break; }
+    if (pos_lt(h, hmin) || fails > 60) { status = CHEM_CELL_STEP_FAIL; break; }
     double t_new = t + h;
-    if (t_new > dt || dt - t_new < hmin) t_new = dt;
+    if (pos_gt(t_new, dt) || pos_lt(dt - t_new, hmin)) t_new = dt;
     // predictor and the history term psi
     const double ig = bdf_inv_gamma(order);
     switch (order) {
@@ -1010,7 +1015,9 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
       have_lu = false;
       f_at_pred = true;   // f(ypred) doubles as the first Newton residual
     }
-    if (!have_lu || fabsf((float)(c * ic_lu) - 1.0f) > 0.3f) {
+    // c / c_lu in FP32 (it only steers the refactorisation and the correction scale)
+    float cr = narrow_f32(c * ic_lu);
+    if (!have_lu || fabsf(cr - 1.0f) > 0.3f) {
       if (!lu_factor<NPL>(w, n, c, lane)) {
         // singular Newton matrix: shrink the step
         fails++;
@@ -1028,7 +1035,8 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     }
     // modified Newton with a stale h/gamma: scale the correction by 2 / (1 + c / c_lu)
     const bool rescale = c != c_lu;
-    const double lscale = rescale ? (double)(2.0f / (1.0f + (float)(c * ic_lu))) : 1.0;
+    if (!rescale) cr = 1.0f;
+    const double lscale = widen_f64(2.0f / (1.0f + cr));
     bool converged = false;
     float dn_old = 0.0f;
     newton_iters = 0;
@@ -1077,8 +1085,9 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     if (!(en <= 1.0f)) {
       fails++;
       const float fac = fmaxf(0.2f, safety * exp2f(-log2f(fmaxf(en, 1e-30f)) / (float)(order + 1)));
-      rescale_D<NPL>(D, order, (double)fac, w, rc, lane);
-      h *= (double)fac;
+      const double facd = widen_f64(fac);
+      rescale_D<NPL>(D, order, facd, w, rc, lane);
+      h *= facd;
       n_equal = 0;
       continue;
     }
@@ -1124,7 +1133,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
     // every proposed factor is taken, small growth included: a factor up to 1.3 reuses the
     // LU (the refactorisation test above), and keeping h below CVODE's 1.5 threshold cost
     // 16 % more steps on the 30-species workload
-    const double fac = (double)facf;
+    const double fac = widen_f64(facf);
     rescale_D<NPL>(D, order, fac, w, rc, lane);
     h *= fac;
   }
