@@ -647,7 +647,8 @@ __device__ bool lu_factor(const WarpMem& w, int n, double c, int lane) {
     for (int s = 0; s < NPL; ++s) {
       const int r = lane + 32 * s;
       if (r >= col && r < n) {
-        const unsigned long long kv = (unsigned long long)__double_as_longlong(fabs(w.LU[(size_t)r * ld + col]));
+        const unsigned long long kv =
+            (unsigned long long)__double_as_longlong(w.LU[(size_t)r * ld + col]) & 0x7fffffffffffffffull;   // |v|
         if (row == 0xffffffffu || kv > key) { key = kv; row = (unsigned int)r; }
       }
     }

@@ -553,7 +553,9 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_pair(const __grid_constant__
   const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
   const int nkb = (K + tc::BK - 1) / tc::BK;
   const int n_tiles = (N + BN - 1) / BN;
-  const int total = n_tiles * ((M + 2 * tc::BM - 1) / (2 * tc::BM));
+  // tile t: group t / per_group, then 256-row block, then N tile (fastest)
+  const int per_group = n_tiles * ((M + 2 * tc::BM - 1) / (2 * tc::BM));
+  const int total = per_group * (e.groups > 1 ? e.groups : 1);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -579,8 +581,10 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_pair(const __grid_constant__
       const uint32_t full0 = tc::mapa_shared(tc::smem_u32(full), 0);
       int g = 0;
       for (int t = cid; t < total && !gemm_failed(err); t += ncl) {
-        const int m0 = (t / n_tiles) * 2 * tc::BM, n0 = (t % n_tiles) * BN;
-        const int ay = m0 + (int)rank * tc::BM, by = n0 + (int)rank * (BN / 2);
+        const int gr = t / per_group, r = t - gr * per_group;
+        const int m0 = (r / n_tiles) * 2 * tc::BM, n0 = (r % n_tiles) * BN;
+        const int ax = gr * e.a_col, bx = gr * e.b_col;
+        const int ay = gr * e.a_row + m0 + (int)rank * tc::BM, by = gr * e.b_row + n0 + (int)rank * (BN / 2);
         bool stop = false;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % S;
@@ -589,8 +593,8 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_pair(const __grid_constant__
           // the even CTA's stage fills once both CTAs' halves have landed; the odd CTA's bytes
           // may land before this arrival (the transaction count goes transiently negative)
           if (rank == 0) tc::mbar_expect_tx(&full[s], (uint32_t)(2 * (C::A_BYTES + C::B_BYTES)));
-          tc::tma_load_2d_pair(sA + s * C::A_BYTES, &ta, fb, kb * tc::BK, ay);
-          tc::tma_load_2d_pair(sB + s * C::B_BYTES, &tb, fb, kb * tc::BK, by);
+          tc::tma_load_2d_pair(sA + s * C::A_BYTES, &ta, fb, ax + kb * tc::BK, ay);
+          tc::tma_load_2d_pair(sB + s * C::B_BYTES, &tb, fb, bx + kb * tc::BK, by);
         }
         if (stop) break;
       }
@@ -631,17 +635,26 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_pair(const __grid_constant__
       const int b = it & 1, u = it >> 1;
       if (gemm_failed(err) || !tc::mbar_wait(&accf[b], u & 1, err, 24)) break;
       tc::tc_fence_after();
-      const int m0 = (t / n_tiles) * 2 * tc::BM + (int)rank * tc::BM, n0 = (t % n_tiles) * BN;
+      const int gr = t / per_group, r = t - gr * per_group;
+      const int m0 = (r / n_tiles) * 2 * tc::BM + (int)rank * tc::BM, n0 = (r % n_tiles) * BN;
       const int row0 = m0 + quarter * 32, row = row0 + lane;
       const int nrows = max(0, min(32, M - row0));
       uint8_t* wbuf = stage + (warp - 2) * kEpiWarpBytes;
+      GemmEpi eg = e;
+      if (gr) {
+        constexpr size_t osz = (EPI == 0 || EPI == 2) ? 2 : 4;
+        eg.out = (char*)e.out + (size_t)gr * (size_t)e.out_goff * osz;
+        if (e.zout) eg.zout = e.zout + (size_t)gr * (size_t)e.out_goff;
+        if (e.z) eg.z = e.z + (size_t)gr * (size_t)e.z_goff;
+        if (e.bias) eg.bias = e.bias + (size_t)gr * (size_t)e.bias_goff;
+      }
       const uint32_t acc = tmem + (uint32_t)b * C::ACC_COLS + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
       for (int c0 = half * 32; c0 < BN; c0 += 64) {
         if (n0 + c0 >= N) break;
         float v[32];
         tc::tmem_ld32(acc + (uint32_t)c0, v);
-        epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), e, wbuf, row0, nrows, lane);
+        epi_chunk<EPI>(v, row, n0 + c0, min(32, N - (n0 + c0)), eg, wbuf, row0, nrows, lane);
         __syncwarp();
       }
       tc::tc_fence_before();
@@ -700,8 +713,10 @@ static int launch_pair_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
   using P = PairCfg<BN>;
   CUtensorMap ta, tb;
   int rc;
-  if ((rc = make_map(&ta, A, M, K, lda, tc::BM))) return rc;
-  if ((rc = make_map(&tb, B, N, K, ldb, BN / 2))) return rc;
+  const int G = e.groups > 1 ? e.groups : 1;
+  // the maps span every group's operand, as for the single-CTA kernels
+  if ((rc = make_map(&ta, A, M + (int64_t)(G - 1) * e.a_row, K + (int64_t)(G - 1) * e.a_col, lda, tc::BM))) return rc;
+  if ((rc = make_map(&tb, B, N + (int64_t)(G - 1) * e.b_row, K + (int64_t)(G - 1) * e.b_col, ldb, BN / 2))) return rc;
   static int max_clusters = 0;
   static bool configured = false;
   const int nkb = (K + tc::BK - 1) / tc::BK;
@@ -733,7 +748,7 @@ static int launch_pair_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
     max_clusters = nc;
     configured = true;
   }
-  const int64_t total = (int64_t)((N + BN - 1) / BN) * ((M + 2 * tc::BM - 1) / (2 * tc::BM));
+  const int64_t total = (int64_t)((N + BN - 1) / BN) * ((M + 2 * tc::BM - 1) / (2 * tc::BM)) * G;
   if (total > 0x7fffffff) return set_error(CHEM_E_ARG, "gemm: too many tiles in one call");
   const int ncl = (int)std::min<int64_t>(total, (int64_t)max_clusters);
   cfg.gridDim = dim3(2 * (unsigned)ncl, 1, 1);
@@ -757,7 +772,7 @@ static int launch_gemm_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
   } else if (nkb_all > 2 || G > 1) {
     if constexpr (BN >= 128) {
       // long K, wide tiles, at least one 256-row block: CTA pairs (cta_group::2)
-      if (G == 1 && M >= 2 * tc::BM) return launch_pair_t<BN, EPI>(A, lda, B, ldb, M, N, K, e, err, s);
+      if (M >= 2 * tc::BM) return launch_pair_t<BN, EPI>(A, lda, B, ldb, M, N, K, e, err, s);
     }
     // long K: persistent warp-specialised kernel, one CTA per SM
     using P = PersistCfg<BN>;
@@ -827,7 +842,7 @@ int gemm_bf16(int epi, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, i
   int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
   if (N > 128 && K > 128) {
     static const int kBN[] = {256, 224, 160, 128};
-    const bool pair = e.groups <= 1 && M >= 2 * tc::BM && K > 2 * tc::BK;
+    const bool pair = M >= 2 * tc::BM && K > 2 * tc::BK;
     int64_t best = INT64_MAX;
     for (int c : kBN) {
       const int64_t padded = (int64_t)((N + c - 1) / c) * c;

@@ -54,6 +54,7 @@ def _dgelu(x):
 #   wgrad: weight gradient, A [G N, K] row blocks (N rows per group), B [G K', K] row blocks
 #   dgrad: data gradient with GELU', A [M, G K] column blocks, B [G N, K] row blocks
 #   owgrad: output-layer weight gradient, one row per group
+# (fwd 300 x 200 x 136 and wgrad 400 x 800 x 256 also run on CTA pairs)
 CASES = [
     ("fwd", 0, 3, 300, 200, 136),
     ("fwd", 0, 4, 129, 800, 1600),
@@ -65,6 +66,9 @@ CASES = [
     ("dgrad", 2, 3, 200, 72, 40),
     ("dgrad", 2, 2, 130, 800, 400),
     ("owgrad", 3, 6, 1, 48, 264),
+    # at least 256 rows and 128+-wide tiles: CTA pairs
+    ("fwd", 0, 3, 600, 800, 1600),
+    ("dgrad", 2, 2, 520, 800, 400),
 ]
 
 
