@@ -33,10 +33,10 @@ constexpr int kInPad = 64;          // input features padded to one 64-wide K sl
 constexpr int kStatBlock = 256;
 
 // Box-Cox transform of a mass fraction (Eq. 7 read as (x^lambda - 1)/lambda, x clipped >= 0)
-__device__ __forceinline__ float bct_f(double y) {
-  const float x = (float)fmax(y, 0.0);
+__device__ __forceinline__ float bct_x(float x) {
   return x > 0.0f ? (exp2f(kLambda * log2f(x)) - 1.0f) * (1.0f / kLambda) : -1.0f / kLambda;
 }
+__device__ __forceinline__ float bct_f(double y) { return bct_x((float)fmax(y, 0.0)); }
 // inverse: x = (lambda z + 1)^(1/lambda) = t^10, 0 where t <= 0
 __device__ __forceinline__ float ibct_f(float z) {
   const float t = fmaxf(kLambda * z + 1.0f, 0.0f);
@@ -200,11 +200,18 @@ __global__ void stats_partial_kernel(int64_t n, int64_t ld, const double* T, con
 }
 
 // network output -> new state; flags: 1 range, 2 non-finite, 4 element residual, 8 T range, 16 |dT|
+// FP32 work of the update (the enthalpy and element sums of the old and predicted states, T
+// from h by Newton) reads FP32 copies of the NASA-7 and composition tables, so that no
+// FP64 -> FP32 conversion runs per table entry; the element projection stays FP64 and skips
+// the zero entries of the composition (a warp-uniform test: every thread is at the same
+// species).  EC: compile-time bound on the element count (registers for the E x E system).
+template <int EC>
 __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const double* p, double* Y,
                               const float* U, int n_out_pad, const float* out_mean, const float* out_sd,
                               int32_t* flags, int32_t* status, float elem_tol, float Tmin, float Tmax, float dTmax,
                               const int32_t* idx) {
   const int K = m.K, E = m.E;
+  const float Tmidf = (float)m.Tmid;
   for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < n;
        slot += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = idx ? (int64_t)idx[slot] : slot;   // cell column; U, flags, status by slot
@@ -212,9 +219,10 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
     if (flag == 0) {
       float yn[CHEM_MAX_SPECIES];    // prediction (inverse Box-Cox, renormalised)
       float yp[CHEM_MAX_SPECIES];    // the state T' is solved for: projected, or yn when flagged
-      float eo[kMaxElem], en[kMaxElem];
-      double eod[kMaxElem], lam[kMaxElem];
-      for (int e = 0; e < E; ++e) {
+      float eo[EC], en[EC];
+      double eod[EC], lam[EC];
+#pragma unroll
+      for (int e = 0; e < EC; ++e) {
         eo[e] = en[e] = 0.0f;
         eod[e] = lam[e] = 0.0;
       }
@@ -222,19 +230,24 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
       // enthalpy of the old state (FP32 NASA-7 sums) and old element moles
       float h0 = 0.0f, ysum = 0.0f;
       bool finite = true;
-      const int hi0 = T0 >= (float)m.Tmid ? 1 : 0;
+      const int hi0 = T0 >= Tmidf ? 1 : 0;
       for (int k = 0; k < K; ++k) {
         const double y = Y[(size_t)k * ld + i];
-        const double* a = m.th + ((size_t)k * 2 + hi0) * kThermoStride;
-        const float hRT = (float)a[5] + T0 * ((float)a[6] + T0 * ((float)a[7] + T0 * ((float)a[8] + T0 * (float)a[9])))
-                          + (float)a[10] / T0;
-        h0 += (float)(y * m.invW[k]) * hRT;
-        for (int e = 0; e < E; ++e) {
-          const double c = y * m.compW[(size_t)k * E + e];
-          eod[e] += c;
-          eo[e] += (float)c;
+        const float yf = narrow_f32(y);
+        const float* a = m.th32 + ((size_t)k * 2 + hi0) * 16;
+        const float hRT = a[5] + T0 * (a[6] + T0 * (a[7] + T0 * (a[8] + T0 * a[9]))) + a[10] / T0;
+        h0 += yf * m.invW32[k] * hRT;
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+          if (e < E) {
+            const float cf = m.compW32[(size_t)k * E + e];
+            if (cf != 0.0f) {
+              eod[e] = fma(y, m.compW[(size_t)k * E + e], eod[e]);
+              eo[e] = fmaf(yf, cf, eo[e]);
+            }
+          }
         }
-        const float z = bct_f(y) + U[(size_t)slot * n_out_pad + k] * out_sd[k] + out_mean[k];
+        const float z = bct_x((float)fmax(y, 0.0)) + U[(size_t)slot * n_out_pad + k] * out_sd[k] + out_mean[k];
         finite = finite && isfinite(z);   // ibct_f would map a NaN to 0 (fmaxf)
         const float v = ibct_f(z);
         yn[k] = v;
@@ -246,56 +259,88 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
         const float is = 1.0f / ysum;
         for (int k = 0; k < K; ++k) {
           yn[k] *= is;
-          for (int e = 0; e < E; ++e) en[e] += yn[k] * (float)m.compW[(size_t)k * E + e];
+#pragma unroll
+          for (int e = 0; e < EC; ++e)
+            if (e < E) en[e] = fmaf(yn[k], m.compW32[(size_t)k * E + e], en[e]);
         }
         float res = 0.0f;
-        for (int e = 0; e < E; ++e)
-          if (eo[e] > 0.0f) res = fmaxf(res, fabsf(en[e] - eo[e]) / eo[e]);
+#pragma unroll
+        for (int e = 0; e < EC; ++e)
+          if (e < E && eo[e] > 0.0f) res = fmaxf(res, fabsf(en[e] - eo[e]) / eo[e]);
         if (!(res <= elem_tol)) flag |= 4;
         if (!flag) {
           // accepted: project onto exact element conservation, min sum_k dY_k^2 / w_k with
           // w_k = Y_k subject to sum_k c_ke (Y_k + dY_k) = E_old_e (c = composition / W):
           // dY = diag(w) C^T lam, (C diag(w) C^T) lam = E_old - C Y.  In FP64: the E x E system
           // can be ill-conditioned (an element carried mostly by one abundant species), and
-          // the projected state conserves the elements to FP64 rounding.
-          double Mx[kMaxElem][kMaxElem + 1];
-          for (int a1 = 0; a1 < E; ++a1) {
-            for (int a2 = 0; a2 <= E; ++a2) Mx[a1][a2] = 0.0;
-            Mx[a1][E] = eod[a1];
+          // the projected state conserves the elements to FP64 rounding.  The matrix is
+          // accumulated on its upper triangle and mirrored.
+          double Mx[EC][EC + 1];
+#pragma unroll
+          for (int a1 = 0; a1 < EC; ++a1) {
+#pragma unroll
+            for (int a2 = 0; a2 < EC; ++a2) Mx[a1][a2] = 0.0;
+            Mx[a1][EC] = eod[a1];
           }
           for (int k = 0; k < K; ++k) {
             const double wk = (double)yn[k];
-            for (int a1 = 0; a1 < E; ++a1) {
-              const double c1 = m.compW[(size_t)k * E + a1] * wk;
-              Mx[a1][E] -= c1;
-              for (int a2 = 0; a2 < E; ++a2) Mx[a1][a2] += c1 * m.compW[(size_t)k * E + a2];
+#pragma unroll
+            for (int a1 = 0; a1 < EC; ++a1) {
+              if (a1 < E && m.compW32[(size_t)k * E + a1] != 0.0f) {
+                const double c1 = m.compW[(size_t)k * E + a1] * wk;
+                Mx[a1][EC] -= c1;
+#pragma unroll
+                for (int a2 = a1; a2 < EC; ++a2)
+                  if (a2 < E && m.compW32[(size_t)k * E + a2] != 0.0f)
+                    Mx[a1][a2] = fma(c1, m.compW[(size_t)k * E + a2], Mx[a1][a2]);
+              }
             }
           }
+#pragma unroll
+          for (int a1 = 0; a1 < EC; ++a1)
+#pragma unroll
+            for (int a2 = 0; a2 < a1; ++a2) Mx[a1][a2] = Mx[a2][a1];
           // Gauss-Jordan with partial pivoting; elements absent from both states have a zero
           // row and column and keep lam = 0
-          bool live[kMaxElem];
-          for (int c = 0; c < E; ++c) live[c] = Mx[c][c] > 0.0;
-          for (int c = 0; c < E; ++c) {
+          bool live[EC];
+#pragma unroll
+          for (int c = 0; c < EC; ++c) live[c] = c < E && Mx[c][c] > 0.0;
+#pragma unroll
+          for (int c = 0; c < EC; ++c) {
             if (!live[c]) continue;
             int piv = c;
-            for (int r = c + 1; r < E; ++r)
+#pragma unroll
+            for (int r = c + 1; r < EC; ++r)
               if (live[r] && fabs(Mx[r][c]) > fabs(Mx[piv][c])) piv = r;
-            if (!(fabs(Mx[piv][c]) > 0.0)) continue;
-            if (piv != c)
-              for (int j = 0; j <= E; ++j) { const double t = Mx[c][j]; Mx[c][j] = Mx[piv][j]; Mx[piv][j] = t; }
+            // rows swapped through a select chain (indices stay compile-time constants)
+#pragma unroll
+            for (int r = c + 1; r < EC; ++r) {
+              if (r == piv) {
+#pragma unroll
+                for (int j = 0; j <= EC; ++j) { const double t = Mx[c][j]; Mx[c][j] = Mx[r][j]; Mx[r][j] = t; }
+              }
+            }
+            if (!(fabs(Mx[c][c]) > 0.0)) continue;
             const double d = 1.0 / Mx[c][c];
-            for (int j = 0; j <= E; ++j) Mx[c][j] *= d;
-            for (int r = 0; r < E; ++r) {
+#pragma unroll
+            for (int j = 0; j <= EC; ++j) Mx[c][j] *= d;
+#pragma unroll
+            for (int r = 0; r < EC; ++r) {
               if (r == c) continue;
               const double f = Mx[r][c];
-              for (int j = 0; j <= E; ++j) Mx[r][j] -= f * Mx[c][j];
+#pragma unroll
+              for (int j = 0; j <= EC; ++j) Mx[r][j] = fma(-f, Mx[c][j], Mx[r][j]);
             }
           }
-          for (int c = 0; c < E; ++c) lam[c] = (live[c] && fabs(Mx[c][c] - 1.0) < 1e-9) ? Mx[c][E] : 0.0;
+#pragma unroll
+          for (int c = 0; c < EC; ++c) lam[c] = (live[c] && fabs(Mx[c][c] - 1.0) < 1e-9) ? Mx[c][EC] : 0.0;
           for (int k = 0; k < K; ++k) {
             double cl = 0.0;
-            for (int e = 0; e < E; ++e) cl += m.compW[(size_t)k * E + e] * lam[e];
-            yp[k] = (float)fmax((double)yn[k] * (1.0 + cl), 0.0);
+#pragma unroll
+            for (int e = 0; e < EC; ++e)
+              if (e < E && m.compW32[(size_t)k * E + e] != 0.0f) cl = fma(m.compW[(size_t)k * E + e], lam[e], cl);
+            const double yd = (double)yn[k];
+            yp[k] = (float)fmax(fma(yd, cl, yd), 0.0);
           }
         } else {
           for (int k = 0; k < K; ++k) yp[k] = yn[k];
@@ -303,14 +348,13 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
         // T from h(T, Y_new) = h0 by Newton's method
         float Tn = T0;
         for (int it = 0; it < 8; ++it) {
-          const int hi = Tn >= (float)m.Tmid ? 1 : 0;
+          const int hi = Tn >= Tmidf ? 1 : 0;
           float h = 0.0f, cp = 0.0f;
           for (int k = 0; k < K; ++k) {
-            const double* a = m.th + ((size_t)k * 2 + hi) * kThermoStride;
-            const float yw = yp[k] * (float)m.invW[k];
-            const float cpR = (float)a[0] + Tn * ((float)a[1] + Tn * ((float)a[2] + Tn * ((float)a[3] + Tn * (float)a[4])));
-            const float hRT = (float)a[5] + Tn * ((float)a[6] + Tn * ((float)a[7] + Tn * ((float)a[8] + Tn * (float)a[9])))
-                              + (float)a[10] / Tn;
+            const float* a = m.th32 + ((size_t)k * 2 + hi) * 16;
+            const float yw = yp[k] * m.invW32[k];
+            const float cpR = a[0] + Tn * (a[1] + Tn * (a[2] + Tn * (a[3] + Tn * a[4])));
+            const float hRT = a[5] + Tn * (a[6] + Tn * (a[7] + Tn * (a[8] + Tn * a[9]))) + a[10] / Tn;
             h += yw * hRT * Tn;
             cp += yw * cpR;
           }
@@ -325,8 +369,11 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
           // the projected state in FP64 (accepted cells were projected)
           for (int k = 0; k < K; ++k) {
             double cl = 0.0;
-            for (int e = 0; e < E; ++e) cl += m.compW[(size_t)k * E + e] * lam[e];
-            Y[(size_t)k * ld + i] = fmax((double)yn[k] * (1.0 + cl), 0.0);
+#pragma unroll
+            for (int e = 0; e < EC; ++e)
+              if (e < E && m.compW32[(size_t)k * E + e] != 0.0f) cl = fma(m.compW[(size_t)k * E + e], lam[e], cl);
+            const double yd = (double)yn[k];
+            Y[(size_t)k * ld + i] = fmax(fma(yd, cl, yd), 0.0);
           }
           T[i] = (double)Tn;
         }
@@ -335,6 +382,24 @@ __global__ void update_kernel(DevMech m, int64_t n, int64_t ld, double* T, const
     flags[slot] = flag;
     status[slot] = flag ? CHEM_CELL_ANN_FALLBACK : CHEM_CELL_OK;
   }
+}
+
+int grid_for(int64_t n, int threads);
+
+// update_kernel with its element bound chosen from the mechanism (C/H/O/N: 4)
+static int launch_update(const DevMech& m, int64_t n, int64_t ld, double* T, const double* p, double* Y,
+                         const float* U, int n_out_pad, const float* out_mean, const float* out_sd,
+                         int32_t* flags, int32_t* status, float elem_tol, float Tmin, float Tmax, float dTmax,
+                         const int32_t* idx, cudaStream_t s) {
+  const unsigned grid = grid_for(n, 128);
+#define CHEM_UPDATE_CASE(EC)                                                                                  \
+  update_kernel<EC><<<grid, 128, 0, s>>>(m, n, ld, T, p, Y, U, n_out_pad, out_mean, out_sd, flags, status,  \
+                                         elem_tol, Tmin, Tmax, dTmax, idx)
+  if (m.E <= 3) CHEM_UPDATE_CASE(3);
+  else if (m.E <= 4) CHEM_UPDATE_CASE(4);
+  else CHEM_UPDATE_CASE(kMaxElem);
+#undef CHEM_UPDATE_CASE
+  return cuda_check(cudaGetLastError(), "update_kernel launch");
 }
 
 // deterministic compaction of cells with status != 0: per-block counts, scan, write
@@ -921,11 +986,8 @@ int chem_ann_update(chem_ann a, int64_t n, int64_t ld, double* T, const double* 
   if (opts) o = *opts;
   ann_fill_defaults(o);
   const float* om = a->norm + 4 * a->n_in;
-  update_kernel<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(a->dm, n, ld, T, p, Y, U, a->n_out_pad, om,
-                                                                   om + a->n_out, flags, status, (float)o.elem_tol,
-                                                                   (float)o.T_min, (float)o.T_max, (float)o.dT_max,
-                                                                   idx);
-  return cuda_check(cudaGetLastError(), "update_kernel launch");
+  return launch_update(a->dm, n, ld, T, p, Y, U, a->n_out_pad, om, om + a->n_out, flags, status, (float)o.elem_tol,
+                       (float)o.T_min, (float)o.T_max, (float)o.dT_max, idx, (cudaStream_t)stream);
 }
 
 int chem_ann_targets(chem_ann a, int64_t n, int64_t ld, const double* Y0, const double* Y1, float* U,
@@ -1103,10 +1165,9 @@ int chem_step_ann(chem_mech mech, chem_ann a, int64_t n, int64_t ld, double dt, 
   }
   // 3. new state, checks
   const float* om = a->norm + 4 * a->n_in;
-  update_kernel<<<grid_for(n, 128), 128, 0, s>>>(a->dm, n, ld, T, p, Y, U, a->n_out_pad, om, om + a->n_out, flags,
-                                                status, (float)o.elem_tol, (float)o.T_min, (float)o.T_max,
-                                                (float)o.dT_max, idx_in);
-  if ((rc = cuda_check(cudaGetLastError(), "update_kernel launch"))) return rc;
+  if ((rc = launch_update(a->dm, n, ld, T, p, Y, U, a->n_out_pad, om, om + a->n_out, flags, status,
+                          (float)o.elem_tol, (float)o.T_min, (float)o.T_max, (float)o.dT_max, idx_in, s)))
+    return rc;
   if (!o.no_fallback) {
     // 4. compaction of flagged cells (deterministic order) and direct integration of those
     compact_count_kernel<<<nb, kCompactBlock, 0, s>>>(n, status, blk);

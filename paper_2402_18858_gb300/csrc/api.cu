@@ -361,6 +361,16 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
     logtab[3 * (j - 96) + 1] = (double)(1.0L / F);
     logtab[3 * (j - 96) + 2] = (double)std::log(F);
   }
+  // FP32 copies for the learned step's update (its enthalpy, element sums and T(h) run in
+  // FP32): NASA-7 c_p/R (5) and h/RT (6) per species and range, 1/W, composition / W
+  std::vector<float> th32((size_t)K * 2 * 16, 0.0f), invW32(K), compW32((size_t)K * E);
+  for (int k = 0; k < K; ++k) {
+    invW32[k] = (float)(1.0 / hm.W[k]);
+    for (int rg = 0; rg < 2; ++rg)
+      for (int c = 0; c < 11; ++c)
+        th32[((size_t)k * 2 + rg) * 16 + c] = (float)th[((size_t)k * 2 + rg) * kThermoStride + c];
+    for (int e = 0; e < E; ++e) compW32[(size_t)k * E + e] = (float)(hm.comp[(size_t)k * E + e] / hm.W[k]);
+  }
   std::vector<double> compW((size_t)K * E);
   for (int k = 0; k < K; ++k)
     for (int e = 0; e < E; ++e) compW[(size_t)k * E + e] = hm.comp[(size_t)k * E + e] / hm.W[k];
@@ -464,6 +474,8 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   size_t otroe = add(troe.data(), troe.size() * 8), optr = add(sp_ptr.data(), sp_ptr.size() * 4);
   size_t orxn = add(sp_rxn.data(), sp_rxn.size() * 4), onu = add(sp_nu.data(), sp_nu.size() * 8);
   size_t ogn = add(gneg.data(), gneg.size() * 8);
+  size_t oth32 = add(th32.data(), th32.size() * 4), oiw32 = add(invW32.data(), invW32.size() * 4);
+  size_t ocw32 = add(compW32.data(), compW32.size() * 4);
   size_t oexp = add(exptab.data(), exptab.size() * 8), ocw = add(compW.data(), compW.size() * 8);
   size_t oxa = add(xarg.data(), xarg.size() * 8), olog = add(logtab.data(), logtab.size() * 8);
   size_t obal = add(bal.data(), bal.size() * 4), orun = add(run_ptr.data(), run_ptr.size() * 4);
@@ -493,6 +505,9 @@ static int upload(const HostMech& hm, chem_mech_s* cm) {
   m.exptab = (const double*)(b + oexp);
   m.logtab = (const double*)(b + olog);
   m.compW = (const double*)(b + ocw);
+  m.th32 = (const float*)(b + oth32);
+  m.invW32 = (const float*)(b + oiw32);
+  m.compW32 = (const float*)(b + ocw32);
   m.n_x = n_x;
   m.xarg = (const double*)(b + oxa);
   m.bal_P = bal_P;

@@ -47,6 +47,10 @@ struct DevMech {
   const double* exptab;    // [256] 2^(j/256), the table of the FP64 exponential below
   const double* logtab;    // [97][3] F = j/128, 1/F, log F (j = 96..192): the table of log_t below
   const double* compW;     // [K][E] element counts divided by the molar mass (mol/kg)
+  // the same rounded to FP32, for the learned step's FP32 parts
+  const float* th32;       // [K][2][16]: c_p/R (5: a1..a5), h/RT (6: a1 a2/2 .. a5/5 a6), pad
+  const float* invW32;     // [K]
+  const float* compW32;    // [K][E]
   // Exponentials of one right-hand side, in lane rounds: item t < n_tb_end is k_f of reaction
   // t, then 5 per falloff reaction (k_inf, k_0/k_inf, the three F_cent terms).  Item t is
   // exp(x) with x = xarg[4t] + xarg[4t+1] ln T - xarg[4t+2] / T + xarg[4t+3] T, the
