@@ -521,8 +521,12 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_persistent(const __grid_cons
 // ------------------------------------------------------------------------------------------
 template <int BN>
 struct PairCfg {
-  static constexpr size_t A_BYTES = (size_t)tc::BM * tc::BK * 2;
-  static constexpr size_t B_BYTES = (size_t)(BN / 2) * tc::BK * 2;
+  // KSUB 64-wide K boxes per stage: one barrier round trip and one commit per 128 of K
+  static constexpr int KSUB = 2;
+  static constexpr size_t A_BOX = (size_t)tc::BM * tc::BK * 2;
+  static constexpr size_t B_BOX = (size_t)(BN / 2) * tc::BK * 2;
+  static constexpr size_t A_BYTES = KSUB * A_BOX;
+  static constexpr size_t B_BYTES = KSUB * B_BOX;
   static constexpr int STAGES = (int)((204 * 1024) / (A_BYTES + B_BYTES)) < 8
                                     ? (int)((204 * 1024) / (A_BYTES + B_BYTES)) : 8;
   static constexpr uint32_t ACC_COLS = BN <= 128 ? 128 : 256;
@@ -551,7 +555,7 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_pair(const __grid_constant__
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = tc::cluster_rank();
   const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
-  const int nkb = (K + tc::BK - 1) / tc::BK;
+  const int nkb = (K + C::KSUB * tc::BK - 1) / (C::KSUB * tc::BK);
   const int n_tiles = (N + BN - 1) / BN;
   // tile t: group t / per_group, then 256-row block, then N tile (fastest)
   const int per_group = n_tiles * ((M + 2 * tc::BM - 1) / (2 * tc::BM));
@@ -593,8 +597,12 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_pair(const __grid_constant__
           // the even CTA's stage fills once both CTAs' halves have landed; the odd CTA's bytes
           // may land before this arrival (the transaction count goes transiently negative)
           if (rank == 0) tc::mbar_expect_tx(&full[s], (uint32_t)(2 * (C::A_BYTES + C::B_BYTES)));
-          tc::tma_load_2d_pair(sA + s * C::A_BYTES, &ta, fb, ax + kb * tc::BK, ay);
-          tc::tma_load_2d_pair(sB + s * C::B_BYTES, &tb, fb, bx + kb * tc::BK, by);
+#pragma unroll
+          for (int q = 0; q < C::KSUB; ++q) {
+            const int kx = (kb * C::KSUB + q) * tc::BK;
+            tc::tma_load_2d_pair(sA + s * C::A_BYTES + q * C::A_BOX, &ta, fb, ax + kx, ay);
+            tc::tma_load_2d_pair(sB + s * C::B_BYTES + q * C::B_BOX, &tb, fb, bx + kx, by);
+          }
         }
         if (stop) break;
       }
@@ -614,12 +622,16 @@ __global__ void __launch_bounds__(320, 1) gemm_bf16_pair(const __grid_constant__
           const int s = g % S;
           if (!tc::mbar_wait(&full[s], (g / S) & 1, err, 23)) { stop = true; break; }
           tc::tc_fence_after();
-          const uint64_t da = tc::sw128_desc(sA + s * C::A_BYTES);
-          const uint64_t db = tc::sw128_desc(sB + s * C::B_BYTES);
 #pragma unroll
-          for (int k = 0; k < tc::BK / tc::UMMA_K; ++k)
-            tc::mma_bf16_pair(acc, da + (uint64_t)((k * tc::UMMA_K * 2) >> 4),
-                              db + (uint64_t)((k * tc::UMMA_K * 2) >> 4), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          for (int q = 0; q < C::KSUB; ++q) {
+            const uint64_t da = tc::sw128_desc(sA + s * C::A_BYTES + q * C::A_BOX);
+            const uint64_t db = tc::sw128_desc(sB + s * C::B_BYTES + q * C::B_BOX);
+#pragma unroll
+            for (int k = 0; k < tc::BK / tc::UMMA_K; ++k)
+              tc::mma_bf16_pair(acc, da + (uint64_t)((k * tc::UMMA_K * 2) >> 4),
+                                db + (uint64_t)((k * tc::UMMA_K * 2) >> 4), idesc,
+                                (kb > 0 || q > 0 || k > 0) ? 1u : 0u);
+          }
           tc::mma_commit_pair(&empty[s]);
         }
         if (stop) break;
@@ -719,7 +731,7 @@ static int launch_pair_t(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
   if ((rc = make_map(&tb, B, N + (int64_t)(G - 1) * e.b_row, K + (int64_t)(G - 1) * e.b_col, ldb, BN / 2))) return rc;
   static int max_clusters = 0;
   static bool configured = false;
-  const int nkb = (K + tc::BK - 1) / tc::BK;
+  const int nkb = (K + P::KSUB * tc::BK - 1) / (P::KSUB * tc::BK);
   const int S = nkb < P::STAGES ? nkb : P::STAGES;
   const size_t smem = 1024 + (size_t)S * (P::A_BYTES + P::B_BYTES) + (2 * (size_t)S + 4) * 8 + 16 + 128 +
                       8 * (size_t)kEpiWarpBytes;
