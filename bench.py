@@ -31,7 +31,7 @@ from paper_2402_18858_gb300 import workload as wl  # noqa: E402
 
 METRIC = "chem-step cells/s: GPU DI vs ANN+fallback at stated err; serve p50/p99 ms"
 WORKLOAD = "di_c_30sp_1m"
-DI_RTOL = 1e-9           # library defaults (rtol 1e-9, atol_Y 1e-18, Newton 0.1): what the parity tests validate
+DI_RTOL = 1e-9           # library defaults (rtol 1e-9, atol_Y 1e-18, Newton 0.2): what the parity tests validate
 MECH_DIR = os.path.join(tempfile.gettempdir(), "chem_bench_mech")
 # FP64 flops of one exponential and one logarithm, FMA = 2: those of the kernels' own routines --
 # the table-driven exp (5 FMAs + 1 multiply + the 2 FMAs of the argument reduction: 13), its

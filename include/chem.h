@@ -91,7 +91,7 @@ typedef struct {
   double atol_Y;     /* absolute tolerance on mass fractions (default 1e-18 when <= 0) */
   double atol_T;     /* absolute tolerance on T in K (default 1e-9 when <= 0) */
   double newton_tol; /* Newton stop: estimated remaining correction in units of the local
-                        error test (default 0.1 when <= 0) */
+                        error test (default 0.2 when <= 0) */
   int max_steps;     /* per-cell step budget (default 20000 when <= 0) */
   int reserved;
 } chem_di_opts;

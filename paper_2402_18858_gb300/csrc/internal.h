@@ -14,7 +14,7 @@ constexpr double kR = 8.314462618;    // J/mol/K
 constexpr double kP0 = 101325.0;      // standard pressure of the NASA-7 entropies, Pa
 constexpr int kMaxEx = 4;             // non-unit third-body efficiencies kept per reaction
 constexpr int kThermoStride = 17;     // per species and range: cp(5) h(6) s(6)
-constexpr double kDefaultNewtonTol = 0.1;   // Newton stop, in units of the local error test
+constexpr double kDefaultNewtonTol = 0.2;   // Newton stop, in units of the local error test
 
 // Device-resident mechanism tables.  Reactions are stored sorted by kind:
 // [0, n_elem) elementary, [n_elem, n_tb_end) third-body, [n_tb_end, I) Troe falloff.
