@@ -761,9 +761,10 @@ __device__ void lu_solve(const WarpMem& w, int n, double (&x)[NPL], int lane) {
 // ------------------------------------------------------------------------------------------
 constexpr int kMaxOrd = 5;
 constexpr int kNewtonMax = 3;
-// accepted steps between Jacobian evaluations (CVODE's default is 51); a Newton failure with a
-// stale Jacobian refreshes it earlier
-constexpr int kJacMaxAge = 50;
+// accepted steps between Jacobian evaluations (CVODE's default is 51; with the Newton stop at
+// 0.2, 100 steps cost 2.9 % less time at unchanged parity); a Newton failure with a stale
+// Jacobian refreshes it earlier
+constexpr int kJacMaxAge = 100;
 
 __device__ __forceinline__ double bdf_gamma(int k) {
   // gamma_k = sum_{i=1..k} 1/i
