@@ -93,7 +93,9 @@ typedef struct {
   double newton_tol; /* Newton stop: estimated remaining correction in units of the local
                         error test (default 0.2 when <= 0) */
   int max_steps;     /* per-cell step budget (default 20000 when <= 0) */
-  int reserved;
+  int jac_max_age;   /* accepted steps a Jacobian is reused before it is re-evaluated (default
+                        100 when <= 0; a Newton failure with a stale Jacobian refreshes it
+                        earlier) */
 } chem_di_opts;
 
 /* Advance cells over dt by direct integration of the closed, adiabatic, constant-pressure

@@ -32,7 +32,7 @@ class HfrdOpts(C.Structure):
 
 class DiOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol_Y", C.c_double), ("atol_T", C.c_double),
-                ("newton_tol", C.c_double), ("max_steps", C.c_int), ("reserved", C.c_int)]
+                ("newton_tol", C.c_double), ("max_steps", C.c_int), ("jac_max_age", C.c_int)]
 
 
 def lib(auto_build: bool = False):
@@ -153,13 +153,13 @@ def chem_workspace_bytes(m: Mech, n: int) -> int:
 
 def chem_step_di(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0, atol_Y=0.0, atol_T=0.0,
                  max_steps=0, stats=None, workspace=None, n: Optional[int] = None,
-                 stream=None, newton_tol=0.0) -> None:
+                 stream=None, newton_tol=0.0, jac_max_age=0) -> None:
     ld = _ld(Y, m)
     if n is None:
         n = idx.numel() if idx is not None else ld
     if workspace is None:
         raise ValueError("chem_step_di needs a workspace tensor (chem_workspace_bytes)")
-    o = DiOpts(rtol, atol_Y, atol_T, newton_tol, max_steps, 0)
+    o = DiOpts(rtol, atol_Y, atol_T, newton_tol, max_steps, jac_max_age)
     _check(lib().chem_step_di(m.handle, n, ld, float(dt), _ptr(T, torch.float64),
                               _ptr(p, torch.float64), _ptr(Y, torch.float64),
                               _ptr(idx, torch.int32), C.byref(o), _ptr(status, torch.int32),
@@ -169,7 +169,7 @@ def chem_step_di(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0, atol_Y
 
 def chem_step_di_noalloc(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0, atol_Y=0.0,
                          atol_T=0.0, max_steps=0, stats=None, n: Optional[int] = None,
-                         stream=None, newton_tol=0.0) -> None:
+                         stream=None, newton_tol=0.0, jac_max_age=0) -> None:
     """chem_step_di without a workspace, for callers that cannot allocate device memory.
 
     Its scratch is a fixed device array inside the library shared by every call: calls that
@@ -178,7 +178,7 @@ def chem_step_di_noalloc(m: Mech, dt: float, T, p, Y, status, idx=None, rtol=0.0
     ld = _ld(Y, m)
     if n is None:
         n = idx.numel() if idx is not None else ld
-    o = DiOpts(rtol, atol_Y, atol_T, newton_tol, max_steps, 0)
+    o = DiOpts(rtol, atol_Y, atol_T, newton_tol, max_steps, jac_max_age)
     _check(lib().chem_step_di_noalloc(m.handle, n, ld, float(dt), _ptr(T, torch.float64),
                                       _ptr(p, torch.float64), _ptr(Y, torch.float64),
                                       _ptr(idx, torch.int32), C.byref(o),
@@ -534,12 +534,13 @@ def chem_ann_error(a: Ann) -> int:
 
 def chem_step_ann(m: Mech, a: Ann, dt: float, T, p, Y, status, workspace, idx=None, range_margin=0.05,
                   elem_tol=1e-2, T_min=250.0, T_max=3500.0, dT_max=0.0, no_fallback=False,
-                  di_rtol=0.0, di_atol_Y=0.0, n: Optional[int] = None, stream=None) -> None:
+                  di_rtol=0.0, di_atol_Y=0.0, n: Optional[int] = None, stream=None,
+                  di_newton_tol=0.0, di_jac_max_age=0) -> None:
     ld = _ld(Y, m)
     if n is None:
         n = idx.numel() if idx is not None else ld
     o = AnnOpts(range_margin, elem_tol, T_min, T_max, dT_max, int(no_fallback), 0,
-                DiOpts(di_rtol, di_atol_Y, 0.0, 0.0, 0, 0))
+                DiOpts(di_rtol, di_atol_Y, 0.0, di_newton_tol, 0, di_jac_max_age))
     _check(lib().chem_step_ann(m.handle, a.handle, n, ld, float(dt), _ptr(T, torch.float64),
                                _ptr(p, torch.float64), _ptr(Y, torch.float64), _ptr(idx, torch.int32),
                                C.byref(o),

@@ -597,6 +597,7 @@ void chem::di_fill_defaults(chem_di_opts& o) {
   if (!(o.atol_T > 0)) o.atol_T = 1e-9;
   if (o.max_steps <= 0) o.max_steps = 20000;
   if (!(o.newton_tol > 0)) o.newton_tol = kDefaultNewtonTol;
+  if (o.jac_max_age <= 0) o.jac_max_age = kDefaultJacMaxAge;
 }
 
 extern "C" {

@@ -761,10 +761,6 @@ __device__ void lu_solve(const WarpMem& w, int n, double (&x)[NPL], int lane) {
 // ------------------------------------------------------------------------------------------
 constexpr int kMaxOrd = 5;
 constexpr int kNewtonMax = 3;
-// accepted steps between Jacobian evaluations (CVODE's default is 51; with the Newton stop at
-// 0.2, 100 steps cost 2.9 % less time at unchanged parity); a Newton failure with a stale
-// Jacobian refreshes it earlier
-constexpr int kJacMaxAge = 100;
 
 __device__ __forceinline__ double bdf_gamma(int k) {
   // gamma_k = sum_{i=1..k} 1/i
@@ -909,7 +905,7 @@ __device__ __forceinline__ void bdf_accept(double (&D)[kMaxOrd + 3][NPL], const 
 
 struct DiOpts {
   double rtol, atol_Y, atol_T, newton_tol;
-  int max_steps;
+  int max_steps, jac_max_age;   // Jacobian reuse: a Newton failure with a stale one refreshes it
 };
 
 template <int NPL>
@@ -1106,7 +1102,7 @@ __device__ int integrate_cell(const DevMech& m, const WarpMem& w, double pc, dou
       case 4: bdf_accept<4, NPL>(D, d); break;
       default: bdf_accept<5, NPL>(D, d); break;
     }
-    if (jac_age >= kJacMaxAge) need_jac = true;
+    if (jac_age >= o.jac_max_age) need_jac = true;
     if (n_equal < order + 1) continue;
     // order and step-size selection
     double em[NPL], ep[NPL];
@@ -1388,7 +1384,7 @@ int launch_di(const DevMech& m, int64_t n, int64_t ld, double dt, double* T, con
               double* Y, const int32_t* idx, const chem_di_opts& opts, int32_t* status,
               int32_t* stats, unsigned int* queue, cudaStream_t s, const int32_t* n_dev) {
   const size_t wb = di_smem_per_warp(m);
-  DiOpts o{opts.rtol, opts.atol_Y, opts.atol_T, opts.newton_tol, opts.max_steps};
+  DiOpts o{opts.rtol, opts.atol_Y, opts.atol_T, opts.newton_tol, opts.max_steps, opts.jac_max_age};
   int wpb;
   size_t smem;
   int rc;

@@ -15,6 +15,9 @@ constexpr double kP0 = 101325.0;      // standard pressure of the NASA-7 entropi
 constexpr int kMaxEx = 4;             // non-unit third-body efficiencies kept per reaction
 constexpr int kThermoStride = 17;     // per species and range: cp(5) h(6) s(6)
 constexpr double kDefaultNewtonTol = 0.2;   // Newton stop, in units of the local error test
+// accepted steps between Jacobian evaluations (CVODE's default is 51; with the Newton stop at
+// 0.2, 100 steps cost 2.9 % less time on the 30-species workload at unchanged parity)
+constexpr int kDefaultJacMaxAge = 100;
 
 // Device-resident mechanism tables.  Reactions are stored sorted by kind:
 // [0, n_elem) elementary, [n_elem, n_tb_end) third-body, [n_tb_end, I) Troe falloff.
