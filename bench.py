@@ -57,9 +57,9 @@ def load_peaks() -> dict:
 
 PEAKS = load_peaks()
 # DRAM bytes of one di_kernel launch per cell, from an 8,202-cell ncu capture of the current
-# kernel (dram__bytes_read.sum + dram__bytes_write.sum = 2,946,816 + 0 B; the written state
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum = 2,968,576 + 0 B; the written state
 # stayed in L2 there), scaled to a launch by the cells processed
-DI_DRAM_BYTES_PER_CELL = 2946816 / 8202
+DI_DRAM_BYTES_PER_CELL = 2968576 / 8202
 
 
 # ------------------------------------------------------------------------------------------
