@@ -86,7 +86,8 @@ struct WarpMem {
   double* kre;    // I   effective reverse coefficient
   double* aux;    // I   d q / d [M] factor (third-body: q0, Troe: dk/dM (fwd - rev/Kc))
   double* qT;     // I   d q / d T at fixed C
-  double* tr;     // 14 per Troe reaction: exponentials, F_cent, P_r, logs, k, dk/d[M], dln k/dT
+  double* tr;     // 14 per Troe reaction: [0..4] the exponentials of the rounds, [10] k,
+                  // [11] dk/d[M], [12] dln k/dT (the other slots are spare)
   double* invd;   // n   reciprocal pivots
   double* ru;     // 64  step-size change matrix (0..24) and R(f) (32..56)
   int* perm;      // n   row permutation of the LU
