@@ -6,6 +6,7 @@
     python -m paper_2402_18858_gb300.profile_cases thermo64 --cells 1048576
     python -m paper_2402_18858_gb300.profile_cases mlp --cells 65536
     python -m paper_2402_18858_gb300.profile_cases mlp_ps --cells 65536
+    python -m paper_2402_18858_gb300.profile_cases ann --cells 2000000 --state-seed 3 --dt-cap 0
     python -m paper_2402_18858_gb300.profile_cases rates --cells 65536
     python -m paper_2402_18858_gb300.profile_cases jacobian --cells 8192
     python -m paper_2402_18858_gb300.profile_cases pasr --cells 1048576
@@ -31,12 +32,15 @@ CKPT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models", "ann_c
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["di", "thermo", "thermo64", "mlp", "mlp_ps", "rates", "jacobian", "pasr"])
+    ap.add_argument("case", choices=["di", "thermo", "thermo64", "mlp", "mlp_ps", "ann", "rates", "jacobian", "pasr"])
     ap.add_argument("--cells", type=int, default=8192)
     ap.add_argument("--repeats", type=int, default=2)
     ap.add_argument("--kind", default=MECH[0], help="mechanism kind (the DI case only; default c_30)")
     ap.add_argument("--mech-seed", type=int, default=MECH[1])
     ap.add_argument("--dt", type=float, default=5e-6, help="flow step of the DI case (s)")
+    ap.add_argument("--state-seed", type=int, default=101, help="seed of the cell states")
+    ap.add_argument("--dt-cap", type=float, default=0.0,
+                    help="ann case: fallback when the predicted |dT| exceeds it (0: no cap)")
     a = ap.parse_args()
     if (a.kind, a.mech_seed) != MECH and a.case != "di":
         ap.error("--kind/--mech-seed apply to the di case only")
@@ -44,7 +48,7 @@ def main():
     mech = (a.kind, a.mech_seed)
     m = wl.make_mechanism(*mech)
     gm = chem.chem_load_mech(wl.mechanism_file(*mech, os.path.join(tempfile.gettempdir(), "chem_mech")))
-    st = wl.make_states(m, a.cells, 101)
+    st = wl.make_states(m, a.cells, a.state_seed)
     dev = torch.device("cuda")
     T0 = torch.as_tensor(st.T, device=dev)
     p = torch.as_tensor(st.p, device=dev)
@@ -88,6 +92,19 @@ def main():
 
         def run():
             chem.thermo_props(gm, T0, Y0, *outs, mixed_precision=mixed)
+    elif a.case == "ann":
+        # the learned step (features, MLP, update, fallback DI at rtol 1e-5) with the committed
+        # network, in place on fresh copies of the states
+        ann = chem.chem_ann_load(gm, CKPT)
+        status = torch.empty(n, dtype=torch.int32, device=dev)
+        ws = torch.empty(chem.chem_ann_workspace_bytes(ann, n), dtype=torch.uint8, device=dev)
+        T, Y = T0.clone(), Y0.clone()
+
+        def run():
+            T.copy_(T0)
+            Y.copy_(Y0)
+            chem.chem_step_ann(gm, ann, a.dt, T, p, Y, status, ws, elem_tol=1e-2, dT_max=a.dt_cap,
+                               di_rtol=1e-5, di_atol_Y=1e-10)
     elif a.case == "mlp_ps":
         # one 1600-800-400 network per species (grouped GEMMs), random weights
         ann0 = chem.chem_ann_load(gm, CKPT)
@@ -122,6 +139,8 @@ def main():
         # per-cell means of the kernel's counters: BDF steps, RHS, Jacobians, LU factorisations
         c = stats.view(4, n).double().mean(dim=1).tolist()
         out.update(steps=c[0], rhs=c[1], jac=c[2], lu=c[3], failed=int((status != 0).sum().item()))
+    if a.case == "ann":
+        out.update(fallback=int((status != 0).sum().item()))
     print(json.dumps(out))
 
 
