@@ -242,8 +242,8 @@ def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 # ------------------------------------------------------------------------------------------
 # the learned step's update of the cell state (Sec. 2.2 output definition with Eq. 7, and the
-# fallback rules of the spec reading: range, non-finite values, element conservation,
-# temperature range and an optional cap on |dT|)
+# fallback rules, which the paper does not state: range, non-finite values, element
+# conservation, temperature range and an optional cap on |dT|)
 # ------------------------------------------------------------------------------------------
 FLAG_RANGE, FLAG_NONFINITE, FLAG_ELEMENTS, FLAG_T_RANGE, FLAG_DT = 1, 2, 4, 8, 16
 
